@@ -1,0 +1,407 @@
+"""Throughput benchmark of the lock-exchange LBM step on GB300.
+
+Workload (one bench step): 100 time steps of the 2048 x 128 x 256 lock-exchange
+box, D3Q19 BGK-Smagorinsky + D3Q7 scalar, FP32 storage (H = x0 = 256,
+u_b = 0.03, Re = 30000, Sc = 1, C_s = 0.17), followed by one diagnostics pass
+(front, F_w, FP64 budgets) - the logging interval of the paper's runs.  The
+state (7 GB) is far larger than L2, so no flush is needed between steps.
+
+Prints one JSON line (rank 0): MNUPS over all ranks, the end-to-end figure
+through host buffers, the HBM roofline of the step kernel, the FP64 oracle
+timed on the host cores, side measurements (16-bit storage, cumulant model,
+adjoint / forward ratio) and the SM clocks seen during the timed region.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+INNER = 100                     # time steps per bench step
+WORKLOAD = dict(nx=2048, ny=128, nz=256, H=256, x0=256, u_b=0.03, Re=30000.0)
+BYTES_PER_NODE = {("bgk", "fp32"): 208, ("cumulant", "fp32"): 272,
+                  ("bgk", "fp16s"): 104, ("bgk", "bf16s"): 104,
+                  ("cumulant", "fp16s"): 136, ("cumulant", "bf16s"): 136}
+PROFILE = os.path.join(ROOT, "profiles", "aa_step_bgk_fp32_traffic.md")
+KERNEL_SOURCES = ["paper_2112_08479_gb300/csrc/lbm_bgk.cu",
+                  "paper_2112_08479_gb300/csrc/lbm_common.cuh"]
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for s in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, s), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(nodes: int):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary,
+    scaled to `nodes`; None when the kernel changed since the capture."""
+    try:
+        txt = open(PROFILE).read()
+    except OSError:
+        return None
+    m = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", txt)
+    b = re.search(r"dram_bytes_per_node_update:\s*([0-9.eE+-]+)", txt)
+    if not m or not b or m.group(1) != kernel_hash():
+        return None
+    return float(b.group(1)) * nodes
+
+
+def measured_peak_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.fh = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        self.t0 = self.t1 = None
+
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.flush()
+        self.fh.seek(0)
+        rows = [r.split(",") for r in self.fh.read().strip().splitlines() if r.strip()]
+        os.unlink(self.fh.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                mhz = float(r[1]); mx = float(r[2]); pw = float(r[3])
+            except (ValueError, IndexError):
+                continue
+            if pw > 300.0:  # under load
+                sm.append(mhz)
+                smax.append(mx)
+                for name, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples_under_load": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+            dist.init_process_group(backend, device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group(backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v: float, ws: int) -> float:
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+def oracle_sample(seconds_hint: float = 15.0):
+    """The FP64 C oracle (single thread, as it stands) on a bounded sample of
+    the workload's physics: a 1024 x 64 x 128 box with the same lattice
+    parameters, 2 time steps."""
+    import oracle as O
+    nx, ny, nz, steps = 1024, 64, 128, 2
+    u_b, H, Re = WORKLOAD["u_b"], WORKLOAD["H"], WORKLOAD["Re"]
+    nu = u_b * H / Re
+    p = O.OracleParams(nx, ny, nz, model=0, nu=nu, D=nu, cs_smag=0.17, gprime=u_b * u_b / H)
+    f, phi = O.init(p, O.lock_chi0(nx, ny, nz, 128, 1e-3, 2112))
+    t = time.perf_counter()
+    O.run(p, steps, f, phi)
+    dt = time.perf_counter() - t
+    return {"value": nx * ny * nz * steps / dt / 1e6, "unit": "MNUPS", "cores": 1, "kind": "oracle",
+            "sample": f"{steps} steps of a {nx}x{ny}x{nz} box with the workload's lattice "
+                      f"parameters (BGK-Smagorinsky D3Q19 + D3Q7, FP64, single thread), {dt:.1f} s"}
+
+
+def run_reference(args, ws, rank):
+    """Reference arm: the FP64 oracle as it stands on the host cores."""
+    if rank != 0:
+        return
+    import oracle as O
+    O.build()
+    nx, ny, nz = 256, 64, 128
+    u_b, H, Re = WORKLOAD["u_b"], WORKLOAD["H"], WORKLOAD["Re"]
+    nu = u_b * H / Re
+    p = O.OracleParams(nx, ny, nz, model=0, nu=nu, D=nu, cs_smag=0.17, gprime=u_b * u_b / H)
+    f, phi = O.init(p, O.lock_chi0(nx, ny, nz, 32, 1e-3, 2112))
+    for _ in range(args.warmup):
+        f, phi = O.run(p, 1, f, phi)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        f, phi = O.run(p, 1, f, phi)
+    dt = time.perf_counter() - t
+    v = nx * ny * nz * args.steps / dt / 1e6
+    line = {"metric": "MNUPS (lattice node updates per second / 1e6), fused LBM step",
+            "value": v, "unit": "MNUPS", "impl": "reference", "n_gpus": 0, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict(ws),
+            "cpu_baseline": {"value": v, "unit": "MNUPS", "cores": 1, "kind": "oracle",
+                             "sample": f"one time step per bench step of a {nx}x{ny}x{nz} box "
+                                       "with the workload's lattice parameters"},
+            "e2e": {"value": v, "unit": "MNUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_dict(ws):
+    return {"workload": "lock-exchange 2048x128x256, D3Q19 BGK-Smagorinsky + D3Q7 scalar, "
+                        "FP32, Re=30000, 100 steps + diagnostics per bench step",
+            "nodes": WORKLOAD["nx"] * WORKLOAD["ny"] * WORKLOAD["nz"],
+            "steps_per_bench_step": INNER, "parallelism": f"replicas x{ws}",
+            "l2": "inputs larger than L2 (7.0 GB state), no flush"}
+
+
+# ---------------------------------------------------------------------------
+def make_lattice(model="bgk", storage="fp32", **over):
+    from paper_2112_08479_gb300 import lbm
+    w = dict(WORKLOAD)
+    w.update(over)
+    p = lbm.lock_exchange(w["nx"], w["ny"], w["nz"], H=w["H"], x0=w["x0"], u_b=w["u_b"],
+                          Re=w["Re"], model=model, storage=storage)
+    return lbm.Lattice(p, device="cuda")
+
+
+def timed_loop(lat, steps, warmup, torch, inner=INNER, with_diag=True, kernel_events=True):
+    """Returns (total seconds, mean step-kernel seconds, launches)."""
+    s = lat.stream
+    for _ in range(warmup):
+        lat.step(inner)
+        if with_diag:
+            lat.diag()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(s)
+    for k in range(steps):
+        evs[k][0].record(s)
+        lat.step(inner)
+        evs[k][1].record(s)
+        if with_diag:
+            lat.diag()
+    t1.record(s)
+    torch.cuda.synchronize()
+    total = t0.elapsed_time(t1) / 1e3
+    kern = sum(a.elapsed_time(b) for a, b in evs) / 1e3 / (steps * inner)
+    launches = steps * (inner + (2 if with_diag else 0))
+    return total, kern, launches
+
+
+def side_variant(torch, model, storage, steps=3):
+    lat = make_lattice(model, storage)
+    total, kern, _ = timed_loop(lat, steps, 1, torch, with_diag=False)
+    n = lat.N
+    mnups = n / kern / 1e6
+    gbs = BYTES_PER_NODE[(model, storage)] * n / kern / 1e9
+    del lat
+    torch.cuda.empty_cache()
+    return {"mnups": mnups, "ms_per_time_step": kern * 1e3, "achieved_gbs": gbs}
+
+
+def adjoint_ratio(torch):
+    """Forward step vs one reverse step (forward recompute with trajectory save
+    + adjoint kernel) on the 256 x 32 x 64 differentiation box."""
+    from paper_2112_08479_gb300 import lbm
+    p = lbm.lock_exchange(256, 32, 64, H=64, x0=64, u_b=0.03, Re=2000.0)
+    lat = lbm.Lattice(p, device="cuda")
+    K = 100
+    s = lat.stream
+    states = torch.empty(K, 26, p.N, device="cuda")
+    lam = [torch.zeros(26, p.N, device="cuda") for _ in range(2)]
+    dcs = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ck = lat.get_state()
+
+    def fwd():
+        lat.step(K)
+
+    def rev():
+        lat.set_state(ck, 0)
+        for k in range(K):
+            lat.step_save(states[k])
+        for k in range(K - 1, -1, -1):
+            lat.adjoint_step(states[k], lam[(k + 1) % 2], lam[k % 2], dcs, 1.0)
+
+    out = {}
+    for name, fn in (("forward", fwd), ("reverse", rev)):
+        fn()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        for _ in range(3):
+            fn()
+        b.record(s)
+        torch.cuda.synchronize()
+        out[name] = a.elapsed_time(b) / 3 / K
+    return {"workload": "256x32x64 BGK-Smagorinsky, K=100 segment", "fwd_ms_per_step": out["forward"],
+            "adj_ms_per_step": out["reverse"], "ratio": out["reverse"] / out["forward"]}
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+    from paper_2112_08479_gb300 import lbm
+    lbm.load()
+    torch.cuda.set_device(local)
+    sampler = ClockSampler(torch.cuda.current_device() if ws == 1 else local)
+
+    lat = make_lattice()
+    N = lat.N
+    barrier(ws)
+    torch.cuda.synchronize()
+    sampler.mark_start()
+    total, kern, launches = timed_loop(lat, args.steps, args.warmup, torch)
+    sampler.mark_end()
+    barrier(ws)
+    tmax = max_over_ranks(total, ws)
+    value = N * INNER * args.steps * ws / tmax / 1e6
+    d = lat.diag()
+
+    # end to end through the public API with host buffers: the step's scalar
+    # field comes from pinned host memory, the diagnostics go back to the host
+    import numpy as np
+    chi0 = torch.from_numpy(
+        np.where(np.arange(WORKLOAD["nx"]) < WORKLOAD["x0"], 1.0, 0.0).astype(np.float32)
+    ).repeat(WORKLOAD["ny"] * WORKLOAD["nz"]).pin_memory()
+    s = lat.stream
+    for _ in range(max(1, args.warmup)):
+        lat.set_scalar(chi0)
+        lat.step(INNER)
+        lat.diag()
+    torch.cuda.synchronize()
+    barrier(ws)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        lat.set_scalar(chi0)
+        lat.step(INNER)
+        lat.diag()
+    torch.cuda.synchronize()
+    e2e_t = max_over_ranks(time.perf_counter() - t0, ws)
+    e2e = {"value": N * INNER * args.steps * ws / e2e_t / 1e6, "unit": "MNUPS",
+           "h2d_bytes_per_step": int(chi0.numel() * 4),
+           "d2h_bytes_per_step": int(__import__("ctypes").sizeof(lbm.lbm_diagnostics))}
+    clocks = sampler.stop()
+    del lat
+    torch.cuda.empty_cache()
+
+    peak, peak_kind = measured_peak_hbm()
+    achieved = BYTES_PER_NODE[("bgk", "fp32")] * N / kern / 1e9
+    roof = {"bound": "hbm", "kernel": "bgk_step_kernel (AA even/odd, FP32)",
+            "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": profiled_traffic(N),
+            "algorithmic_bytes_per_launch": BYTES_PER_NODE[("bgk", "fp32")] * N,
+            "mean_launch_ms": kern * 1e3}
+
+    extra = {}
+    if rank == 0 and ws == 1 and not args.no_side:
+        variants = {}
+        for model, storage in (("bgk", "fp16s"), ("bgk", "bf16s"), ("cumulant", "fp32"),
+                               ("cumulant", "fp16s")):
+            r = side_variant(torch, model, storage)
+            r["hbm_frac"] = r.pop("achieved_gbs") / peak
+            variants[f"{model}_{storage}"] = r
+        extra["variants"] = variants
+        extra["adjoint"] = adjoint_ratio(torch)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        cpu = oracle_sample()
+
+    if rank == 0:
+        line = {"metric": "MNUPS (lattice node updates per second / 1e6), fused LBM step",
+                "value": value, "unit": "MNUPS", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": tmax / args.steps * 1e3,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic (lock-exchange initial condition)",
+                "config": config_dict(ws), "e2e": e2e, "gpu_launches": launches,
+                "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
+                "diag_at_end": {"front": d["front"], "Fw": d["Fw"], "step": d["step"]}}
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-side", action="store_true", help="skip the side measurements")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle timing")
+    args = ap.parse_args()
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

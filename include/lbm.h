@@ -1,0 +1,218 @@
+/*
+ * lbm.h -- C ABI of the GB300 lock-exchange lattice Boltzmann library.
+ *
+ * The library advances the coupled fluid / scalar lattice Boltzmann model of
+ * Adekanye et al., "GPU accelerated LBM simulations of dilute gravity
+ * currents" (arXiv 2112.08479), one fused stream + collide kernel per time
+ * step, on one CUDA device:
+ *
+ *   fluid   D3Q19 BGK with a Smagorinsky eddy viscosity and Guo forcing
+ *           (Sec. 2.3.1, Eq. 17-26, 32-34), or D3Q27 cumulant
+ *           (Sec. 2.3.1 "VirtualFluids", Eq. 52-58);
+ *   scalar  D3Q7 BGK advection-diffusion (Eq. 27-30, 35);
+ *   force   Boussinesq body force F = g' chi e^g (Sec. 2.1, Eq. 11);
+ *   walls   half-way bounce-back at both x ends and both z ends, periodic
+ *           in y (Sec. 2.5).
+ *
+ * Conventions shared by every entry point:
+ *  - Lattice units, dx = dt = 1.  Node index n = x + nx * (y + ny * z).
+ *  - Ownership: the caller allocates every device buffer, including the
+ *    workspace handed to lbm_init; the library allocates no device memory.
+ *    lbm_ctx is a small host object owned by the library.
+ *  - Execution: all device work is enqueued on the CUDA stream given to
+ *    lbm_init and is asynchronous, except where an entry point says it
+ *    synchronises.  Device pointers must be usable on that stream's device.
+ *  - Errors: arguments are checked on the host before anything is enqueued
+ *    (LBM_ERR_ARG, nothing happens).  Launch failures return LBM_ERR_CUDA.
+ *    Asynchronous faults and the device-side sticky flags (non-finite value,
+ *    rho <= 0) are reported by the next synchronising call (lbm_diag,
+ *    lbm_sync).  Nothing aborts, exits or traps.
+ *  - Canonical state layout (lbm_get_state / lbm_set_state / adjoint):
+ *    FP32, direction-major, [Q + 7][N]: rows 0..Q-1 hold f_i - w_i of the
+ *    pre-collision (streamed) fluid populations, rows Q..Q+6 hold Phi_k of
+ *    the scalar populations.  Direction orders: D3Q19 as in Eq. 23; D3Q27
+ *    as Eq. 23 followed by the corners (1,1,1), (-1,-1,-1), (1,1,-1),
+ *    (-1,-1,1), (1,-1,1), (-1,1,-1), (-1,1,1), (1,-1,-1); D3Q7 rest, +x, -x,
+ *    +y, -y, +z, -z.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LBM_API __attribute__((visibility("default")))
+#else
+#define LBM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum lbm_status {
+    LBM_OK = 0,
+    LBM_ERR_ARG = 1,       /* invalid argument; nothing was enqueued */
+    LBM_ERR_CUDA = 2,      /* a CUDA call or launch failed */
+    LBM_ERR_NOMEM = 3,     /* workspace smaller than lbm_workspace_bytes */
+    LBM_ERR_UNSTABLE = 4,  /* sticky device flag: non-finite value or rho <= 0 */
+    LBM_ERR_STATE = 5,     /* call not valid in the context's current state */
+    LBM_ERR_TIMEOUT = 6    /* a bounded wait gave up */
+} lbm_status;
+
+typedef enum lbm_model {
+    LBM_BGK_SMAG_Q19 = 0,  /* Sec. 2.3.1 RAFSINE physics: Eq. 21-26, 32-34 */
+    LBM_CUMULANT_Q27 = 1   /* Sec. 2.3.1 VirtualFluids physics: Eq. 54-58, all
+                              rates of order >= 3 equal to 1 */
+} lbm_model;
+
+typedef enum lbm_storage {
+    LBM_FP32 = 0,   /* populations stored as FP32: f - w and Phi */
+    LBM_FP16S = 1,  /* FP16, scale_f * (f - w) and scale_phi * Phi, RN rounding */
+    LBM_BF16S = 2   /* BF16, same shifts and scales, RN rounding */
+} lbm_storage;
+
+/* lbm_params.flags */
+#define LBM_FLAG_NO_COLLIDE 1  /* skip every collision: pure streaming (tests) */
+#define LBM_FLAG_PERIODIC_X 2  /* periodic instead of walls at the x ends */
+#define LBM_FLAG_PERIODIC_Z 4  /* periodic instead of walls at the z ends */
+
+/* sticky device flags reported in lbm_diagnostics.flags */
+#define LBM_DEVFLAG_NONFINITE 1   /* a macroscopic value was NaN or Inf */
+#define LBM_DEVFLAG_RHO_NONPOS 2  /* rho <= 0 at some node */
+
+typedef struct lbm_params {
+    int32_t nx, ny, nz;       /* nodes; 1 <= nx, ny, nz; nx*ny*nz < 2^31;
+                                 ny, nz <= 65535 */
+    int32_t model;            /* lbm_model */
+    int32_t storage;          /* lbm_storage */
+    int32_t flags;            /* LBM_FLAG_* */
+    double nu;                /* molecular viscosity, tau0 = 3 nu + 1/2 (Eq. 25); > 0 */
+    double D;                 /* molecular diffusivity, tau_Phi = 1/2 + 4 D (Eq. 30
+                                 with c_sPhi^2 = 1/4 on D3Q7); > 0 */
+    double cs_smag;           /* classical Smagorinsky constant, nu_T = (C_s)^2 |S|
+                                 (Eq. 32, Delta = 1); BGK only; >= 0 */
+    double sc_t;              /* turbulent Schmidt number, D_eff = D + nu_T / Sc_T
+                                 (Eq. 35); > 0 */
+    double gprime;            /* reduced gravity g' in F = g' chi e^g (Eq. 11) */
+    double eg[3];             /* gravity direction e^g, (0, 0, -1) in the paper */
+    double omega_bulk;        /* cumulant: relaxation rate of the second-order trace
+                                 (1 = equilibrium each step); (0, 2) */
+    int32_t x0;               /* lock gate: chi0 = 1 for x < x0 (Table 1); 0..nx */
+    int32_t H;                /* depth used to scale the front, > 0 (usually nz) */
+    double noise_amp;         /* chi0 += noise_amp * U(-1, 1) on column x0 - 1 */
+    uint64_t seed;            /* noise draw for node n: splitmix64(seed ^ n) */
+    double front_threshold;   /* span-averaged chi threshold of the front (0.02) */
+    double scale_f;           /* 16-bit storage scale of f - w (power of two) */
+    double scale_phi;         /* 16-bit storage scale of Phi (power of two) */
+} lbm_params;
+
+typedef struct lbm_diagnostics {
+    double front;        /* (x_f + 1/2 - x0) / H, Sec. 3.1 */
+    double front_node;   /* x_f in node coordinates, -1 when no column reaches
+                            the threshold */
+    double Fw;           /* bottom-wall friction sum_{x,y} tau_w, Eq. 62-64,
+                            lattice units, streamwise component */
+    double mass_delta;   /* sum over nodes of rho - 1 (FP64 reduction) */
+    double scalar_mass;  /* sum over nodes of chi (FP64 reduction) */
+    int64_t step;        /* time step the values belong to */
+    int32_t flags;       /* LBM_DEVFLAG_* seen since lbm_init (sticky) */
+    int32_t pad_;
+} lbm_diagnostics;
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Human-readable name of a status code.  Never NULL. */
+LBM_API const char* lbm_status_string(lbm_status s);
+
+/* Last error message recorded on ctx (empty string when none). */
+LBM_API const char* lbm_last_error(const lbm_ctx* ctx);
+
+/* Checks p without touching the device.  LBM_OK or LBM_ERR_ARG. */
+LBM_API lbm_status lbm_validate(const lbm_params* p);
+
+/* Bytes of device workspace lbm_init needs for p; 0 when p is invalid.
+ * Populations take (Q + 7) * N * (4 or 2) bytes; the rest is a few N/nx-sized
+ * staging and reduction buffers. */
+LBM_API size_t lbm_workspace_bytes(const lbm_params* p);
+
+/* Creates a context over a caller-owned device workspace of `bytes` bytes
+ * (>= lbm_workspace_bytes(p), 256-byte aligned) and enqueues the initial
+ * condition of Sec. 2.5 on `cuda_stream` (a cudaStream_t, NULL = legacy
+ * default stream): f = w (rho = 1, u = 0), chi0 = 1 for x < x0 else 0, plus
+ * the noise on column x0 - 1, Phi_k = w_k chi0.  The workspace must outlive
+ * the context.  *out is set only on LBM_OK. */
+LBM_API lbm_status lbm_init(const lbm_params* p, void* workspace, size_t bytes,
+                    void* cuda_stream, lbm_ctx** out);
+
+/* Re-initialises the state from a caller-given scalar field chi0 (N floats,
+ * host or device memory; copied on the stream before return of control to
+ * the device queue): f = w, Phi_k = w_k chi0.  Resets the step counter. */
+LBM_API lbm_status lbm_set_scalar(lbm_ctx* ctx, const float* chi0);
+
+/* Advances nsteps >= 0 time steps (Eq. 17): one fused in-place kernel per
+ * step (AA pattern: even steps collide in place, odd steps gather from and
+ * scatter to the neighbours).  Asynchronous. */
+LBM_API lbm_status lbm_step(lbm_ctx* ctx, int32_t nsteps);
+
+/* One time step that also writes the pre-collision state of the current
+ * step, in the canonical layout, to state_out ((Q + 7) * N floats, device).
+ * Used to record the forward trajectory for the adjoint. */
+LBM_API lbm_status lbm_step_save(lbm_ctx* ctx, float* state_out);
+
+/* Macroscopic fields of the current state (Eq. 19, 20 with the half-force
+ * shift, 27): rho (N floats), u (3 * N floats, component-major [3][N]), chi
+ * (N floats).  Device buffers; any may be NULL.  Asynchronous. */
+LBM_API lbm_status lbm_macros(lbm_ctx* ctx, float* rho, float* u, float* chi);
+
+/* Diagnostics of the current state (Sec. 3.1 front, Eq. 62-64 F_w, FP64
+ * mass and scalar budgets) into a host struct.  Synchronises the stream.
+ * Returns LBM_ERR_UNSTABLE when a sticky device flag is set (the struct is
+ * still filled), LBM_ERR_CUDA on an asynchronous fault. */
+LBM_API lbm_status lbm_diag(lbm_ctx* ctx, lbm_diagnostics* out_host);
+
+/* Adds weight * F_w(current state) to *acc_dev (one device double).
+ * Asynchronous.  Used for the time-integrated friction objective. */
+LBM_API lbm_status lbm_fw_accumulate(lbm_ctx* ctx, double* acc_dev, double weight);
+
+/* Copies the current state to dst ((Q + 7) * N floats, canonical layout,
+ * device).  Asynchronous. */
+LBM_API lbm_status lbm_get_state(lbm_ctx* ctx, float* dst);
+
+/* Loads a state in the canonical layout (device) and sets the step counter.
+ * Asynchronous. */
+LBM_API lbm_status lbm_set_state(lbm_ctx* ctx, const float* src, int64_t step);
+
+/* One reverse step of the discrete adjoint of the BGK-Smagorinsky + scalar +
+ * Boussinesq step (BGK model, FP32 arithmetic):
+ *   lam_n = (dT/ds_n)^T lam_next + w_fw * dF_w(s_n)/ds_n,
+ *   *dJdCs_dev += lam_next . dT/dC_s (s_n),
+ * where T is the time step of lbm_step, s_n = state_n (canonical layout,
+ * device, (Q + 7) * N floats) is the state it was applied to, and lam_next,
+ * lam_n are adjoint states in the canonical layout (device, (Q + 7) * N
+ * floats; lam_next == NULL means zero).  lam_n must not alias lam_next or
+ * state_n.  dJdCs_dev: one device double, accumulated.  Asynchronous.
+ * LBM_ERR_STATE for the cumulant model. */
+LBM_API lbm_status lbm_adjoint_step(lbm_ctx* ctx, const float* state_n, const float* lam_next,
+                            float* lam_n, double* dJdCs_dev, double w_fw);
+
+/* Gradient with respect to the initial scalar field of a quantity whose
+ * adjoint at step 0 is lam0: grad_chi0[n] = sum_k w_k lam0_Phi_k[n]
+ * (since Phi_k = w_k chi0 at t = 0).  Device buffers.  Asynchronous. */
+LBM_API lbm_status lbm_adjoint_chi0(lbm_ctx* ctx, const float* lam0, float* grad_chi0);
+
+/* Current step counter. */
+LBM_API int64_t lbm_get_step(const lbm_ctx* ctx);
+
+/* Synchronises the stream; reports asynchronous CUDA faults. */
+LBM_API lbm_status lbm_sync(lbm_ctx* ctx);
+
+/* Frees the host context (not the caller's workspace).  NULL is a no-op. */
+LBM_API void lbm_destroy(lbm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

@@ -1,0 +1,338 @@
+// lbm_api.cu -- host side of the C ABI declared in include/lbm.h.
+//
+// Validates parameters, lays out the caller-owned workspace, derives the
+// kernel constants from the physical parameters and enqueues the kernels on
+// the caller's stream.  The library allocates no device memory.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "lbm_internal.h"
+
+using namespace lbmgpu;
+
+struct lbm_ctx {
+    lbm_params p;
+    KParams kp;
+    Views v;
+    cudaStream_t stream;
+    int64_t step;
+    int odd;          // parity of the AA layout: the next step is odd when set
+    char err[256];
+};
+
+namespace {
+
+thread_local char g_err[256] = "";
+
+constexpr size_t ALIGN = 256;
+inline size_t up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
+
+struct Layout {
+    size_t f, phi, stage, chibar, colmax, part, fwpart, ddiag, total;
+    unsigned nblocks;
+};
+
+int q_of(const lbm_params* p) { return p->model == LBM_CUMULANT_Q27 ? 27 : 19; }
+size_t elem_size(const lbm_params* p) { return p->storage == LBM_FP32 ? 4 : 2; }
+
+bool finite(double v) { return isfinite(v) != 0; }
+
+const char* check(const lbm_params* p) {
+    if (!p) return "params is NULL";
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1) return "nx, ny, nz must be >= 1";
+    if (p->ny > 65535 || p->nz > 65535) return "ny and nz must be <= 65535";
+    if ((double)p->nx * p->ny * p->nz >= 2147483648.0) return "nx*ny*nz must be < 2^31";
+    if (p->model != LBM_BGK_SMAG_Q19 && p->model != LBM_CUMULANT_Q27) return "unknown model";
+    if (p->storage != LBM_FP32 && p->storage != LBM_FP16S && p->storage != LBM_BF16S)
+        return "unknown storage";
+    if (p->flags & ~(LBM_FLAG_NO_COLLIDE | LBM_FLAG_PERIODIC_X | LBM_FLAG_PERIODIC_Z))
+        return "unknown flag bits";
+    if (!finite(p->nu) || p->nu <= 0.0) return "nu must be finite and > 0";
+    if (!finite(p->D) || p->D <= 0.0) return "D must be finite and > 0";
+    if (!finite(p->cs_smag) || p->cs_smag < 0.0) return "cs_smag must be finite and >= 0";
+    if (!finite(p->sc_t) || p->sc_t <= 0.0) return "sc_t must be finite and > 0";
+    if (!finite(p->gprime)) return "gprime must be finite";
+    if (!finite(p->eg[0]) || !finite(p->eg[1]) || !finite(p->eg[2])) return "eg must be finite";
+    if (p->model == LBM_CUMULANT_Q27 && (!finite(p->omega_bulk) || p->omega_bulk <= 0.0 ||
+                                         p->omega_bulk >= 2.0))
+        return "omega_bulk must lie in (0, 2)";
+    if (p->x0 < 0 || p->x0 > p->nx) return "x0 must lie in [0, nx]";
+    if (p->H <= 0) return "H must be > 0";
+    if (!finite(p->noise_amp) || p->noise_amp < 0.0) return "noise_amp must be finite and >= 0";
+    if (!finite(p->front_threshold)) return "front_threshold must be finite";
+    if (!finite(p->scale_f) || p->scale_f <= 0.0 || !finite(p->scale_phi) || p->scale_phi <= 0.0)
+        return "scale_f and scale_phi must be finite and > 0";
+    return nullptr;
+}
+
+Layout layout(const lbm_params* p) {
+    Layout L;
+    const size_t N = (size_t)p->nx * p->ny * p->nz, es = elem_size(p);
+    L.nblocks = diag_block_count(p->nx, p->nz);
+    size_t o = 0;
+    L.f = o;      o = up(o + (size_t)q_of(p) * N * es);
+    L.phi = o;    o = up(o + 7 * N * es);
+    L.stage = o;  o = up(o + N * sizeof(float));
+    L.chibar = o; o = up(o + (size_t)p->nx * p->nz * sizeof(float));
+    L.colmax = o; o = up(o + (size_t)p->nx * sizeof(unsigned));
+    L.part = o;   o = up(o + (size_t)L.nblocks * 2 * sizeof(double));
+    L.fwpart = o; o = up(o + (size_t)L.nblocks * 2 * sizeof(float));
+    L.ddiag = o;  o = up(o + sizeof(DevDiag) + 2 * sizeof(int));
+    L.total = o;
+    return L;
+}
+
+KParams kparams(const lbm_params* p) {
+    KParams k;
+    memset(&k, 0, sizeof k);
+    k.nx = p->nx; k.ny = p->ny; k.nz = p->nz; k.flags = p->flags;
+    k.N = (unsigned)((size_t)p->nx * p->ny * p->nz);
+    k.nxny = (unsigned)((size_t)p->nx * p->ny);
+    const double tau0 = 3.0 * p->nu + 0.5;                        // Eq. 25
+    k.tau0 = (float)tau0;
+    k.A = (float)(18.0 * sqrt(2.0) * p->cs_smag * p->cs_smag);    // Eq. 34, R3
+    k.taup0 = (float)(0.5 + 4.0 * p->D);                          // Eq. 30, D3Q7
+    k.kT = p->model == LBM_BGK_SMAG_Q19 ? (float)(4.0 / (3.0 * p->sc_t)) : 0.0f;  // Eq. 35
+    k.om1 = (float)(1.0 / tau0);                                  // Eq. 58
+    k.om2 = (float)p->omega_bulk;
+    k.gx = (float)(p->gprime * p->eg[0]);                         // Eq. 11
+    k.gy = (float)(p->gprime * p->eg[1]);
+    k.gz = (float)(p->gprime * p->eg[2]);
+    const bool s16 = p->storage != LBM_FP32;
+    k.sf = s16 ? (float)p->scale_f : 1.0f;
+    k.isf = 1.0f / k.sf;
+    k.sp = s16 ? (float)p->scale_phi : 1.0f;
+    k.isp = 1.0f / k.sp;
+    k.nu = (float)p->nu;
+    return k;
+}
+
+lbm_status cuda_fail(lbm_ctx* c, cudaError_t e, const char* where) {
+    snprintf(c->err, sizeof c->err, "%s: %s", where, cudaGetErrorString(e));
+    return LBM_ERR_CUDA;
+}
+
+lbm_status arg_fail(lbm_ctx* c, const char* what) {
+    if (c) snprintf(c->err, sizeof c->err, "%s", what);
+    else snprintf(g_err, sizeof g_err, "%s", what);
+    return LBM_ERR_ARG;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lbm_status_string(lbm_status s) {
+    switch (s) {
+        case LBM_OK: return "ok";
+        case LBM_ERR_ARG: return "invalid argument";
+        case LBM_ERR_CUDA: return "CUDA error";
+        case LBM_ERR_NOMEM: return "workspace too small";
+        case LBM_ERR_UNSTABLE: return "unstable: non-finite value or rho <= 0";
+        case LBM_ERR_STATE: return "call not valid in this state";
+        case LBM_ERR_TIMEOUT: return "timeout";
+    }
+    return "unknown status";
+}
+
+const char* lbm_last_error(const lbm_ctx* ctx) { return ctx ? ctx->err : g_err; }
+
+lbm_status lbm_validate(const lbm_params* p) {
+    const char* m = check(p);
+    if (m) { snprintf(g_err, sizeof g_err, "%s", m); return LBM_ERR_ARG; }
+    return LBM_OK;
+}
+
+size_t lbm_workspace_bytes(const lbm_params* p) {
+    if (check(p)) return 0;
+    return layout(p).total;
+}
+
+lbm_status lbm_init(const lbm_params* p, void* workspace, size_t bytes, void* cuda_stream,
+                    lbm_ctx** out) {
+    if (!out) return arg_fail(nullptr, "out is NULL");
+    const char* m = check(p);
+    if (m) return arg_fail(nullptr, m);
+    if (!workspace) return arg_fail(nullptr, "workspace is NULL");
+    if ((uintptr_t)workspace % ALIGN) return arg_fail(nullptr, "workspace must be 256-byte aligned");
+    const Layout L = layout(p);
+    if (bytes < L.total) {
+        snprintf(g_err, sizeof g_err, "workspace has %zu bytes, needs %zu", bytes, L.total);
+        return LBM_ERR_NOMEM;
+    }
+    lbm_ctx* c = (lbm_ctx*)calloc(1, sizeof(lbm_ctx));
+    if (!c) return arg_fail(nullptr, "host allocation of the context failed");
+    c->p = *p;
+    c->kp = kparams(p);
+    c->stream = (cudaStream_t)cuda_stream;
+    uint8_t* w = (uint8_t*)workspace;
+    c->v.f = w + L.f;
+    c->v.phi = w + L.phi;
+    c->v.stage = (float*)(w + L.stage);
+    c->v.chibar = (float*)(w + L.chibar);
+    c->v.colmax = (unsigned*)(w + L.colmax);
+    c->v.part = (double*)(w + L.part);
+    c->v.fwpart = (float*)(w + L.fwpart);
+    c->v.ddiag = (DevDiag*)(w + L.ddiag);
+    c->v.devflags = (int*)(w + L.ddiag + sizeof(DevDiag));
+    c->v.diag_blocks = L.nblocks;
+    cudaError_t e = launch_init(c->kp, p->model, p->storage, c->v, nullptr, p->x0, p->noise_amp,
+                                p->seed, c->stream);
+    if (e != cudaSuccess) {
+        snprintf(g_err, sizeof g_err, "init launch: %s", cudaGetErrorString(e));
+        free(c);
+        return LBM_ERR_CUDA;
+    }
+    c->step = 0;
+    c->odd = 0;
+    *out = c;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_scalar(lbm_ctx* c, const float* chi0) {
+    if (!c) return arg_fail(nullptr, "ctx is NULL");
+    if (!chi0) return arg_fail(c, "chi0 is NULL");
+    cudaError_t e = cudaMemcpyAsync(c->v.stage, chi0, (size_t)c->kp.N * sizeof(float),
+                                    cudaMemcpyDefault, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "set_scalar copy");
+    e = launch_init(c->kp, c->p.model, c->p.storage, c->v, c->v.stage, 0, 0.0, 0, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "set_scalar init");
+    c->step = 0;
+    c->odd = 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_ctx* c, int32_t nsteps) {
+    if (!c) return arg_fail(nullptr, "ctx is NULL");
+    if (nsteps < 0) return arg_fail(c, "nsteps must be >= 0");
+    for (int32_t s = 0; s < nsteps; ++s) {
+        cudaError_t e = launch_step(c->kp, c->p.model, c->p.storage, c->odd != 0, c->v.f, c->v.phi,
+                                    nullptr, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "step launch");
+        c->odd ^= 1;
+        ++c->step;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_step_save(lbm_ctx* c, float* state_out) {
+    if (!c) return arg_fail(nullptr, "ctx is NULL");
+    if (!state_out) return arg_fail(c, "state_out is NULL");
+    cudaError_t e = launch_step(c->kp, c->p.model, c->p.storage, c->odd != 0, c->v.f, c->v.phi,
+                                state_out, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "step launch");
+    c->odd ^= 1;
+    ++c->step;
+    return LBM_OK;
+}
+
+lbm_status lbm_macros(lbm_ctx* c, float* rho, float* u, float* chi) {
+    if (!c) return arg_fail(nullptr, "ctx is NULL");
+    if (!rho && !u && !chi) return LBM_OK;
+    cudaError_t e = launch_macros(c->kp, c->p.model, c->p.storage, c->odd != 0, c->v, rho, u, chi,
+                                  c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "macros launch");
+    return LBM_OK;
+}
+
+lbm_status lbm_diag(lbm_ctx* c, lbm_diagnostics* out) {
+    if (!c) return arg_fail(nullptr, "ctx is NULL");
+    if (!out) return arg_fail(c, "out is NULL");
+    cudaError_t e = launch_diag(c->kp, c->p.model, c->p.storage, c->odd != 0, c->v,
+                                c->p.front_threshold, c->p.x0, (double)c->p.H, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "diag launch");
+    struct { DevDiag d; int flags[2]; } rec;
+    e = cudaMemcpyAsync(&rec, c->v.ddiag, sizeof rec, cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "diag copy");
+    e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "diag sync");
+    out->front = rec.d.front;
+    out->front_node = rec.d.front_node;
+    out->Fw = rec.d.Fw;
+    out->mass_delta = rec.d.mass_delta;
+    out->scalar_mass = rec.d.scalar_mass;
+    out->step = c->step;
+    out->flags = rec.flags[0];
+    out->pad_ = 0;
+    if (rec.flags[0]) {
+        snprintf(c->err, sizeof c->err, "sticky device flags 0x%x", rec.flags[0]);
+        return LBM_ERR_UNSTABLE;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_fw_accumulate(lbm_ctx* c, double* acc_dev, double weight) {
+    if (!c) return arg_fail(nullptr, "ctx is NULL");
+    if (!acc_dev) return arg_fail(c, "acc_dev is NULL");
+    if (!isfinite(weight)) return arg_fail(c, "weight must be finite");
+    cudaError_t e = launch_fw_accumulate(c->kp, c->p.model, c->p.storage, c->odd != 0, c->v,
+                                         acc_dev, weight, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "fw launch");
+    return LBM_OK;
+}
+
+lbm_status lbm_get_state(lbm_ctx* c, float* dst) {
+    if (!c) return arg_fail(nullptr, "ctx is NULL");
+    if (!dst) return arg_fail(c, "dst is NULL");
+    cudaError_t e = launch_get_state(c->kp, c->p.model, c->p.storage, c->odd != 0, c->v, dst,
+                                     c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "get_state launch");
+    return LBM_OK;
+}
+
+lbm_status lbm_set_state(lbm_ctx* c, const float* src, int64_t step) {
+    if (!c) return arg_fail(nullptr, "ctx is NULL");
+    if (!src) return arg_fail(c, "src is NULL");
+    if (step < 0) return arg_fail(c, "step must be >= 0");
+    cudaError_t e = launch_set_state(c->kp, c->p.model, c->p.storage, c->v, src, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "set_state launch");
+    c->step = step;
+    c->odd = 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_adjoint_step(lbm_ctx* c, const float* state_n, const float* lam_next, float* lam_n,
+                            double* dJdCs_dev, double w_fw) {
+    if (!c) return arg_fail(nullptr, "ctx is NULL");
+    if (c->p.model != LBM_BGK_SMAG_Q19) {
+        snprintf(c->err, sizeof c->err, "the adjoint exists for the BGK model only");
+        return LBM_ERR_STATE;
+    }
+    if (!state_n || !lam_n) return arg_fail(c, "state_n and lam_n must not be NULL");
+    if (lam_n == lam_next || lam_n == state_n) return arg_fail(c, "lam_n must not alias its inputs");
+    if (!isfinite(w_fw)) return arg_fail(c, "w_fw must be finite");
+    const float dAdCs = (float)(36.0 * sqrt(2.0) * c->p.cs_smag);
+    cudaError_t e = launch_adjoint_step(c->kp, state_n, lam_next, lam_n, dJdCs_dev, (float)w_fw,
+                                        dAdCs, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "adjoint launch");
+    return LBM_OK;
+}
+
+lbm_status lbm_adjoint_chi0(lbm_ctx* c, const float* lam0, float* grad_chi0) {
+    if (!c) return arg_fail(nullptr, "ctx is NULL");
+    if (!lam0 || !grad_chi0) return arg_fail(c, "lam0 and grad_chi0 must not be NULL");
+    if (c->p.model != LBM_BGK_SMAG_Q19) {
+        snprintf(c->err, sizeof c->err, "the adjoint exists for the BGK model only");
+        return LBM_ERR_STATE;
+    }
+    cudaError_t e = launch_adjoint_chi0(c->kp, lam0, grad_chi0, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "adjoint_chi0 launch");
+    return LBM_OK;
+}
+
+int64_t lbm_get_step(const lbm_ctx* c) { return c ? c->step : -1; }
+
+lbm_status lbm_sync(lbm_ctx* c) {
+    if (!c) return arg_fail(nullptr, "ctx is NULL");
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "sync");
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, "sync");
+    return LBM_OK;
+}
+
+void lbm_destroy(lbm_ctx* c) { free(c); }
+
+}  // extern "C"

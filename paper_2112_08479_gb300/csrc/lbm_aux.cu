@@ -1,0 +1,428 @@
+// lbm_aux.cu -- initial condition, macroscopic fields, state import/export,
+// diagnostics and the small adjoint helpers of the GB300 LBM library.
+//
+// Diagnostics (Sec. 3.1 and 3.2):
+//   chibar(x, z) = (1/ny) sum_y chi,  m(x) = max_z chibar(x, z),
+//   x_f = largest x with m(x) >= threshold, moved to the linear crossing
+//   between x_f and x_f + 1; front = (x_f + 1/2 - x0) / H;
+//   F_w = sum_{x,y} nu (9 u_x(x,y,0) - u_x(x,y,1)) / 3   (Eq. 62-64: the
+//   derivative at the wall z = -1/2 of the quadratic through u = 0 there and
+//   the first two nodes);
+//   budgets sum (rho - 1) and sum chi.
+// Column sums run in FP32 with Kahan compensation, block and grid sums of the
+// budgets in FP64, the friction in compensated FP32 pairs; every reduction
+// has a fixed order, so results are bitwise reproducible.
+#include <type_traits>
+
+#include "lbm_internal.h"
+
+namespace lbmgpu {
+
+template <typename S>
+__device__ __forceinline__ constexpr bool is16() { return !std::is_same<S, float>::value; }
+
+// rho - 1, u (with the half-force shift, Eq. 20) and chi at node n.
+template <int Q, bool ODD, typename S>
+__device__ __forceinline__ void node_macros(const KParams& kp, const S* __restrict__ f,
+                                            const S* __restrict__ phi, int x, int y, int z,
+                                            unsigned n, float& drho, float& ux, float& uy,
+                                            float& uz, float& chi) {
+    float fv[Q], pv[7];
+    gather<Q, ODD>(kp, f, x, y, z, n, fv);
+    gather<7, ODD>(kp, phi, x, y, z, n, pv);
+    float c = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) c += pv[k];
+    if (is16<S>()) c *= kp.isp;
+    float d = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        d += fv[i];
+        jx += cx27(i) * fv[i];
+        jy += cy27(i) * fv[i];
+        jz += cz27(i) * fv[i];
+    }
+    if (is16<S>()) { d *= kp.isf; jx *= kp.isf; jy *= kp.isf; jz *= kp.isf; }
+    const float irho = 1.0f / (1.0f + d);
+    drho = d;
+    chi = c;
+    ux = (jx + 0.5f * kp.gx * c) * irho;
+    uy = (jy + 0.5f * kp.gy * c) * irho;
+    uz = (jz + 0.5f * kp.gz * c) * irho;
+}
+
+// ---------------------------------------------------------------------------
+// Initial condition (Sec. 2.5, Table 1): f = w, Phi_k = w_k chi0, with chi0
+// either given or the lock field plus the gate-column perturbation drawn from
+// splitmix64(seed ^ n) (Steele, Lea & Flood 2014).
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long s) {
+    unsigned long long z = s + 0x9e3779b97f4a7c15ULL;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+
+template <int Q, typename S>
+__global__ void init_kernel(KParams kp, S* __restrict__ f, S* __restrict__ phi,
+                            const float* __restrict__ chi0, int x0, double amp,
+                            unsigned long long seed) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= kp.nx) return;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const unsigned n = (unsigned)x + (unsigned)kp.nx * ((unsigned)y + (unsigned)kp.ny * (unsigned)z);
+    const size_t N = kp.N;
+    float c;
+    if (chi0) {
+        c = chi0[n];
+    } else {
+        double v = x < x0 ? 1.0 : 0.0;
+        if (x == x0 - 1) {
+            const double r = (double)(splitmix64(seed ^ (unsigned long long)n) >> 11) * 0x1.0p-53;
+            v += amp * (2.0 * r - 1.0);
+        }
+        c = (float)v;
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) Store<S>::st(f + (size_t)i * N + n, 0.0f);
+#pragma unroll
+    for (int k = 0; k < 7; ++k) Store<S>::st(phi + (size_t)k * N + n, kp.sp * (w7(k) * c));
+}
+
+template <int Q, typename S>
+__global__ void fill_keys_kernel(unsigned* __restrict__ keys, int n, int* __restrict__ flags,
+                                 int reset_flags) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) keys[i] = 0x007fffffu;  // key of -inf
+    if (reset_flags && i == 0) *flags = 0;
+}
+
+// ---------------------------------------------------------------------------
+template <int Q, bool ODD, typename S>
+__global__ void macros_kernel(KParams kp, const S* __restrict__ f, const S* __restrict__ phi,
+                              float* __restrict__ rho, float* __restrict__ u,
+                              float* __restrict__ chi) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= kp.nx) return;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const unsigned n = (unsigned)x + (unsigned)kp.nx * ((unsigned)y + (unsigned)kp.ny * (unsigned)z);
+    float d, ux, uy, uz, c;
+    node_macros<Q, ODD>(kp, f, phi, x, y, z, n, d, ux, uy, uz, c);
+    const size_t N = kp.N;
+    if (rho) rho[n] = 1.0f + d;
+    if (u) { u[n] = ux; u[N + n] = uy; u[2 * N + n] = uz; }
+    if (chi) chi[n] = c;
+}
+
+template <int Q, bool ODD, typename S>
+__global__ void get_state_kernel(KParams kp, const S* __restrict__ f, const S* __restrict__ phi,
+                                 float* __restrict__ dst) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= kp.nx) return;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const unsigned n = (unsigned)x + (unsigned)kp.nx * ((unsigned)y + (unsigned)kp.ny * (unsigned)z);
+    float fv[Q], pv[7];
+    gather<Q, ODD>(kp, f, x, y, z, n, fv);
+    gather<7, ODD>(kp, phi, x, y, z, n, pv);
+    const size_t N = kp.N;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) dst[(size_t)i * N + n] = is16<S>() ? fv[i] * kp.isf : fv[i];
+#pragma unroll
+    for (int k = 0; k < 7; ++k) dst[(size_t)(Q + k) * N + n] = is16<S>() ? pv[k] * kp.isp : pv[k];
+}
+
+template <int Q, typename S>
+__global__ void set_state_kernel(KParams kp, S* __restrict__ f, S* __restrict__ phi,
+                                 const float* __restrict__ src) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= kp.nx) return;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const unsigned n = (unsigned)x + (unsigned)kp.nx * ((unsigned)y + (unsigned)kp.ny * (unsigned)z);
+    const size_t N = kp.N;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const float v = src[(size_t)i * N + n];
+        Store<S>::st(f + (size_t)i * N + n, is16<S>() ? v * kp.sf : v);
+    }
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+        const float v = src[(size_t)(Q + k) * N + n];
+        Store<S>::st(phi + (size_t)k * N + n, is16<S>() ? v * kp.sp : v);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Diagnostics.  One thread per column (x, z), looping over y.
+__device__ __forceinline__ unsigned fkey(float v) {
+    const unsigned b = __float_as_uint(v);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float fkey_inv(unsigned k) {
+    const unsigned b = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
+    return __uint_as_float(b);
+}
+
+// (s, c) + (t, d) with an error-free transformation of the leading parts
+__device__ __forceinline__ void pair_add(float& s, float& c, float t, float d) {
+    float r, e;
+    two_sum(s, t, r, e);
+    s = r;
+    c = c + d + e;
+}
+
+constexpr int DIAG_BX = 128;
+
+template <int Q, bool ODD, typename S>
+__global__ void __launch_bounds__(DIAG_BX) diag_columns_kernel(
+    KParams kp, const S* __restrict__ f, const S* __restrict__ phi, float* __restrict__ chibar,
+    unsigned* __restrict__ colmax, double* __restrict__ part, float* __restrict__ fwpart,
+    int* __restrict__ flags) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int z = blockIdx.y;
+    double m_rho = 0.0, m_chi = 0.0;
+    float fs = 0.0f, fc = 0.0f;
+    if (x < kp.nx) {
+        Kahan kc, kr, ku;
+        int bad = 0;
+        for (int y = 0; y < kp.ny; ++y) {
+            const unsigned n =
+                (unsigned)x + (unsigned)kp.nx * ((unsigned)y + (unsigned)kp.ny * (unsigned)z);
+            float d, ux, uy, uz, c;
+            node_macros<Q, ODD>(kp, f, phi, x, y, z, n, d, ux, uy, uz, c);
+            kc.add(c);
+            kr.add(d);
+            ku.add(ux);
+            if (!(1.0f + d > 0.0f)) bad |= LBM_DEVFLAG_RHO_NONPOS;
+            if (!isfinite(d) || !isfinite(ux) || !isfinite(uy) || !isfinite(uz) || !isfinite(c))
+                bad |= LBM_DEVFLAG_NONFINITE;
+        }
+        if (bad) atomicOr(flags, bad);
+        const float cb = (kc.s + kc.c) / (float)kp.ny;
+        chibar[(size_t)z * kp.nx + x] = cb;
+        atomicMax(colmax + x, fkey(cb));
+        m_rho = (double)kr.s + (double)kr.c;
+        m_chi = (double)kc.s + (double)kc.c;
+        if (kp.nz >= 2 && z < 2) {
+            const float a = z == 0 ? 3.0f * kp.nu : -kp.nu * (1.0f / 3.0f);
+            fs = a * ku.s;
+            fc = a * ku.c;
+        }
+    }
+    // block reductions: budgets in FP64, friction in compensated FP32 pairs
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        m_rho += __shfl_down_sync(0xffffffffu, m_rho, o);
+        m_chi += __shfl_down_sync(0xffffffffu, m_chi, o);
+        const float ts = __shfl_down_sync(0xffffffffu, fs, o);
+        const float tc = __shfl_down_sync(0xffffffffu, fc, o);
+        pair_add(fs, fc, ts, tc);
+    }
+    __shared__ double sr[DIAG_BX / 32], sc[DIAG_BX / 32];
+    __shared__ float ss[DIAG_BX / 32], se[DIAG_BX / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) { sr[wid] = m_rho; sc[wid] = m_chi; ss[wid] = fs; se[wid] = fc; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        float s = 0.0f, c = 0.0f;
+        for (int w = 0; w < DIAG_BX / 32; ++w) { a += sr[w]; b += sc[w]; pair_add(s, c, ss[w], se[w]); }
+        const unsigned blk = blockIdx.y * gridDim.x + blockIdx.x;
+        part[2 * blk] = a;
+        part[2 * blk + 1] = b;
+        fwpart[2 * blk] = s;
+        fwpart[2 * blk + 1] = c;
+    }
+}
+
+constexpr int FIN_T = 512;
+
+__global__ void __launch_bounds__(FIN_T) diag_finalize_kernel(
+    int nx, unsigned nblocks, const double* __restrict__ part, const float* __restrict__ fwpart,
+    unsigned* __restrict__ colmax, DevDiag* __restrict__ out, double thr, int x0, double H) {
+    __shared__ double sa[FIN_T], sb[FIN_T];
+    __shared__ float ss[FIN_T], sc[FIN_T];
+    __shared__ int sx[FIN_T];
+    const int t = threadIdx.x;
+    double a = 0.0, b = 0.0;
+    float s = 0.0f, c = 0.0f;
+    for (unsigned i = t; i < nblocks; i += FIN_T) {
+        a += part[2 * i];
+        b += part[2 * i + 1];
+        pair_add(s, c, fwpart[2 * i], fwpart[2 * i + 1]);
+    }
+    int xf = -1;
+    for (int x = t; x < nx; x += FIN_T)
+        if ((double)fkey_inv(colmax[x]) >= thr) xf = x;
+    sa[t] = a; sb[t] = b; ss[t] = s; sc[t] = c; sx[t] = xf;
+    __syncthreads();
+    for (int w = FIN_T / 2; w > 0; w >>= 1) {
+        if (t < w) {
+            sa[t] += sa[t + w];
+            sb[t] += sb[t + w];
+            float s0 = ss[t], c0 = sc[t];
+            pair_add(s0, c0, ss[t + w], sc[t + w]);
+            ss[t] = s0; sc[t] = c0;
+            sx[t] = max(sx[t], sx[t + w]);
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        const int x = sx[0];
+        double xn;
+        if (x < 0) xn = -1.0;
+        else if (x == nx - 1) xn = (double)x;
+        else {
+            const double m0 = fkey_inv(colmax[x]), m1 = fkey_inv(colmax[x + 1]);
+            xn = x + (m0 - thr) / (m0 - m1);
+        }
+        out->front_node = xn;
+        out->front = (xn + 0.5 - x0) / H;
+        out->Fw = (double)ss[0] + (double)sc[0];
+        out->mass_delta = sa[0];
+        out->scalar_mass = sb[0];
+    }
+    __syncthreads();
+    for (int x = t; x < nx; x += FIN_T) colmax[x] = 0x007fffffu;  // ready for the next call
+}
+
+// Adds weight * F_w to *acc.  One thread per (x, y) of the bottom rows.
+template <int Q, bool ODD, typename S>
+__global__ void __launch_bounds__(128) fw_kernel(KParams kp, const S* __restrict__ f,
+                                                 const S* __restrict__ phi, double* __restrict__ acc,
+                                                 double weight) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    double v = 0.0;
+    if (x < kp.nx) {
+        float d, ux0, ux1, uy, uz, c;
+        const unsigned n0 = (unsigned)x + (unsigned)kp.nx * (unsigned)y;
+        const unsigned n1 = n0 + kp.nxny;
+        node_macros<Q, ODD>(kp, f, phi, x, y, 0, n0, d, ux0, uy, uz, c);
+        node_macros<Q, ODD>(kp, f, phi, x, y, 1, n1, d, ux1, uy, uz, c);
+        v = (double)(kp.nu * (9.0f * ux0 - ux1) * (1.0f / 3.0f));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    __shared__ double red[4];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) atomicAdd(acc, weight * (red[0] + red[1] + red[2] + red[3]));
+}
+
+__global__ void adjoint_chi0_kernel(unsigned N, int Q, const float* __restrict__ lam,
+                                    float* __restrict__ grad) {
+    const unsigned n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    float g = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) g += w7(k) * lam[(size_t)(Q + k) * N + n];
+    grad[n] = g;
+}
+
+// ---------------------------------------------------------------------------
+// Launchers.
+static inline dim3 node_grid(const KParams& kp) { return dim3((kp.nx + 127) / 128, kp.ny, kp.nz); }
+
+unsigned diag_block_count(int nx, int nz) { return (unsigned)((nx + DIAG_BX - 1) / DIAG_BX) * nz; }
+
+// Calls fn.template operator()<Q, S>() for the model and storage at hand.
+template <typename Fn>
+static cudaError_t dispatch(int model, int storage, Fn&& fn) {
+    if (model == LBM_BGK_SMAG_Q19) {
+        if (storage == LBM_FP32) return fn.template operator()<19, float>();
+        if (storage == LBM_FP16S) return fn.template operator()<19, __half>();
+        if (storage == LBM_BF16S) return fn.template operator()<19, __nv_bfloat16>();
+    } else if (model == LBM_CUMULANT_Q27) {
+        if (storage == LBM_FP32) return fn.template operator()<27, float>();
+        if (storage == LBM_FP16S) return fn.template operator()<27, __half>();
+        if (storage == LBM_BF16S) return fn.template operator()<27, __nv_bfloat16>();
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_step(const KParams& kp, int model, int storage, bool odd, void* f, void* phi,
+                        float* save, cudaStream_t st) {
+    if (model == LBM_BGK_SMAG_Q19) return launch_bgk_step(kp, storage, odd, f, phi, save, st);
+    if (model == LBM_CUMULANT_Q27) return launch_cumulant_step(kp, storage, odd, f, phi, save, st);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_init(const KParams& kp, int model, int storage, const Views& v, const float* chi0,
+                        int x0, double amp, uint64_t seed, cudaStream_t st) {
+    return dispatch(model, storage, [&]<int Q, typename S>() {
+        init_kernel<Q, S><<<node_grid(kp), 128, 0, st>>>(kp, (S*)v.f, (S*)v.phi, chi0, x0, amp,
+                                                          (unsigned long long)seed);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        fill_keys_kernel<Q, S><<<(kp.nx + 255) / 256, 256, 0, st>>>(v.colmax, kp.nx, v.devflags, 1);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_macros(const KParams& kp, int model, int storage, bool odd, const Views& v,
+                          float* rho, float* u, float* chi, cudaStream_t st) {
+    return dispatch(model, storage, [&]<int Q, typename S>() {
+        if (odd)
+            macros_kernel<Q, true, S><<<node_grid(kp), 128, 0, st>>>(kp, (const S*)v.f, (const S*)v.phi, rho, u, chi);
+        else
+            macros_kernel<Q, false, S><<<node_grid(kp), 128, 0, st>>>(kp, (const S*)v.f, (const S*)v.phi, rho, u, chi);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_get_state(const KParams& kp, int model, int storage, bool odd, const Views& v,
+                             float* dst, cudaStream_t st) {
+    return dispatch(model, storage, [&]<int Q, typename S>() {
+        if (odd)
+            get_state_kernel<Q, true, S><<<node_grid(kp), 128, 0, st>>>(kp, (const S*)v.f, (const S*)v.phi, dst);
+        else
+            get_state_kernel<Q, false, S><<<node_grid(kp), 128, 0, st>>>(kp, (const S*)v.f, (const S*)v.phi, dst);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_set_state(const KParams& kp, int model, int storage, const Views& v,
+                             const float* src, cudaStream_t st) {
+    return dispatch(model, storage, [&]<int Q, typename S>() {
+        set_state_kernel<Q, S><<<node_grid(kp), 128, 0, st>>>(kp, (S*)v.f, (S*)v.phi, src);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_diag(const KParams& kp, int model, int storage, bool odd, const Views& v,
+                        double threshold, int x0, double H, cudaStream_t st) {
+    return dispatch(model, storage, [&]<int Q, typename S>() {
+        dim3 grid((kp.nx + DIAG_BX - 1) / DIAG_BX, kp.nz);
+        if (odd)
+            diag_columns_kernel<Q, true, S><<<grid, DIAG_BX, 0, st>>>(
+                kp, (const S*)v.f, (const S*)v.phi, v.chibar, v.colmax, v.part, v.fwpart, v.devflags);
+        else
+            diag_columns_kernel<Q, false, S><<<grid, DIAG_BX, 0, st>>>(
+                kp, (const S*)v.f, (const S*)v.phi, v.chibar, v.colmax, v.part, v.fwpart, v.devflags);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        diag_finalize_kernel<<<1, FIN_T, 0, st>>>(kp.nx, v.diag_blocks, v.part, v.fwpart, v.colmax,
+                                                  v.ddiag, threshold, x0, H);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_fw_accumulate(const KParams& kp, int model, int storage, bool odd,
+                                 const Views& v, double* acc, double weight, cudaStream_t st) {
+    if (kp.nz < 2) return cudaSuccess;
+    return dispatch(model, storage, [&]<int Q, typename S>() {
+        dim3 grid((kp.nx + 127) / 128, kp.ny);
+        if (odd)
+            fw_kernel<Q, true, S><<<grid, 128, 0, st>>>(kp, (const S*)v.f, (const S*)v.phi, acc, weight);
+        else
+            fw_kernel<Q, false, S><<<grid, 128, 0, st>>>(kp, (const S*)v.f, (const S*)v.phi, acc, weight);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_adjoint_chi0(const KParams& kp, const float* lam0, float* grad, cudaStream_t st) {
+    adjoint_chi0_kernel<<<(kp.N + 255) / 256, 256, 0, st>>>(kp.N, 19, lam0, grad);
+    return cudaGetLastError();
+}
+
+}  // namespace lbmgpu

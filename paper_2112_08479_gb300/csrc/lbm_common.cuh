@@ -1,0 +1,175 @@
+// lbm_common.cuh -- device-side building blocks shared by the kernels of the
+// GB300 lock-exchange LBM library: lattice constants, kernel parameters,
+// storage conversions and the AA-pattern gather / scatter.
+//
+// Lattices (Sec. 2.3.1): D3Q19 in the order of Eq. 23 with the weights of
+// Eq. 24; D3Q27 = D3Q19 followed by the eight corners in opposite pairs;
+// D3Q7 for the scalar (rest, +-x, +-y, +-z; weights 1/4 and 1/8, c_s^2 = 1/4).
+// In every set the direction opposite to i >= 1 is i + 1 for odd i and i - 1
+// for even i.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/lbm.h"
+
+namespace lbmgpu {
+
+// ---------------------------------------------------------------------------
+// Lattice constants (compile-time; folded after loop unrolling).
+
+__host__ __device__ constexpr int cx27(int i) {
+    constexpr int t[27] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0,
+                           1, -1, 1, -1, 1, -1, -1, 1};
+    return t[i];
+}
+__host__ __device__ constexpr int cy27(int i) {
+    constexpr int t[27] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1,
+                           1, -1, 1, -1, -1, 1, 1, -1};
+    return t[i];
+}
+__host__ __device__ constexpr int cz27(int i) {
+    constexpr int t[27] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1,
+                           1, -1, -1, 1, 1, -1, 1, -1};
+    return t[i];
+}
+// D3Q19 is the first 19 entries of the D3Q27 order.
+__host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+
+__host__ __device__ constexpr float w19(int i) {
+    return i == 0 ? 1.0f / 3.0f : (i <= 6 ? 1.0f / 18.0f : 1.0f / 36.0f);
+}
+__host__ __device__ constexpr float w27(int i) {
+    return i == 0 ? 8.0f / 27.0f : (i <= 6 ? 2.0f / 27.0f : (i <= 18 ? 1.0f / 54.0f : 1.0f / 216.0f));
+}
+template <int Q>
+__host__ __device__ constexpr float wq(int i) { return Q == 19 ? w19(i) : w27(i); }
+
+// D3Q7: first 7 entries of the same order.
+__host__ __device__ constexpr float w7(int k) { return k == 0 ? 0.25f : 0.125f; }
+
+// ---------------------------------------------------------------------------
+// Kernel parameters, derived once on the host from lbm_params.
+struct KParams {
+    int nx, ny, nz, flags;
+    unsigned N;          // nodes
+    unsigned nxny;
+    float tau0;          // 3 nu + 1/2                          (Eq. 25)
+    float A;             // 18 sqrt(2) C_s^2                    (Eq. 34, reading R3)
+    float taup0;         // 1/2 + 4 D                           (Eq. 30 on D3Q7)
+    float kT;            // 4 / (3 Sc_T): tau_Phi = taup0 + kT (tau - tau0) (Eq. 35)
+    float om1, om2;      // cumulant shear and bulk rates       (Eq. 58)
+    float gx, gy, gz;    // g' e^g                               (Eq. 11)
+    float sf, isf;       // storage scale of f - w and its inverse
+    float sp, isp;       // storage scale of Phi and its inverse
+    float nu;            // molecular viscosity (wall friction, Eq. 62)
+};
+
+// ---------------------------------------------------------------------------
+// Storage types: FP32, or FP16 / BF16 with round-to-nearest-even.
+template <typename S> struct Store;
+template <> struct Store<float> {
+    static __device__ __forceinline__ float ld(const float* p) { return *p; }
+    static __device__ __forceinline__ void st(float* p, float v) { *p = v; }
+};
+template <> struct Store<__half> {
+    static __device__ __forceinline__ float ld(const __half* p) { return __half2float(*p); }
+    static __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
+};
+template <> struct Store<__nv_bfloat16> {
+    static __device__ __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+    static __device__ __forceinline__ void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+};
+
+// ---------------------------------------------------------------------------
+// Neighbour of (x, y, z) displaced by (dx, dy, dz): y always periodic, x and
+// z bounded by half-way bounce-back walls unless the periodic flags are set.
+// Returns false when the neighbour lies beyond a wall.
+__device__ __forceinline__ bool neighbour(const KParams& kp, int x, int y, int z, int dx, int dy,
+                                          int dz, unsigned& idx) {
+    int xn = x + dx, yn = y + dy, zn = z + dz;
+    if (yn < 0) yn += kp.ny;
+    else if (yn >= kp.ny) yn -= kp.ny;
+    if (xn < 0 || xn >= kp.nx) {
+        if (!(kp.flags & LBM_FLAG_PERIODIC_X)) return false;
+        xn = xn < 0 ? xn + kp.nx : xn - kp.nx;
+    }
+    if (zn < 0 || zn >= kp.nz) {
+        if (!(kp.flags & LBM_FLAG_PERIODIC_Z)) return false;
+        zn = zn < 0 ? zn + kp.nz : zn - kp.nz;
+    }
+    idx = (unsigned)xn + (unsigned)kp.nx * ((unsigned)yn + (unsigned)kp.ny * (unsigned)zn);
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// AA pattern, in place on one array per population set (Q fluid, 7 scalar).
+//
+// Slot i of node n after an even number of steps holds f_i(n), the streamed
+// pre-collision value.  Even steps read slot i of node n and write f*_i to
+// slot opp(i) of node n.  Odd steps read f_i(n) = f*_i(n - c_i) from slot
+// opp(i) of node n - c_i and write f*_i to slot i of node n + c_i.  At a wall
+// the bounce-back partner is the node itself: an odd-step read of a
+// population whose upwind node is a wall takes slot i of node n (where the
+// even step put f*_opp(i)), and an odd-step write towards a wall goes to slot
+// opp(i) of node n.  Each location is read and then written by exactly one
+// thread in each step, so the update is race-free in place.
+
+template <int Q, bool ODD, typename S>
+__device__ __forceinline__ void gather(const KParams& kp, const S* __restrict__ a, int x, int y,
+                                       int z, unsigned n, float (&v)[Q]) {
+    const size_t N = kp.N;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        if (!ODD) {
+            v[i] = Store<S>::ld(a + (size_t)i * N + n);
+        } else {
+            unsigned s;
+            if (i != 0 && neighbour(kp, x, y, z, -cx27(i), -cy27(i), -cz27(i), s))
+                v[i] = Store<S>::ld(a + (size_t)opp(i) * N + s);
+            else
+                v[i] = Store<S>::ld(a + (size_t)i * N + n);
+        }
+    }
+}
+
+template <int Q, bool ODD, typename S>
+__device__ __forceinline__ void scatter(const KParams& kp, S* __restrict__ a, int x, int y, int z,
+                                        unsigned n, const float (&v)[Q]) {
+    const size_t N = kp.N;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        if (!ODD) {
+            Store<S>::st(a + (size_t)opp(i) * N + n, v[i]);
+        } else {
+            unsigned d;
+            if (i != 0 && neighbour(kp, x, y, z, cx27(i), cy27(i), cz27(i), d))
+                Store<S>::st(a + (size_t)i * N + d, v[i]);
+            else
+                Store<S>::st(a + (size_t)opp(i) * N + n, v[i]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Error-free transformation used by the compensated FP32 sums.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+struct Kahan {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float v) {
+        float t, e;
+        two_sum(s, v, t, e);
+        s = t;
+        c = __fadd_rn(c, e);
+    }
+};
+
+}  // namespace lbmgpu

@@ -1,0 +1,218 @@
+// lbm_cumulant.cu -- fused AA stream + collide kernel of the D3Q27 cumulant
+// fluid (Sec. 2.3.1 "VirtualFluids", Eq. 52-58) with the D3Q7 scalar and the
+// Boussinesq force.
+//
+// Cumulants C_abc are the derivatives of ln G, G(Xi) = sum_i f_i exp(Xi.c_i)
+// (Eq. 54).  The collision keeps rho (Eq. 56), moves the first-order
+// cumulants to u* = (j + F) / rho (Eq. 57 plus the body-force impulse),
+// relaxes the second-order ones with omega1 = 1/(3 nu + 1/2) (Eq. 58) on
+// the shear parts and omega_bulk on the trace (Eq. 55, C_eq = c_s^2 = 1/3
+// per axis), and relaxes every cumulant of order >= 3 with rate 1 to its
+// equilibrium 0.  Because all higher cumulants leave the collision as 0,
+// only the pre-collision moments of order <= 2 are needed, and the
+// post-collision distribution has the truncated moment generating function
+//   G* = rho exp(u*.Xi) exp(Xi^T Sigma* Xi / 2)   mod (Xi^3, Y^3, Z^3),
+// whose central moments are rho times the Gaussian moments of Sigma*
+// (Isserlis): kappa_220 = s_xx s_yy + 2 s_xy^2, kappa_211 = s_xx s_yz +
+// 2 s_xy s_xz, kappa_222 = s_xx s_yy s_zz + 2 (s_xx s_yz^2 + s_yy s_xz^2 +
+// s_zz s_xy^2) + 8 s_xy s_xz s_yz, odd orders 0.  The populations follow from
+// the per-axis inverse of the central-moment map in the frame u*, applied on
+// z, then y, then x.  Every quantity is carried as a deviation from the rest
+// state (rho = 1, u = 0, Sigma = I/3) so FP32 keeps its digits.
+#include <type_traits>
+
+#include "lbm_internal.h"
+
+namespace lbmgpu {
+
+// Per-axis inverse of the central-moment map, in deviation form.  A line
+// (k0, k1, k2) of central moments in the frame moving with v holds the rest
+// values s * (1, 0, 1/3) plus the deviations (d0, d1, d2); the populations at
+// c = -1, 0, +1 are the rest values s * (1/6, 2/3, 1/6) plus the returned
+// deviations:
+//   p(0)  = d0 - (s + d0) v^2 - 2 v d1 - d2
+//   p(+-) = ((v^2 +- v)(s + d0) + (2 v +- 1) d1 + d2) / 2
+__device__ __forceinline__ void axis_inverse(float s, float v, float d0, float d1, float d2,
+                                             float& pm, float& p0, float& pp) {
+    const float k0 = s + d0;
+    const float v2 = v * v;
+    p0 = d0 - k0 * v2 - 2.0f * v * d1 - d2;
+    const float a = v2 * k0 + 2.0f * v * d1 + d2;
+    const float b = v * k0 + d1;
+    pp = 0.5f * (a + b);
+    pm = 0.5f * (a - b);
+}
+
+// Index of the D3Q27 direction (cx, cy, cz) in the library order, looked up
+// by (cx + 1) * 9 + (cy + 1) * 3 + (cz + 1).
+__host__ __device__ constexpr int dir27(int x, int y, int z) {
+    constexpr int t[27] = {20, 8, 22, 12, 2, 14, 24, 10, 25, 16, 4, 18, 6, 0,
+                           5, 17, 3, 15, 26, 9, 23, 13, 1, 11, 21, 7, 19};
+    return t[(x + 1) * 9 + (y + 1) * 3 + (z + 1)];
+}
+
+__device__ __forceinline__ void collide_cumulant(const KParams& kp, float (&f)[27], float (&p)[7]) {
+    float chi = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) chi += p[k];
+    const float Fx = kp.gx * chi, Fy = kp.gy * chi, Fz = kp.gz * chi;
+
+    float drho = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
+    float mxx = 0.0f, myy = 0.0f, mzz = 0.0f, mxy = 0.0f, mxz = 0.0f, myz = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 27; ++i) {
+        const float v = f[i];
+        drho += v;
+        if (cx27(i)) { jx += cx27(i) * v; mxx += v; }
+        if (cy27(i)) { jy += cy27(i) * v; myy += v; }
+        if (cz27(i)) { jz += cz27(i) * v; mzz += v; }
+        if (cx27(i) * cy27(i)) mxy += cx27(i) * cy27(i) * v;
+        if (cx27(i) * cz27(i)) mxz += cx27(i) * cz27(i) * v;
+        if (cy27(i) * cz27(i)) myz += cy27(i) * cz27(i) * v;
+    }
+    const float rho = 1.0f + drho;
+    const float irho = 1.0f / rho;
+    // pre-collision mean velocity and second-order cumulants (deviation of
+    // the diagonal from 1/3): C_aa - 1/3 = (M_aa - drho/3)/rho - v_a^2
+    const float vx = jx * irho, vy = jy * irho, vz = jz * irho;
+    const float d3 = drho * (1.0f / 3.0f);
+    const float cxx = (mxx - d3) * irho - vx * vx;
+    const float cyy = (myy - d3) * irho - vy * vy;
+    const float czz = (mzz - d3) * irho - vz * vz;
+    const float cxy = mxy * irho - vx * vy;
+    const float cxz = mxz * irho - vx * vz;
+    const float cyz = myz * irho - vy * vz;
+    // relaxation (Eq. 55): shear with omega1, trace with omega_bulk
+    const float r1 = 1.0f - kp.om1, r2 = 1.0f - kp.om2;
+    const float D1 = r1 * (cxx - cyy), D2 = r1 * (cxx - czz), T = r2 * (cxx + cyy + czz);
+    const float sxx = (T + D1 + D2) * (1.0f / 3.0f);
+    const float syy = sxx - D1, szz = sxx - D2;
+    const float sxy = r1 * cxy, sxz = r1 * cxz, syz = r1 * cyz;
+    // post-collision velocity (first-order cumulants + body-force impulse)
+    const float ux = (jx + Fx) * irho, uy = (jy + Fy) * irho, uz = (jz + Fz) * irho;
+
+    // central-moment deviations K[a][b][c] (rho-normalised) of the Gaussian
+    // with covariance I/3 + s; entries of odd total order vanish
+    const float t3 = 1.0f / 3.0f;
+    const float sgx = t3 + sxx, sgy = t3 + syy, sgz = t3 + szz;
+    float K[3][3][3];
+#pragma unroll
+    for (int a = 0; a < 27; ++a) (&K[0][0][0])[a] = 0.0f;
+    K[2][0][0] = sxx; K[0][2][0] = syy; K[0][0][2] = szz;
+    K[1][1][0] = sxy; K[1][0][1] = sxz; K[0][1][1] = syz;
+    K[2][2][0] = (sxx + syy) * t3 + sxx * syy + 2.0f * sxy * sxy;
+    K[2][0][2] = (sxx + szz) * t3 + sxx * szz + 2.0f * sxz * sxz;
+    K[0][2][2] = (syy + szz) * t3 + syy * szz + 2.0f * syz * syz;
+    K[2][1][1] = sgx * syz + 2.0f * sxy * sxz;
+    K[1][2][1] = sgy * sxz + 2.0f * sxy * syz;
+    K[1][1][2] = sgz * sxy + 2.0f * sxz * syz;
+    K[2][2][2] = (sxx + syy + szz) * (1.0f / 9.0f) + (sxx * syy + sxx * szz + syy * szz) * t3 +
+                 sxx * syy * szz + 2.0f * (sgx * syz * syz + sgy * sxz * sxz + sgz * sxy * sxy) +
+                 8.0f * sxy * sxz * syz;
+
+    // rest value per moment order r = (1, 0, 1/3), per velocity w1 = (1/6, 2/3, 1/6)
+    // for c = -1, 0, +1 (index c + 1)
+    constexpr float R[3] = {1.0f, 0.0f, 1.0f / 3.0f};
+    constexpr float W1[3] = {1.0f / 6.0f, 2.0f / 3.0f, 1.0f / 6.0f};
+    float A[3][3][3];  // [a][b][cz + 1]
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+            axis_inverse(R[a] * R[b], uz, K[a][b][0], K[a][b][1], K[a][b][2], A[a][b][0],
+                         A[a][b][1], A[a][b][2]);
+    float B[3][3][3];  // [a][cy + 1][cz + 1]
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            axis_inverse(R[a] * W1[c], uy, A[a][0][c], A[a][1][c], A[a][2][c], B[a][0][c],
+                         B[a][1][c], B[a][2][c]);
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float pm, p0, pp;
+            axis_inverse(W1[b] * W1[c], ux, B[0][b][c], B[1][b][c], B[2][b][c], pm, p0, pp);
+            // f*_i - w_i = drho w_i + rho (P_i - w_i)
+            const int im = dir27(-1, b - 1, c - 1), i0 = dir27(0, b - 1, c - 1),
+                      ip = dir27(1, b - 1, c - 1);
+            f[im] = drho * w27(im) + rho * pm;
+            f[i0] = drho * w27(i0) + rho * p0;
+            f[ip] = drho * w27(ip) + rho * pp;
+        }
+
+    // scalar (Eq. 28-30) with the half-force velocity and the molecular D
+    const float hx = (jx + 0.5f * Fx) * irho, hy = (jy + 0.5f * Fy) * irho,
+                hz = (jz + 0.5f * Fz) * irho;
+    const float omp = 1.0f / kp.taup0;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+        const float cu = cx27(k) * hx + cy27(k) * hy + cz27(k) * hz;
+        const float peq = w7(k) * chi * (1.0f + 4.0f * cu);
+        p[k] = p[k] - omp * (p[k] - peq);
+    }
+}
+
+template <bool ODD, bool SAVE, typename S>
+__global__ void __launch_bounds__(128) cumulant_step_kernel(KParams kp, S* __restrict__ f,
+                                                            S* __restrict__ phi,
+                                                            float* __restrict__ save) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= kp.nx) return;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const unsigned n = (unsigned)x + (unsigned)kp.nx * ((unsigned)y + (unsigned)kp.ny * (unsigned)z);
+
+    float fv[27], pv[7];
+    gather<27, ODD>(kp, f, x, y, z, n, fv);
+    gather<7, ODD>(kp, phi, x, y, z, n, pv);
+    if (!std::is_same<S, float>::value) {
+#pragma unroll
+        for (int i = 0; i < 27; ++i) fv[i] *= kp.isf;
+#pragma unroll
+        for (int k = 0; k < 7; ++k) pv[k] *= kp.isp;
+    }
+    if (SAVE) {
+        const size_t N = kp.N;
+#pragma unroll
+        for (int i = 0; i < 27; ++i) save[(size_t)i * N + n] = fv[i];
+#pragma unroll
+        for (int k = 0; k < 7; ++k) save[(size_t)(27 + k) * N + n] = pv[k];
+    }
+    if (!(kp.flags & LBM_FLAG_NO_COLLIDE)) collide_cumulant(kp, fv, pv);
+    if (!std::is_same<S, float>::value) {
+#pragma unroll
+        for (int i = 0; i < 27; ++i) fv[i] *= kp.sf;
+#pragma unroll
+        for (int k = 0; k < 7; ++k) pv[k] *= kp.sp;
+    }
+    scatter<27, ODD>(kp, f, x, y, z, n, fv);
+    scatter<7, ODD>(kp, phi, x, y, z, n, pv);
+}
+
+template <typename S>
+static cudaError_t launch_cumulant_typed(const KParams& kp, bool odd, S* f, S* phi, float* save,
+                                        cudaStream_t st) {
+    dim3 block(128), grid((kp.nx + 127) / 128, kp.ny, kp.nz);
+    if (save) {
+        if (odd) cumulant_step_kernel<true, true, S><<<grid, block, 0, st>>>(kp, f, phi, save);
+        else cumulant_step_kernel<false, true, S><<<grid, block, 0, st>>>(kp, f, phi, save);
+    } else {
+        if (odd) cumulant_step_kernel<true, false, S><<<grid, block, 0, st>>>(kp, f, phi, nullptr);
+        else cumulant_step_kernel<false, false, S><<<grid, block, 0, st>>>(kp, f, phi, nullptr);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cumulant_step(const KParams& kp, int storage, bool odd, void* f, void* phi,
+                                 float* save, cudaStream_t st) {
+    switch (storage) {
+        case LBM_FP32: return launch_cumulant_typed(kp, odd, (float*)f, (float*)phi, save, st);
+        case LBM_FP16S: return launch_cumulant_typed(kp, odd, (__half*)f, (__half*)phi, save, st);
+        case LBM_BF16S:
+            return launch_cumulant_typed(kp, odd, (__nv_bfloat16*)f, (__nv_bfloat16*)phi, save, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace lbmgpu

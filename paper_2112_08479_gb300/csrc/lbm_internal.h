@@ -1,0 +1,58 @@
+// lbm_internal.h -- host-side launchers shared by the C-ABI layer and the
+// kernel translation units (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lbm_common.cuh"
+
+namespace lbmgpu {
+
+// Device-side diagnostics record written by the finalize kernel.
+struct DevDiag {
+    double front, front_node, Fw, mass_delta, scalar_mass;
+};
+
+// Workspace views handed to the launchers.
+struct Views {
+    void* f;              // Q * N storage elements
+    void* phi;            // 7 * N storage elements
+    float* stage;         // N floats: staging of a caller scalar field
+    float* chibar;        // nx * nz floats: span-averaged scalar
+    unsigned* colmax;     // nx order-preserving keys of max_z chibar
+    double* part;         // 2 doubles per diagnostics block
+    float* fwpart;        // 2 floats per diagnostics block
+    DevDiag* ddiag;       // one record
+    int* devflags;        // sticky device flags
+    unsigned diag_blocks; // number of diagnostics blocks
+};
+
+// Per-model step launchers (lbm_bgk.cu, lbm_cumulant.cu).
+cudaError_t launch_bgk_step(const KParams& kp, int storage, bool odd, void* f, void* phi,
+                            float* save, cudaStream_t st);
+cudaError_t launch_cumulant_step(const KParams& kp, int storage, bool odd, void* f, void* phi,
+                                 float* save, cudaStream_t st);
+
+// model: lbm_model; storage: lbm_storage; odd: parity of the AA step.
+cudaError_t launch_step(const KParams& kp, int model, int storage, bool odd, void* f, void* phi,
+                        float* save, cudaStream_t st);
+cudaError_t launch_init(const KParams& kp, int model, int storage, const Views& v, const float* chi0,
+                        int x0, double amp, uint64_t seed, cudaStream_t st);
+cudaError_t launch_macros(const KParams& kp, int model, int storage, bool odd, const Views& v,
+                          float* rho, float* u, float* chi, cudaStream_t st);
+cudaError_t launch_get_state(const KParams& kp, int model, int storage, bool odd, const Views& v,
+                             float* dst, cudaStream_t st);
+cudaError_t launch_set_state(const KParams& kp, int model, int storage, const Views& v,
+                             const float* src, cudaStream_t st);
+cudaError_t launch_diag(const KParams& kp, int model, int storage, bool odd, const Views& v,
+                        double threshold, int x0, double H, cudaStream_t st);
+cudaError_t launch_fw_accumulate(const KParams& kp, int model, int storage, bool odd,
+                                 const Views& v, double* acc, double weight, cudaStream_t st);
+cudaError_t launch_adjoint_step(const KParams& kp, const float* state, const float* lam_next,
+                                float* lam, double* dcs, float wfw, float dAdCs, cudaStream_t st);
+cudaError_t launch_adjoint_chi0(const KParams& kp, const float* lam0, float* grad, cudaStream_t st);
+
+unsigned diag_block_count(int nx, int nz);
+
+}  // namespace lbmgpu

@@ -1,0 +1,86 @@
+"""Shared test helpers: parameter mapping between the library and the oracle,
+conversion between the library's canonical state layout ([Q+7][nz][ny][nx],
+f - w and Phi) and the oracle's node-major arrays, and a light-cone window
+that lets the oracle reproduce single nodes of a full-size run."""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle as O
+from paper_2112_08479_gb300 import lbm
+
+
+def oracle_params(p: lbm.Params, **kw) -> O.OracleParams:
+    op = O.OracleParams(p.nx, p.ny, p.nz, model=p.model, nu=p.nu, D=p.D, cs_smag=p.cs_smag,
+                        sc_t=p.sc_t, gprime=p.gprime, eg=tuple(p.eg), omega_bulk=p.omega_bulk,
+                        omega_high=1.0,
+                        periodic_x=bool(p.flags & lbm.LBM_FLAG_PERIODIC_X),
+                        periodic_z=bool(p.flags & lbm.LBM_FLAG_PERIODIC_Z),
+                        no_collide=bool(p.flags & lbm.LBM_FLAG_NO_COLLIDE))
+    for k, v in kw.items():
+        setattr(op, k, v)
+    return op
+
+
+def weights(model: int) -> np.ndarray:
+    return O.velocities(model)[1]
+
+
+def canonical_to_oracle(state: np.ndarray, p: lbm.Params, shifted: bool = True):
+    """[Q+7, N] float32 (f - w, Phi) -> oracle (f, phi) float64 arrays."""
+    Q = p.Q
+    s = np.asarray(state, dtype=np.float64).reshape(Q + 7, *p.shape)
+    f = np.moveaxis(s[:Q], 0, -1).copy()
+    phi = np.moveaxis(s[Q:], 0, -1).copy()
+    if shifted:
+        f += weights(p.model)
+    return f, phi
+
+
+def oracle_to_canonical(f: np.ndarray, phi: np.ndarray, p: lbm.Params, shifted: bool = True):
+    """oracle (f, phi) -> [Q+7, N] float64 in the library layout."""
+    ff = f - weights(p.model) if shifted else f
+    return np.concatenate([np.moveaxis(ff, -1, 0), np.moveaxis(phi, -1, 0)]).reshape(p.Q + 7, -1)
+
+
+def lock_state_oracle(p: lbm.Params):
+    op = oracle_params(p)
+    chi0 = O.lock_chi0(p.nx, p.ny, p.nz, p.x0, p.noise_amp, p.seed)
+    return op, O.init(op, chi0)
+
+
+def rel_inf(a, b) -> float:
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    den = np.abs(b).max()
+    return float(np.abs(a - b).max() / den) if den > 0 else float(np.abs(a - b).max())
+
+
+def window_oracle(p: lbm.Params, state0: np.ndarray, node, steps: int):
+    """Oracle value of every population at `node` after `steps` steps of a
+    full-size run, from a (2 steps + 1)-wide window of the initial canonical
+    state `state0` ([Q+7, nz, ny, nx] float32, host).  Window edges inside the
+    domain are given walls (x, z) or a wrap (y); their wrong values travel one
+    node per step and do not reach the centre within `steps` steps."""
+    Q = p.Q
+    x, y, z = node
+    k = steps
+    xs = np.arange(max(0, x - k), min(p.nx, x + k + 1))
+    zs = np.arange(max(0, z - k), min(p.nz, z + k + 1))
+    if p.ny >= 2 * k + 1:
+        ys = (np.arange(y - k, y + k + 1)) % p.ny
+        cy = k
+    else:
+        ys = np.arange(p.ny)
+        cy = y
+    sub = state0[:, zs][:, :, ys][:, :, :, xs].astype(np.float64)
+    f = np.moveaxis(sub[:Q], 0, -1) + weights(p.model)
+    phi = np.moveaxis(sub[Q:], 0, -1).copy()
+    op = oracle_params(p)
+    op.nx, op.ny, op.nz = len(xs), len(ys), len(zs)
+    op.periodic_x = False
+    op.periodic_z = False
+    f, phi = O.run(op, steps, f, phi)
+    cx = int(np.where(xs == x)[0][0])
+    cz = int(np.where(zs == z)[0][0])
+    return f[cz, cy, cx] - weights(p.model), phi[cz, cy, cx]

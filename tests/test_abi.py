@@ -1,0 +1,120 @@
+"""The C ABI boundary without a GPU: the library loads, exports every entry
+point that include/lbm.h declares, the Python binding declares the same set,
+the ctypes structures match the C layouts, and argument checking (which runs
+on the host before anything is enqueued) rejects bad parameters."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_2112_08479_gb300 import _build
+from paper_2112_08479_gb300 import lbm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lbm.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return lbm.load()
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbm_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_symbols_exported(lib):
+    names = _declared()
+    assert len(names) >= 18
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(n for n, _, _ in lbm.SIGNATURES) == names
+
+
+def test_struct_layouts():
+    # sizes computed from the C declarations with natural alignment
+    assert C.sizeof(lbm.lbm_params) == 6 * 4 + 5 * 8 + 3 * 8 + 8 + 2 * 4 + 8 + 8 + 3 * 8
+    assert C.sizeof(lbm.lbm_diagnostics) == 5 * 8 + 8 + 4 + 4
+
+
+def _good(**kw):
+    p = lbm.Params(nx=16, ny=4, nz=8, x0=4, H=8, gprime=1e-4)
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p.c()
+
+
+def test_validate_accepts_defaults(lib):
+    assert lbm.lbm_validate(_good()) == lbm.LBM_OK
+    assert lbm.lbm_workspace_bytes(_good()) > (19 + 7) * 16 * 4 * 8 * 4
+
+
+@pytest.mark.parametrize("field,value", [
+    ("nx", 0), ("ny", 70000), ("nz", -1), ("model", 5), ("storage", 9), ("flags", 64),
+    ("nu", 0.0), ("nu", float("nan")), ("D", -1.0), ("cs_smag", -0.1), ("sc_t", 0.0),
+    ("gprime", float("inf")), ("x0", 17), ("x0", -1), ("H", 0), ("noise_amp", -1.0),
+    ("scale_f", 0.0), ("front_threshold", float("nan")),
+])
+def test_validate_rejects(lib, field, value):
+    p = _good(**{field: value})
+    assert lbm.lbm_validate(p) == lbm.LBM_ERR_ARG
+    assert lbm.lbm_workspace_bytes(p) == 0
+
+
+def test_cumulant_bulk_rate_range(lib):
+    assert lbm.lbm_validate(_good(model=lbm.LBM_CUMULANT_Q27, omega_bulk=2.5)) == lbm.LBM_ERR_ARG
+    assert lbm.lbm_validate(_good(model=lbm.LBM_CUMULANT_Q27, omega_bulk=1.0)) == lbm.LBM_OK
+
+
+def test_too_many_nodes(lib):
+    assert lbm.lbm_validate(_good(nx=65536, ny=1024, nz=32)) == lbm.LBM_ERR_ARG
+
+
+def test_workspace_scales_with_storage(lib):
+    b32 = lbm.lbm_workspace_bytes(_good(nx=256, ny=32, nz=64))
+    b16 = lbm.lbm_workspace_bytes(_good(nx=256, ny=32, nz=64, storage=lbm.LBM_FP16S))
+    N = 256 * 32 * 64
+    assert b32 - b16 == pytest.approx(26 * N * 2, abs=4096)
+
+
+def test_init_checks_before_touching_the_device(lib):
+    # invalid parameters, null workspace, small workspace and misalignment are
+    # all rejected on the host, so no device is needed
+    with pytest.raises(lbm.LBMError) as e:
+        lbm.lbm_init(_good(nu=-1.0), 256, 1 << 20, 0)
+    assert e.value.status == lbm.LBM_ERR_ARG
+    with pytest.raises(lbm.LBMError) as e:
+        lbm.lbm_init(_good(), 0, 1 << 20, 0)
+    assert e.value.status == lbm.LBM_ERR_ARG
+    with pytest.raises(lbm.LBMError) as e:
+        lbm.lbm_init(_good(), 4096 + 8, 1 << 30, 0)
+    assert e.value.status == lbm.LBM_ERR_ARG
+    with pytest.raises(lbm.LBMError) as e:
+        lbm.lbm_init(_good(), 4096, 1024, 0)
+    assert e.value.status == lbm.LBM_ERR_NOMEM
+
+
+def test_status_strings(lib):
+    for s in range(7):
+        assert lbm.lbm_status_string(s)
+    assert lbm.lbm_status_string(99) == "unknown status"
+
+
+def test_null_context_is_rejected(lib):
+    assert lib.lbm_step(None, 1) == lbm.LBM_ERR_ARG
+    assert lib.lbm_sync(None) == lbm.LBM_ERR_ARG
+    assert lib.lbm_get_step(None) == -1
+    lib.lbm_destroy(None)
+
+
+def test_lock_exchange_parameters():
+    """Sec. 2.5 / Eq. 12-14 in lattice units: u_b = sqrt(g' H), nu = u_b H / Re."""
+    p = lbm.lock_exchange(2048, 128, 256, H=256, x0=256, u_b=0.03, Re=30000.0)
+    assert p.gprime == pytest.approx(0.03**2 / 256)
+    assert p.nu == pytest.approx(2.56e-4)
+    assert p.D == p.nu
+    assert 3 * p.nu + 0.5 == pytest.approx(0.500768)

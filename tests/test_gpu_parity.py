@@ -1,0 +1,221 @@
+"""GPU parity: the CUDA kernels, called through the C ABI, against the FP64 oracle.
+
+Bars (stated per test): bit-exact for the streaming permutation; for FP32
+macros 1e-5 relative after one step and 1e-3 after 1000 steps (per field,
+||a - b||_inf / ||b||_inf for u and chi, absolute for rho); derived rounding
+bounds for the 16-bit storage forms.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2112_08479_gb300 import inputs
+from paper_2112_08479_gb300 import lbm
+
+from helpers import (canonical_to_oracle, lock_state_oracle, oracle_params, oracle_to_canonical,
+                     rel_inf, weights)
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _lat(p):
+    return lbm.Lattice(p, device="cuda")
+
+
+def _random_state(p: lbm.Params, seed: int, amp: float = 0.05, chi_amp: float = 1.0):
+    """Near-equilibrium canonical state: f - w = w amp U(-1,1), Phi = w_k chi, chi in [0, chi_amp]."""
+    w = weights(p.model)
+    fdev = w[:, None] * inputs.uniform((p.Q, p.N), seed, amp)
+    chi = chi_amp * 0.5 * (1.0 + inputs.uniform(p.N, seed + 1, 1.0))
+    w7 = O.velocities_q7()[1]
+    phi = w7[:, None] * chi[None, :] * (1.0 + inputs.uniform((7, p.N), seed + 2, amp))
+    return np.concatenate([fdev, phi]).astype(np.float32)
+
+
+def _to_dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("model", [0, 1])
+@pytest.mark.parametrize("shape", [(5, 3, 4), (7, 4, 6), (130, 2, 3)])
+@pytest.mark.parametrize("flags", [0, lbm.LBM_FLAG_PERIODIC_X, lbm.LBM_FLAG_PERIODIC_Z])
+def test_streaming_permutation_bit_exact(model, shape, flags):
+    """Collision off: after n steps (even and odd AA parities) the GPU state is
+    exactly the oracle's pull-streamed permutation of the same FP32 values."""
+    nx, ny, nz = shape
+    p = lbm.Params(nx, ny, nz, model=model, flags=lbm.LBM_FLAG_NO_COLLIDE | flags, x0=1, H=nz)
+    lat = _lat(p)
+    s0 = inputs.distinct_values((p.Q + 7, p.N), 7).astype(np.float32)
+    lat.set_state(_to_dev(s0))
+    op = oracle_params(p)
+    f, phi = canonical_to_oracle(s0, p, shifted=False)
+    for n in range(1, 6):
+        lat.step(1)
+        f, phi = O.step(op, f, phi)
+        got = lat.get_state().cpu().numpy()
+        want = oracle_to_canonical(f, phi, p, shifted=False).astype(np.float32)
+        assert np.array_equal(got, want), f"step {n}"
+
+
+def test_streaming_conserves_sums_exactly():
+    p = lbm.Params(9, 5, 7, flags=lbm.LBM_FLAG_NO_COLLIDE, x0=1, H=7)
+    lat = _lat(p)
+    s0 = inputs.distinct_values((26, p.N), 3).astype(np.float32)
+    lat.set_state(_to_dev(s0))
+    lat.step(7)
+    got = lat.get_state().cpu().numpy()
+    assert np.array_equal(np.sort(got, axis=None), np.sort(s0, axis=None))
+
+
+# ---------------------------------------------------------------------------
+def _config1(model="bgk", **kw):
+    # 128 x 8 x 16 lock-exchange box: H = 16, x0 = 16, u_b = 0.05, Re = 1000, Sc = 1
+    return lbm.lock_exchange(128, 8, 16, H=16, x0=16, u_b=0.05, Re=1000.0, model=model, **kw)
+
+
+def _compare_macros(lat, op, f, phi):
+    rho, u, chi = (t.cpu().numpy() for t in lat.macros())
+    rho_o, u_o, chi_o = O.macros(op, f, phi)
+    return (np.abs(rho - rho_o).max(), rel_inf(np.moveaxis(u, 0, -1), u_o), rel_inf(chi, chi_o))
+
+
+@pytest.mark.parametrize("model", ["bgk", "cumulant"])
+def test_lock_exchange_one_step(model):
+    p = _config1(model)
+    lat = _lat(p)
+    op, (f, phi) = lock_state_oracle(p)
+    # the initial condition itself
+    e_rho, e_u, e_chi = _compare_macros(lat, op, f, phi)
+    assert e_rho == 0 and e_chi < 1e-7
+    lat.step(1)
+    f, phi = O.step(op, f, phi)
+    e_rho, e_u, e_chi = _compare_macros(lat, op, f, phi)
+    assert e_rho < 1e-5 and e_u < 1e-5 and e_chi < 1e-5, (e_rho, e_u, e_chi)
+
+
+@pytest.mark.parametrize("model,steps", [("bgk", 1000), ("cumulant", 400)])
+def test_lock_exchange_long_run(model, steps):
+    p = _config1(model)
+    lat = _lat(p)
+    op, (f, phi) = lock_state_oracle(p)
+    lat.step(steps)
+    f, phi = O.run(op, steps, f, phi)
+    e_rho, e_u, e_chi = _compare_macros(lat, op, f, phi)
+    assert e_rho < 1e-3 and e_u < 1e-3 and e_chi < 1e-3, (e_rho, e_u, e_chi)
+    d = lat.diag()
+    do = O.diag(op, f, phi, p.x0, float(p.H))
+    assert abs(d["front"] - do["front"]) < 1e-3 * max(1.0, abs(do["front"]))
+    assert abs(d["Fw"] - do["Fw"]) < 1e-3 * abs(do["Fw"])
+    assert d["scalar_mass"] == pytest.approx(do["scalar_mass"], rel=1e-5)
+    assert abs(d["mass_delta"] - do["mass_delta"]) < 1e-6 * p.N
+    assert d["step"] == steps and d["flags"] == 0
+
+
+@pytest.mark.parametrize("model", [0, 1])
+@pytest.mark.parametrize("shape", [(33, 5, 6), (130, 3, 2), (17, 1, 1)])
+def test_random_state_two_steps(model, shape):
+    """Random near-equilibrium state with an oblique force: one even and one odd
+    step, whole state compared population by population."""
+    nx, ny, nz = shape
+    p = lbm.Params(nx, ny, nz, model=model, nu=0.01, D=0.012, cs_smag=0.3, sc_t=0.7,
+                   gprime=2e-3, eg=(0.48, 0.6, -0.64), omega_bulk=0.8, x0=1, H=nz)
+    lat = _lat(p)
+    s0 = _random_state(p, 11)
+    lat.set_state(_to_dev(s0))
+    op = oracle_params(p)
+    f, phi = canonical_to_oracle(s0, p)
+    scale = np.abs(s0[: p.Q]).max()
+    for n in (1, 2):
+        lat.step(1)
+        f, phi = O.step(op, f, phi)
+        got = lat.get_state().cpu().numpy().astype(np.float64)
+        want = oracle_to_canonical(f, phi, p)
+        assert np.abs(got[: p.Q] - want[: p.Q]).max() < 2e-6 * scale, n
+        assert np.abs(got[p.Q:] - want[p.Q:]).max() < 2e-7, n
+
+
+@pytest.mark.parametrize("model", [0, 1])
+@pytest.mark.parametrize("flags", [lbm.LBM_FLAG_PERIODIC_X, lbm.LBM_FLAG_PERIODIC_Z,
+                                   lbm.LBM_FLAG_PERIODIC_X | lbm.LBM_FLAG_PERIODIC_Z])
+def test_periodic_variants(model, flags):
+    p = lbm.Params(24, 4, 10, model=model, flags=flags, nu=0.005, D=0.005, gprime=1e-3,
+                   x0=8, H=10)
+    lat = _lat(p)
+    op, (f, phi) = lock_state_oracle(p)
+    lat.step(30)
+    f, phi = O.run(op, 30, f, phi)
+    e_rho, e_u, e_chi = _compare_macros(lat, op, f, phi)
+    assert e_rho < 1e-5 and e_u < 1e-4 and e_chi < 1e-5, (e_rho, e_u, e_chi)
+
+
+@pytest.mark.parametrize("x0", [0, 1, 40])
+def test_lock_edges(x0):
+    """No lock, a one-column lock, and the whole box as lock."""
+    p = lbm.Params(40, 3, 5, nu=0.01, D=0.01, gprime=1e-3, x0=x0, H=5)
+    lat = _lat(p)
+    op, (f, phi) = lock_state_oracle(p)
+    lat.step(12)
+    f, phi = O.run(op, 12, f, phi)
+    e_rho, e_u, e_chi = _compare_macros(lat, op, f, phi)
+    assert e_rho < 1e-5 and e_chi < 1e-5 and (e_u < 1e-4 or np.abs(O.macros(op, f, phi)[1]).max() < 1e-9)
+    d = lat.diag()
+    do = O.diag(op, f, phi, p.x0, float(p.H))
+    assert d["front_node"] == pytest.approx(do["front_node"], abs=1e-4)
+
+
+def test_set_scalar_host_and_device():
+    p = _config1()
+    chi0 = O.lock_chi0(p.nx, p.ny, p.nz, p.x0, p.noise_amp, p.seed).astype(np.float32).ravel()
+    a = _lat(p)
+    b = _lat(p)
+    b.set_scalar(torch.from_numpy(chi0))                 # pageable host memory
+    c = _lat(p)
+    c.set_scalar(torch.from_numpy(chi0).pin_memory())    # pinned host memory
+    d = _lat(p)
+    d.set_scalar(torch.from_numpy(chi0).cuda())          # device memory
+    for lat in (a, b, c, d):
+        lat.step(3)
+    sa = a.get_state()
+    for lat in (b, c, d):
+        assert torch.equal(lat.get_state(), sa)
+
+
+def test_state_round_trip_fp32():
+    p = lbm.Params(19, 3, 4, x0=1, H=4)
+    lat = _lat(p)
+    s0 = _random_state(p, 5)
+    lat.set_state(_to_dev(s0), step=42)
+    assert lat.step_count == 42
+    assert np.array_equal(lat.get_state().cpu().numpy(), s0)
+
+
+def test_unstable_flag_is_sticky_and_reset_by_init():
+    """A non-finite value planted in the state raises the sticky flag at the
+    next diagnostics; re-initialising clears it.  No device fault involved."""
+    p = lbm.Params(12, 3, 4, nu=0.01, D=0.01, x0=4, H=4)
+    lat = _lat(p)
+    s0 = _random_state(p, 9)
+    s0[3, 17] = np.nan
+    lat.set_state(_to_dev(s0))
+    lat.step(2)
+    with pytest.raises(lbm.LBMError) as e:
+        lat.diag()
+    assert e.value.status == lbm.LBM_ERR_UNSTABLE
+    d = lat.diag(raise_unstable=False)
+    assert d["flags"] & lbm.LBM_DEVFLAG_NONFINITE
+    lat.set_scalar(torch.zeros(p.N, dtype=torch.float32, device="cuda"))
+    assert lat.diag()["flags"] == 0
+
+
+def test_fw_accumulate_matches_diag():
+    p = _config1()
+    lat = _lat(p)
+    lat.step(150)
+    acc = torch.zeros(1, dtype=torch.float64, device="cuda")
+    lat.fw_accumulate(acc, 1.0)
+    lat.fw_accumulate(acc, 2.0)
+    d = lat.diag()
+    assert acc.item() == pytest.approx(3.0 * d["Fw"], rel=1e-5)

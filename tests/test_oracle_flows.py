@@ -296,6 +296,8 @@ def test_front_on_synthetic_fields():
     ramp = np.broadcast_to(np.linspace(1.0, 0.0, nx)[None, None, :], (nz, ny, nx)).copy()
     xc = (1.0 - 0.02) * (nx - 1)            # exact crossing of a linear ramp
     assert O.front_node(ramp, 0.02) == pytest.approx(xc, abs=1e-12)
+    tail = np.broadcast_to((0.1 - 0.0095 * np.arange(nx))[None, None, :], (nz, ny, nx)).copy()
+    assert O.front_node(tail, 0.02) == pytest.approx(8 + 0.004 / 0.0095, abs=1e-12)
     assert O.front_node(np.zeros((nz, ny, nx)), 0.02) == -1.0
     full = np.ones((nz, ny, nx))
     assert O.front_node(full, 0.02) == nx - 1

@@ -30,7 +30,13 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 INNER = 100                     # time steps per bench step
-WORKLOAD = dict(nx=2048, ny=128, nz=256, H=256, x0=256, u_b=0.03, Re=30000.0)
+WORKLOADS = {
+    # the 67 M-node box the headline number is quoted on
+    "config3": dict(nx=2048, ny=128, nz=256, H=256, x0=256, u_b=0.03, Re=30000.0),
+    # a 4.2 M-node box (436 MB in FP32, larger than L2) for profiler captures
+    "profile": dict(nx=512, ny=128, nz=64, H=64, x0=64, u_b=0.03, Re=30000.0 / 4),
+}
+WORKLOAD = dict(WORKLOADS["config3"])
 BYTES_PER_NODE = {("bgk", "fp32"): 208, ("cumulant", "fp32"): 272,
                   ("bgk", "fp16s"): 104, ("bgk", "bf16s"): 104,
                   ("cumulant", "fp16s"): 136, ("cumulant", "bf16s"): 136}
@@ -208,12 +214,14 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
-def config_dict(ws):
-    return {"workload": "lock-exchange 2048x128x256, D3Q19 BGK-Smagorinsky + D3Q7 scalar, "
-                        "FP32, Re=30000, 100 steps + diagnostics per bench step",
+def config_dict(ws, model="bgk", storage="fp32"):
+    fluid = "D3Q19 BGK-Smagorinsky" if model == "bgk" else "D3Q27 cumulant"
+    return {"workload": f"lock-exchange {WORKLOAD['nx']}x{WORKLOAD['ny']}x{WORKLOAD['nz']}, "
+                        f"{fluid} + D3Q7 scalar, {storage.upper()} storage, Re={WORKLOAD['Re']:g}, "
+                        "100 steps + diagnostics per bench step",
             "nodes": WORKLOAD["nx"] * WORKLOAD["ny"] * WORKLOAD["nz"],
             "steps_per_bench_step": INNER, "parallelism": f"replicas x{ws}",
-            "l2": "inputs larger than L2 (7.0 GB state), no flush"}
+            "l2": "inputs larger than L2 (state >= 436 MB), no flush"}
 
 
 # ---------------------------------------------------------------------------
@@ -310,7 +318,7 @@ def run_ours(args, ws, rank, local):
     torch.cuda.set_device(local)
     sampler = ClockSampler(torch.cuda.current_device() if ws == 1 else local)
 
-    lat = make_lattice()
+    lat = make_lattice(args.model, args.storage)
     N = lat.N
     barrier(ws)
     torch.cuda.synchronize()
@@ -328,6 +336,7 @@ def run_ours(args, ws, rank, local):
     chi0 = torch.from_numpy(
         np.where(np.arange(WORKLOAD["nx"]) < WORKLOAD["x0"], 1.0, 0.0).astype(np.float32)
     ).repeat(WORKLOAD["ny"] * WORKLOAD["nz"]).pin_memory()
+    assert chi0.numel() == N
     s = lat.stream
     for _ in range(max(1, args.warmup)):
         lat.set_scalar(chi0)
@@ -350,15 +359,17 @@ def run_ours(args, ws, rank, local):
     torch.cuda.empty_cache()
 
     peak, peak_kind = measured_peak_hbm()
-    achieved = BYTES_PER_NODE[("bgk", "fp32")] * N / kern / 1e9
-    roof = {"bound": "hbm", "kernel": "bgk_step_kernel (AA even/odd, FP32)",
+    bpn = BYTES_PER_NODE[(args.model, args.storage)]
+    achieved = bpn * N / kern / 1e9
+    headline = (args.model, args.storage) == ("bgk", "fp32") and args.workload == "config3"
+    roof = {"bound": "hbm",
+            "kernel": f"{args.model}_step_kernel (AA even/odd, {args.storage.upper()})",
             "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": profiled_traffic(N),
-            "algorithmic_bytes_per_launch": BYTES_PER_NODE[("bgk", "fp32")] * N,
-            "mean_launch_ms": kern * 1e3}
+            "frac": achieved / peak, "traffic": profiled_traffic(N) if headline else None,
+            "algorithmic_bytes_per_launch": bpn * N, "mean_launch_ms": kern * 1e3}
 
     extra = {}
-    if rank == 0 and ws == 1 and not args.no_side:
+    if rank == 0 and ws == 1 and not args.no_side and args.workload == "config3":
         variants = {}
         for model, storage in (("bgk", "fp16s"), ("bgk", "bf16s"), ("cumulant", "fp32"),
                                ("cumulant", "fp16s")):
@@ -377,7 +388,8 @@ def run_ours(args, ws, rank, local):
                 "warmup": args.warmup, "ms_per_step": tmax / args.steps * 1e3,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32", "data": "synthetic (lock-exchange initial condition)",
-                "config": config_dict(ws), "e2e": e2e, "gpu_launches": launches,
+                "config": config_dict(ws, args.model, args.storage), "e2e": e2e,
+                "gpu_launches": launches,
                 "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
                 "diag_at_end": {"front": d["front"], "Fw": d["Fw"], "step": d["step"]}}
         line.update(extra)
@@ -392,7 +404,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-side", action="store_true", help="skip the side measurements")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle timing")
+    ap.add_argument("--workload", default="config3", choices=sorted(WORKLOADS))
+    ap.add_argument("--model", default="bgk", choices=["bgk", "cumulant"])
+    ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16s", "bf16s"])
     args = ap.parse_args()
+    WORKLOAD.clear()
+    WORKLOAD.update(WORKLOADS[args.workload])
     ws, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, ws, rank)

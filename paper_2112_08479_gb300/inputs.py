@@ -36,3 +36,13 @@ def distinct_values(shape, seed: int) -> np.ndarray:
     rng = np.random.default_rng(seed)
     k = rng.permutation(n).astype(np.float64)
     return ((k + 1.0) / (n + 2.0) * 2.0 - 1.0).astype(np.float32).astype(np.float64).reshape(shape)
+
+
+def torch_uniform(shape, seed: int, scale: float = 1.0, device="cuda"):
+    """Uniform(-scale, scale) float32 tensor drawn on `device` by a seeded
+    torch generator (for inputs too large to draw on the host)."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    t = torch.rand(shape, generator=g, device=device, dtype=torch.float32)
+    return t.mul_(2.0 * scale).sub_(scale)

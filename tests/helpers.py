@@ -59,7 +59,7 @@ def rel_inf(a, b) -> float:
 def window_oracle(p: lbm.Params, state0: np.ndarray, node, steps: int):
     """Oracle value of every population at `node` after `steps` steps of a
     full-size run, from a (2 steps + 1)-wide window of the initial canonical
-    state `state0` ([Q+7, nz, ny, nx] float32, host).  Window edges inside the
+    state `state0` ([Q+7, nz, ny, nx] float32, numpy or torch).  Window edges inside the
     domain are given walls (x, z) or a wrap (y); their wrong values travel one
     node per step and do not reach the centre within `steps` steps."""
     Q = p.Q
@@ -73,7 +73,10 @@ def window_oracle(p: lbm.Params, state0: np.ndarray, node, steps: int):
     else:
         ys = np.arange(p.ny)
         cy = y
-    sub = state0[:, zs][:, :, ys][:, :, :, xs].astype(np.float64)
+    sub = state0[:, zs][:, :, ys][:, :, :, xs]
+    if not isinstance(sub, np.ndarray):          # a torch tensor (possibly on the GPU)
+        sub = sub.cpu().numpy()
+    sub = sub.astype(np.float64)
     f = np.moveaxis(sub[:Q], 0, -1) + weights(p.model)
     phi = np.moveaxis(sub[Q:], 0, -1).copy()
     op = oracle_params(p)

@@ -1,0 +1,120 @@
+"""GPU discrete adjoint (lbm_adjoint_step, LBMObjective) against the FP64
+reference gradient and against central finite differences.
+
+Bar: 1e-3 relative (FP32 arithmetic on the GPU)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import adjoint_ref as A
+from paper_2112_08479_gb300 import inputs, lbm
+from paper_2112_08479_gb300.objective import friction_objective
+
+from helpers import canonical_to_oracle, oracle_params, weights
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _sub_case(nx=32, ny=4, nz=8, **kw):
+    # the 32 x 4 x 8 sub-case with the lattice parameters of the 256 x 32 x 64
+    # differentiation box (H = 64, u_b = 0.03, Re = 2000): nu = 9.6e-4,
+    # g' = 1.40625e-5, C_s = 0.17; lock at x = H of the sub-case
+    base = dict(nx=nx, ny=ny, nz=nz, nu=9.6e-4, D=9.6e-4, cs_smag=0.17, sc_t=1.0,
+                gprime=1.40625e-5, x0=nz, H=nz)
+    base.update(kw)
+    return lbm.Params(**base)
+
+
+def _random_state(p, seed, amp=0.05):
+    w = weights(p.model)
+    fdev = w[:, None] * inputs.uniform((p.Q, p.N), seed, amp)
+    chi = 0.5 * (1 + inputs.uniform(p.N, seed + 1, 1.0))
+    w7 = O.velocities_q7()[1]
+    phi = w7[:, None] * chi[None, :] * (1 + inputs.uniform((7, p.N), seed + 2, amp))
+    return np.concatenate([fdev, phi]).astype(np.float32)
+
+
+@pytest.mark.parametrize("flags", [0, lbm.LBM_FLAG_PERIODIC_X | lbm.LBM_FLAG_PERIODIC_Z])
+@pytest.mark.parametrize("w_fw", [0.0, 1.0])
+def test_adjoint_step_matches_autograd_vjp(flags, w_fw):
+    """One reverse step: lam_n = C^T P^T lam + w dF_w/ds and the C_s term, vs
+    torch.autograd on the FP64 restatement of the step."""
+    p = _sub_case(nx=20, ny=5, nz=6, flags=flags, gprime=3e-3, eg=(0.3, -0.4, -0.866),
+                  cs_smag=0.4, sc_t=0.7, nu=0.01, D=0.02)
+    lat = lbm.Lattice(p, device="cuda")
+    s0 = _random_state(p, 3)
+    lam_next = inputs.normal((26, p.N), 8).astype(np.float32)
+    st = torch.from_numpy(s0).cuda()
+    ln = torch.from_numpy(lam_next).cuda()
+    out = torch.empty(26, p.N, device="cuda")
+    dcs = torch.zeros(1, dtype=torch.float64, device="cuda")
+    lat.adjoint_step(st, ln, out, dcs, w_fw)
+    got = out.cpu().numpy().astype(np.float64)
+
+    op = oracle_params(p)
+    step = A.BGKStep(op)
+    f, phi = canonical_to_oracle(s0, p)
+    ft = torch.tensor(f, requires_grad=True)
+    pt = torch.tensor(phi, requires_grad=True)
+    cs = torch.tensor(p.cs_smag, dtype=torch.float64, requires_grad=True)
+    f1, p1 = step(ft, pt, cs)
+    lf, lp = canonical_to_oracle(lam_next, p, shifted=False)
+    inner = (f1 * torch.tensor(lf)).sum() + (p1 * torch.tensor(lp)).sum() + w_fw * step.friction(ft, pt)
+    gf, gp, gc = torch.autograd.grad(inner, (ft, pt, cs))
+    want = np.concatenate([np.moveaxis(gf.numpy(), -1, 0), np.moveaxis(gp.numpy(), -1, 0)]).reshape(26, -1)
+    err = np.abs(got - want).max() / np.abs(want).max()
+    assert err < 1e-4, err
+    assert dcs.item() == pytest.approx(float(gc), rel=1e-3, abs=1e-6 * abs(float(gc)) + 1e-12)
+
+
+def test_gradient_vs_fp64_reference_sub_case():
+    """Full gradient over 2000 steps on the 32 x 4 x 8 sub-case with
+    checkpoints every 100 steps, vs the FP64 reference gradient."""
+    p = _sub_case()
+    nsteps = 2000
+    chi0 = O.lock_chi0(p.nx, p.ny, p.nz, p.x0, p.noise_amp, p.seed)
+    J_ref, g_ref, gcs_ref = A.gradient(oracle_params(p), chi0, p.cs_smag, nsteps)
+    x = torch.tensor(chi0.ravel(), dtype=torch.float32, device="cuda", requires_grad=True)
+    cs = torch.tensor(p.cs_smag, dtype=torch.float64, device="cuda", requires_grad=True)
+    J = friction_objective(x, cs, p, nsteps, K=100)
+    J.backward()
+    assert J.item() == pytest.approx(J_ref, rel=1e-4)
+    g = x.grad.cpu().numpy().astype(np.float64)
+    rel = np.linalg.norm(g - g_ref.ravel()) / np.linalg.norm(g_ref)
+    assert rel < 1e-3, rel
+    assert cs.grad.item() == pytest.approx(gcs_ref, rel=1e-3)
+
+
+def test_checkpoint_interval_does_not_change_gradient():
+    p = _sub_case()
+    chi0 = torch.tensor(O.lock_chi0(p.nx, p.ny, p.nz, p.x0, p.noise_amp, p.seed).ravel(),
+                        dtype=torch.float32, device="cuda")
+    grads = []
+    for K in (7, 100, 300):
+        x = chi0.clone().requires_grad_(True)
+        friction_objective(x, p.cs_smag, p, 300, K=K).backward()
+        grads.append(x.grad.clone())
+    assert torch.equal(grads[0], grads[1]) and torch.equal(grads[1], grads[2])
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3, 4])
+def test_gradient_vs_central_differences_full_box(seed):
+    """256 x 32 x 64, 2000 steps, K = 100: directional derivative vs central
+    differences of the FP32 forward (J accumulated in FP64)."""
+    p = lbm.lock_exchange(256, 32, 64, H=64, x0=64, u_b=0.03, Re=2000.0)
+    nsteps = 2000
+    lat = lbm.Lattice(p, device="cuda")
+    rho, u, chi = lat.macros()
+    chi0 = chi.reshape(-1).clone()
+    x = chi0.clone().requires_grad_(True)
+    friction_objective(x, p.cs_smag, p, nsteps, K=100).backward()
+    d = torch.tensor(inputs.unit_direction(p.N, seed), dtype=torch.float32, device="cuda")
+    eps = 1e-3 * np.sqrt(p.N)
+
+    def J(c):
+        return friction_objective(c, p.cs_smag, p, nsteps, K=100).item()
+
+    fd = (J(chi0 + eps * d) - J(chi0 - eps * d)) / (2 * eps)
+    ad = float((x.grad.double() * d.double()).sum())
+    assert ad == pytest.approx(fd, rel=1e-3), (ad, fd)

@@ -1,0 +1,80 @@
+"""Parity at the full 2048 x 128 x 256 size, in the launch configuration the
+benchmark times: two steps (one even, one odd AA parity) from a random
+near-equilibrium state, checked node by node on a sample of nodes (corners,
+edges, faces, interior) against the FP64 oracle run on each node's light cone;
+plus conservation over a longer run."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2112_08479_gb300 import inputs, lbm
+
+from helpers import weights, window_oracle
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+NX, NY, NZ = 2048, 128, 256
+
+
+def _sample_nodes(seed=5, n_random=12):
+    xs, ys, zs = [0, 1, NX - 2, NX - 1], [0, NY - 1], [0, 1, NZ - 2, NZ - 1]
+    nodes = [(x, y, z) for x in (0, NX - 1) for y in (0, NY - 1) for z in (0, NZ - 1)]
+    nodes += [(x, 64, 128) for x in xs] + [(1000, y, 128) for y in ys] + [(1000, 64, z) for z in zs]
+    rng = np.random.default_rng(seed)
+    nodes += [(int(rng.integers(NX)), int(rng.integers(NY)), int(rng.integers(NZ))) for _ in range(n_random)]
+    return nodes
+
+
+def _random_full_state(p, seed, amp=0.05):
+    w = torch.tensor(weights(p.model), dtype=torch.float32, device="cuda")
+    w7 = torch.tensor(O.velocities_q7()[1], dtype=torch.float32, device="cuda")
+    s = torch.empty(p.Q + 7, p.N, dtype=torch.float32, device="cuda")
+    s[: p.Q] = inputs.torch_uniform((p.Q, p.N), seed, amp) * w[:, None]
+    chi = 0.5 * (1 + inputs.torch_uniform((p.N,), seed + 1, 1.0))
+    s[p.Q:] = w7[:, None] * chi[None, :] * (1 + inputs.torch_uniform((7, p.N), seed + 2, amp))
+    return s
+
+
+@pytest.mark.parametrize("model,storage", [("bgk", "fp32"), ("cumulant", "fp32"), ("bgk", "fp16s")])
+def test_full_size_sampled_nodes(model, storage):
+    p = lbm.lock_exchange(NX, NY, NZ, H=256, x0=256, u_b=0.03, Re=30000.0, model=model,
+                          storage=storage)
+    # a stronger force so the force terms are visible in two steps
+    p.gprime = 1e-3
+    lat = lbm.Lattice(p, device="cuda")
+    s0 = _random_full_state(p, 17)
+    lat.set_state(s0)
+    s0 = lat.get_state()            # what the storage actually holds (rounded for 16-bit)
+    lat.step(2)                     # the kernel and grid the benchmark launches
+    s2 = lat.get_state()
+    s0v = s0.view(p.Q + 7, NZ, NY, NX)
+    s2v = s2.view(p.Q + 7, NZ, NY, NX)
+    scale = float(s0[: p.Q].abs().max())
+    for node in _sample_nodes():
+        x, y, z = node
+        f_o, phi_o = window_oracle(p, s0v, node, 2)
+        got = s2v[:, z, y, x].cpu().numpy().astype(np.float64)
+        if storage == "fp32":
+            assert np.abs(got[: p.Q] - f_o).max() < 1e-5 * scale, node
+            assert np.abs(got[p.Q:] - phi_o).max() < 1e-6, node
+        else:
+            # FP16: the stored result is the RN rounding of the exact result
+            # (11-bit significand) after FP32 arithmetic
+            tol_f = 2.0**-11 * np.abs(f_o) + 1e-5 * scale
+            tol_p = 2.0**-11 * np.abs(phi_o) + 1e-6
+            assert np.all(np.abs(got[: p.Q] - f_o) <= tol_f), node
+            assert np.all(np.abs(got[p.Q:] - phi_o) <= tol_p), node
+
+
+def test_full_size_budgets_conserved():
+    p = lbm.lock_exchange(NX, NY, NZ, H=256, x0=256, u_b=0.03, Re=30000.0)
+    lat = lbm.Lattice(p, device="cuda")
+    d0 = lat.diag()
+    lat.step(200)
+    d1 = lat.diag()
+    assert d1["flags"] == 0
+    assert abs(d1["scalar_mass"] - d0["scalar_mass"]) < 1e-7 * d0["scalar_mass"]
+    assert abs(d1["mass_delta"] - d0["mass_delta"]) < 1e-7 * p.N
+    # the gate column starts at x0 - 1 = 255: the front has moved forward
+    assert d1["front"] > d0["front"]

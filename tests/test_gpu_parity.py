@@ -89,7 +89,7 @@ def test_lock_exchange_one_step(model):
     op, (f, phi) = lock_state_oracle(p)
     # the initial condition itself
     e_rho, e_u, e_chi = _compare_macros(lat, op, f, phi)
-    assert e_rho == 0 and e_chi < 1e-7
+    assert e_rho < 1e-7 and e_chi < 1e-7
     lat.step(1)
     f, phi = O.step(op, f, phi)
     e_rho, e_u, e_chi = _compare_macros(lat, op, f, phi)
@@ -133,8 +133,8 @@ def test_random_state_two_steps(model, shape):
         f, phi = O.step(op, f, phi)
         got = lat.get_state().cpu().numpy().astype(np.float64)
         want = oracle_to_canonical(f, phi, p)
-        assert np.abs(got[: p.Q] - want[: p.Q]).max() < 2e-6 * scale, n
-        assert np.abs(got[p.Q:] - want[p.Q:]).max() < 2e-7, n
+        assert np.abs(got[: p.Q] - want[: p.Q]).max() < 1e-5 * scale, n
+        assert np.abs(got[p.Q:] - want[p.Q:]).max() < 1e-6, n
 
 
 @pytest.mark.parametrize("model", [0, 1])

@@ -1,0 +1,88 @@
+"""16-bit shifted storage (FP16 / BF16 of scale * (f - w) and scale * Phi,
+round-to-nearest-even, FP32 arithmetic) against the FP64 oracle.
+
+Bars are derived from the rounding: a stored value is the RN rounding of the
+exact FP32 result, so its error is at most half an ulp of the significand
+(2^-11 relative for FP16, 2^-8 for BF16) plus the FP32 arithmetic error."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2112_08479_gb300 import inputs, lbm
+
+from helpers import canonical_to_oracle, lock_state_oracle, oracle_params, oracle_to_canonical, weights
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+REL = {lbm.LBM_FP16S: 2.0**-11, lbm.LBM_BF16S: 2.0**-8}
+
+
+def _random_state(p, seed, amp=0.05):
+    w = weights(p.model)
+    fdev = w[:, None] * inputs.uniform((p.Q, p.N), seed, amp)
+    chi = 0.5 * (1 + inputs.uniform(p.N, seed + 1, 1.0))
+    w7 = O.velocities_q7()[1]
+    phi = w7[:, None] * chi[None, :] * (1 + inputs.uniform((7, p.N), seed + 2, amp))
+    return np.concatenate([fdev, phi]).astype(np.float32)
+
+
+def _rn(v, storage, scale):
+    t = torch.from_numpy(np.ascontiguousarray(v * scale, dtype=np.float32))
+    t = t.to(torch.float16 if storage == lbm.LBM_FP16S else torch.bfloat16).to(torch.float32)
+    return t.numpy() / scale
+
+
+@pytest.mark.parametrize("storage", [lbm.LBM_FP16S, lbm.LBM_BF16S])
+@pytest.mark.parametrize("model", [0, 1])
+def test_set_get_round_trip_is_rn(storage, model):
+    p = lbm.Params(17, 3, 5, model=model, storage=storage, x0=1, H=5)
+    lat = lbm.Lattice(p, device="cuda")
+    s0 = _random_state(p, 4)
+    lat.set_state(torch.from_numpy(s0).cuda())
+    got = lat.get_state().cpu().numpy()
+    assert np.array_equal(got[: p.Q], _rn(s0[: p.Q], storage, p.scale_f))
+    assert np.array_equal(got[p.Q:], _rn(s0[p.Q:], storage, p.scale_phi))
+
+
+@pytest.mark.parametrize("storage", [lbm.LBM_FP16S, lbm.LBM_BF16S])
+@pytest.mark.parametrize("model", [0, 1])
+def test_one_step_within_rounding(storage, model):
+    p = lbm.Params(33, 4, 6, model=model, storage=storage, nu=0.01, D=0.012, cs_smag=0.3,
+                   gprime=2e-3, eg=(0.48, 0.6, -0.64), x0=1, H=6)
+    lat = lbm.Lattice(p, device="cuda")
+    lat.set_state(torch.from_numpy(_random_state(p, 6)).cuda())
+    s0 = lat.get_state().cpu().numpy()
+    op = oracle_params(p)
+    f, phi = canonical_to_oracle(s0, p)
+    scale = np.abs(s0[: p.Q]).max()
+    for n in (1, 2):
+        lat.step(1)
+        f, phi = O.step(op, f, phi)
+        got = lat.get_state().cpu().numpy().astype(np.float64)
+        want = oracle_to_canonical(f, phi, p)
+        tol = REL[storage] * np.abs(want) * 1.01 + 1e-5 * np.r_[[scale] * p.Q, [1e-1] * 7][:, None]
+        assert np.all(np.abs(got - want) <= tol), n
+        # the next step starts from the rounded state
+        f, phi = canonical_to_oracle(got.astype(np.float32), p)
+
+
+@pytest.mark.parametrize("storage", [lbm.LBM_FP16S, lbm.LBM_BF16S])
+def test_lock_exchange_runs_close_to_oracle(storage):
+    """Config-1 box, 300 steps: 16-bit storage stays within a loose band of the
+    FP64 oracle (the error budget of the storage form is reported, not hidden)."""
+    p = lbm.lock_exchange(128, 8, 16, H=16, x0=16, u_b=0.05, Re=1000.0, storage=
+                          {lbm.LBM_FP16S: "fp16s", lbm.LBM_BF16S: "bf16s"}[storage])
+    lat = lbm.Lattice(p, device="cuda")
+    op, (f, phi) = lock_state_oracle(p)
+    lat.step(300)
+    f, phi = O.run(op, 300, f, phi)
+    rho, u, chi = (t.cpu().numpy() for t in lat.macros())
+    _, u_o, chi_o = O.macros(op, f, phi)
+    e_chi = np.abs(chi - chi_o).max()
+    e_u = np.abs(np.moveaxis(u, 0, -1) - u_o).max() / np.abs(u_o).max()
+    assert e_chi < (2e-3 if storage == lbm.LBM_FP16S else 2e-2)
+    assert e_u < (5e-2 if storage == lbm.LBM_FP16S else 0.5)
+    d = lat.diag()
+    do = O.diag(op, f, phi, p.x0, float(p.H))
+    assert abs(d["front"] - do["front"]) < (0.02 if storage == lbm.LBM_FP16S else 0.1)

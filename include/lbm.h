@@ -29,8 +29,9 @@
  *    lbm_sync).  Nothing aborts, exits or traps.
  *  - Canonical state layout (lbm_get_state / lbm_set_state / adjoint):
  *    FP32, direction-major, [Q + 7][N]: rows 0..Q-1 hold f_i - w_i of the
- *    pre-collision (streamed) fluid populations, rows Q..Q+6 hold Phi_k of
- *    the scalar populations.  Direction orders: D3Q19 as in Eq. 23; D3Q27
+ *    pre-collision (streamed) fluid populations, rows Q..Q+6 hold Phi_k - w_k
+ *    of the scalar populations (w the lattice weights; both sets are held as
+ *    deviations from their rest state rho = 1, chi = 1).  Direction orders: D3Q19 as in Eq. 23; D3Q27
  *    as Eq. 23 followed by the corners (1,1,1), (-1,-1,-1), (1,1,-1),
  *    (-1,-1,1), (1,-1,1), (-1,1,-1), (-1,1,1), (1,-1,-1); D3Q7 rest, +x, -x,
  *    +y, -y, +z, -z.
@@ -68,8 +69,8 @@ typedef enum lbm_model {
 } lbm_model;
 
 typedef enum lbm_storage {
-    LBM_FP32 = 0,   /* populations stored as FP32: f - w and Phi */
-    LBM_FP16S = 1,  /* FP16, scale_f * (f - w) and scale_phi * Phi, RN rounding */
+    LBM_FP32 = 0,   /* populations stored as FP32: f - w and Phi - w */
+    LBM_FP16S = 1,  /* FP16, scale_f * (f - w) and scale_phi * (Phi - w), RN rounding */
     LBM_BF16S = 2   /* BF16, same shifts and scales, RN rounding */
 } lbm_storage;
 
@@ -84,7 +85,7 @@ typedef enum lbm_storage {
 
 typedef struct lbm_params {
     int32_t nx, ny, nz;       /* nodes; 1 <= nx, ny, nz; nx*ny*nz < 2^31;
-                                 ny, nz <= 65535 */
+                                 Q*nx*ny*nz < 2^32; ny, nz <= 65535 */
     int32_t model;            /* lbm_model */
     int32_t storage;          /* lbm_storage */
     int32_t flags;            /* LBM_FLAG_* */
@@ -105,7 +106,7 @@ typedef struct lbm_params {
     uint64_t seed;            /* noise draw for node n: splitmix64(seed ^ n) */
     double front_threshold;   /* span-averaged chi threshold of the front (0.02) */
     double scale_f;           /* 16-bit storage scale of f - w (power of two) */
-    double scale_phi;         /* 16-bit storage scale of Phi (power of two) */
+    double scale_phi;         /* 16-bit storage scale of Phi - w (power of two) */
 } lbm_params;
 
 typedef struct lbm_diagnostics {

@@ -8,7 +8,7 @@
 //   F_w = sum_{x,y} nu (9 u_x(x,y,0) - u_x(x,y,1)) / 3   (Eq. 62-64: the
 //   derivative at the wall z = -1/2 of the quadratic through u = 0 there and
 //   the first two nodes);
-//   budgets sum (rho - 1) and sum chi.
+//   budgets sum (rho - 1) and sum chi (= N + sum (chi - 1)).
 // Column sums run in FP32 with Kahan compensation, block and grid sums of the
 // budgets in FP64, the friction in compensated FP32 pairs; every reduction
 // has a fixed order, so results are bitwise reproducible.
@@ -21,16 +21,17 @@ namespace lbmgpu {
 template <typename S>
 __device__ __forceinline__ constexpr bool is16() { return !std::is_same<S, float>::value; }
 
-// rho - 1, u (with the half-force shift, Eq. 20) and chi at node n.
+// rho - 1, u (with the half-force shift, Eq. 20) and chi - 1 at node n.
 template <int Q, bool ODD, typename S>
 __device__ __forceinline__ void node_macros(const KParams& kp, const S* __restrict__ f,
                                             const S* __restrict__ phi, int x, int y, int z,
                                             unsigned n, float& drho, float& ux, float& uy,
-                                            float& uz, float& chi) {
+                                            float& uz, float& chit) {
+    const Stencil st = make_stencil(kp, x, y, z);
     float fv[Q], pv[7];
-    gather<Q, ODD>(kp, f, x, y, z, n, fv);
-    gather<7, ODD>(kp, phi, x, y, z, n, pv);
-    float c = 0.0f;
+    gather<Q, ODD>(kp, f, st, fv);
+    gather<7, ODD>(kp, phi, st, pv);
+    float c = 0.0f;   // chi - 1 (Phi is held as Phi - w)
 #pragma unroll
     for (int k = 0; k < 7; ++k) c += pv[k];
     if (is16<S>()) c *= kp.isp;
@@ -44,11 +45,12 @@ __device__ __forceinline__ void node_macros(const KParams& kp, const S* __restri
     }
     if (is16<S>()) { d *= kp.isf; jx *= kp.isf; jy *= kp.isf; jz *= kp.isf; }
     const float irho = 1.0f / (1.0f + d);
+    const float chi = 1.0f + c;
     drho = d;
-    chi = c;
-    ux = (jx + 0.5f * kp.gx * c) * irho;
-    uy = (jy + 0.5f * kp.gy * c) * irho;
-    uz = (jz + 0.5f * kp.gz * c) * irho;
+    chit = c;
+    ux = (jx + 0.5f * kp.gx * chi) * irho;
+    uy = (jy + 0.5f * kp.gy * chi) * irho;
+    uz = (jz + 0.5f * kp.gz * chi) * irho;
 }
 
 // ---------------------------------------------------------------------------
@@ -71,11 +73,11 @@ __global__ void init_kernel(KParams kp, S* __restrict__ f, S* __restrict__ phi,
     const int y = blockIdx.y, z = blockIdx.z;
     const unsigned n = (unsigned)x + (unsigned)kp.nx * ((unsigned)y + (unsigned)kp.ny * (unsigned)z);
     const size_t N = kp.N;
-    float c;
+    float c;  // chi0 - 1
     if (chi0) {
-        c = chi0[n];
+        c = chi0[n] - 1.0f;
     } else {
-        double v = x < x0 ? 1.0 : 0.0;
+        double v = x < x0 ? 0.0 : -1.0;
         if (x == x0 - 1) {
             const double r = (double)(splitmix64(seed ^ (unsigned long long)n) >> 11) * 0x1.0p-53;
             v += amp * (2.0 * r - 1.0);
@@ -110,7 +112,7 @@ __global__ void macros_kernel(KParams kp, const S* __restrict__ f, const S* __re
     const size_t N = kp.N;
     if (rho) rho[n] = 1.0f + d;
     if (u) { u[n] = ux; u[N + n] = uy; u[2 * N + n] = uz; }
-    if (chi) chi[n] = c;
+    if (chi) chi[n] = 1.0f + c;
 }
 
 template <int Q, bool ODD, typename S>
@@ -119,10 +121,11 @@ __global__ void get_state_kernel(KParams kp, const S* __restrict__ f, const S* _
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= kp.nx) return;
     const int y = blockIdx.y, z = blockIdx.z;
-    const unsigned n = (unsigned)x + (unsigned)kp.nx * ((unsigned)y + (unsigned)kp.ny * (unsigned)z);
+    const Stencil st = make_stencil(kp, x, y, z);
+    const unsigned n = st.n;
     float fv[Q], pv[7];
-    gather<Q, ODD>(kp, f, x, y, z, n, fv);
-    gather<7, ODD>(kp, phi, x, y, z, n, pv);
+    gather<Q, ODD>(kp, f, st, fv);
+    gather<7, ODD>(kp, phi, st, pv);
     const size_t N = kp.N;
 #pragma unroll
     for (int i = 0; i < Q; ++i) dst[(size_t)i * N + n] = is16<S>() ? fv[i] * kp.isf : fv[i];
@@ -196,7 +199,7 @@ __global__ void __launch_bounds__(DIAG_BX) diag_columns_kernel(
                 bad |= LBM_DEVFLAG_NONFINITE;
         }
         if (bad) atomicOr(flags, bad);
-        const float cb = (kc.s + kc.c) / (float)kp.ny;
+        const float cb = 1.0f + (kc.s + kc.c) / (float)kp.ny;
         chibar[(size_t)z * kp.nx + x] = cb;
         atomicMax(colmax + x, fkey(cb));
         m_rho = (double)kr.s + (double)kr.c;
@@ -236,8 +239,9 @@ __global__ void __launch_bounds__(DIAG_BX) diag_columns_kernel(
 constexpr int FIN_T = 512;
 
 __global__ void __launch_bounds__(FIN_T) diag_finalize_kernel(
-    int nx, unsigned nblocks, const double* __restrict__ part, const float* __restrict__ fwpart,
-    unsigned* __restrict__ colmax, DevDiag* __restrict__ out, double thr, int x0, double H) {
+    int nx, double nodes, unsigned nblocks, const double* __restrict__ part,
+    const float* __restrict__ fwpart, unsigned* __restrict__ colmax, DevDiag* __restrict__ out,
+    double thr, int x0, double H) {
     __shared__ double sa[FIN_T], sb[FIN_T];
     __shared__ float ss[FIN_T], sc[FIN_T];
     __shared__ int sx[FIN_T];
@@ -278,7 +282,7 @@ __global__ void __launch_bounds__(FIN_T) diag_finalize_kernel(
         out->front = (xn + 0.5 - x0) / H;
         out->Fw = (double)ss[0] + (double)sc[0];
         out->mass_delta = sa[0];
-        out->scalar_mass = sb[0];
+        out->scalar_mass = nodes + sb[0];   // the columns summed chi - 1
     }
     __syncthreads();
     for (int x = t; x < nx; x += FIN_T) colmax[x] = 0x007fffffu;  // ready for the next call
@@ -401,8 +405,8 @@ cudaError_t launch_diag(const KParams& kp, int model, int storage, bool odd, con
                 kp, (const S*)v.f, (const S*)v.phi, v.chibar, v.colmax, v.part, v.fwpart, v.devflags);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        diag_finalize_kernel<<<1, FIN_T, 0, st>>>(kp.nx, v.diag_blocks, v.part, v.fwpart, v.colmax,
-                                                  v.ddiag, threshold, x0, H);
+        diag_finalize_kernel<<<1, FIN_T, 0, st>>>(kp.nx, (double)kp.N, v.diag_blocks, v.part,
+                                                  v.fwpart, v.colmax, v.ddiag, threshold, x0, H);
         return cudaGetLastError();
     });
 }

@@ -25,11 +25,13 @@
 
 namespace lbmgpu {
 
-// Replaces f (held as f - w) and Phi by their post-collision values.
+// Replaces f (held as f - w) and Phi (held as Phi - w) by their
+// post-collision values.
 __device__ __forceinline__ void collide_bgk(const KParams& kp, float (&f)[19], float (&p)[7]) {
-    float chi = 0.0f;
+    float chit = 0.0f;  // chi - 1
 #pragma unroll
-    for (int k = 0; k < 7; ++k) chi += p[k];
+    for (int k = 0; k < 7; ++k) chit += p[k];
+    const float chi = 1.0f + chit;
     const float Fx = kp.gx * chi, Fy = kp.gy * chi, Fz = kp.gz * chi;
 
     float drho = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
@@ -83,27 +85,28 @@ __device__ __forceinline__ void collide_bgk(const KParams& kp, float (&f)[19], f
         f[i] = f[i] - om * (f[i] - feq) + S;
     }
 
+    // Phi_eq - w = w (chi - 1 + 4 chi c.u)
     const float omp = 1.0f / (kp.taup0 + kp.kT * dtau);
 #pragma unroll
     for (int k = 0; k < 7; ++k) {
         const float cu = cx27(k) * ux + cy27(k) * uy + cz27(k) * uz;
-        const float peq = w7(k) * chi * (1.0f + 4.0f * cu);
+        const float peq = w7(k) * (chit + 4.0f * chi * cu);
         p[k] = p[k] - omp * (p[k] - peq);
     }
 }
 
 template <bool ODD, bool SAVE, typename S>
-__global__ void __launch_bounds__(128) bgk_step_kernel(KParams kp, S* __restrict__ f,
+__global__ void __launch_bounds__(128, LBM_STEP_MINB) bgk_step_kernel(KParams kp, S* __restrict__ f,
                                                        S* __restrict__ phi,
                                                        float* __restrict__ save) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= kp.nx) return;
-    const int y = blockIdx.y, z = blockIdx.z;
-    const unsigned n = (unsigned)x + (unsigned)kp.nx * ((unsigned)y + (unsigned)kp.ny * (unsigned)z);
+    const Stencil st = make_stencil(kp, x, blockIdx.y, blockIdx.z);
+    const unsigned n = st.n;
 
     float fv[19], pv[7];
-    gather<19, ODD>(kp, f, x, y, z, n, fv);
-    gather<7, ODD>(kp, phi, x, y, z, n, pv);
+    gather<19, ODD>(kp, f, st, fv);
+    gather<7, ODD>(kp, phi, st, pv);
     if (!std::is_same<S, float>::value) {
 #pragma unroll
         for (int i = 0; i < 19; ++i) fv[i] *= kp.isf;
@@ -124,8 +127,8 @@ __global__ void __launch_bounds__(128) bgk_step_kernel(KParams kp, S* __restrict
 #pragma unroll
         for (int k = 0; k < 7; ++k) pv[k] *= kp.sp;
     }
-    scatter<19, ODD>(kp, f, x, y, z, n, fv);
-    scatter<7, ODD>(kp, phi, x, y, z, n, pv);
+    scatter<19, ODD>(kp, f, st, fv);
+    scatter<7, ODD>(kp, phi, st, pv);
 }
 
 template <typename S>
@@ -200,9 +203,10 @@ __global__ void __launch_bounds__(128) bgk_adjoint_kernel(KParams kp, const floa
         for (int k = 0; k < 7; ++k) p[k] = st[(size_t)(19 + k) * N + n];
 
         // ---- forward recompute (as collide_bgk) ----
-        float chi = 0.0f;
+        float chit = 0.0f;
 #pragma unroll
-        for (int k = 0; k < 7; ++k) chi += p[k];
+        for (int k = 0; k < 7; ++k) chit += p[k];
+        const float chi = 1.0f + chit;
         const float Fx = kp.gx * chi, Fy = kp.gy * chi, Fz = kp.gz * chi;
         float drho = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
         float mxx = 0.0f, myy = 0.0f, mzz = 0.0f, mxy = 0.0f, mxz = 0.0f, myz = 0.0f;
@@ -241,7 +245,7 @@ __global__ void __launch_bounds__(128) bgk_adjoint_kernel(KParams kp, const floa
 #pragma unroll
         for (int k = 0; k < 7; ++k) {
             const float cu = cx27(k) * ux + cy27(k) * uy + cz27(k) * uz;
-            const float peq = w7(k) * chi * (1.0f + 4.0f * cu);
+            const float peq = w7(k) * (chit + 4.0f * chi * cu);
             gp[k] = (1.0f - omp) * mup[k];
             gomp += mup[k] * (peq - p[k]);
             const float gpeq = omp * mup[k];
@@ -317,7 +321,7 @@ __global__ void __launch_bounds__(128) bgk_adjoint_kernel(KParams kp, const floa
                      gpyy * cyi * cyi + gpzz * czi * czi + gpxy * cxi * cyi + gpxz * cxi * czi +
                      gpyz * cyi * czi;
         }
-        // F = g' chi e^g, chi = sum Phi
+        // F = g' chi e^g, chi = 1 + sum (Phi - w)
         gchi += gFx * kp.gx + gFy * kp.gy + gFz * kp.gz;
 #pragma unroll
         for (int k = 0; k < 7; ++k) gp[k] += gchi;

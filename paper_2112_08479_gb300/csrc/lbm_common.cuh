@@ -69,40 +69,89 @@ struct KParams {
 };
 
 // ---------------------------------------------------------------------------
+// Tuning of the step kernels (compile-time): minimum resident blocks per SM
+// requested from the register allocator, and whether population traffic uses
+// the streaming (evict-first) cache policy.  Each population is touched once
+// per step, so nothing is lost by not keeping it cached.
+#ifndef LBM_STEP_MINB
+#define LBM_STEP_MINB 4
+#endif
+#ifndef LBM_STREAMING_HINTS
+#define LBM_STREAMING_HINTS 0
+#endif
+
+// ---------------------------------------------------------------------------
 // Storage types: FP32, or FP16 / BF16 with round-to-nearest-even.
+template <typename T>
+__device__ __forceinline__ T ld_pop(const T* p) {
+#if LBM_STREAMING_HINTS
+    return __ldcs(p);
+#else
+    return *p;
+#endif
+}
+template <typename T>
+__device__ __forceinline__ void st_pop(T* p, T v) {
+#if LBM_STREAMING_HINTS
+    __stcs(p, v);
+#else
+    *p = v;
+#endif
+}
+
 template <typename S> struct Store;
 template <> struct Store<float> {
-    static __device__ __forceinline__ float ld(const float* p) { return *p; }
-    static __device__ __forceinline__ void st(float* p, float v) { *p = v; }
+    static __device__ __forceinline__ float ld(const float* p) { return ld_pop(p); }
+    static __device__ __forceinline__ void st(float* p, float v) { st_pop(p, v); }
 };
 template <> struct Store<__half> {
-    static __device__ __forceinline__ float ld(const __half* p) { return __half2float(*p); }
-    static __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
+    static __device__ __forceinline__ float ld(const __half* p) { return __half2float(ld_pop(p)); }
+    static __device__ __forceinline__ void st(__half* p, float v) { st_pop(p, __float2half_rn(v)); }
 };
 template <> struct Store<__nv_bfloat16> {
-    static __device__ __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162float(*p); }
-    static __device__ __forceinline__ void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+    static __device__ __forceinline__ float ld(const __nv_bfloat16* p) {
+        return __bfloat162float(ld_pop(p));
+    }
+    static __device__ __forceinline__ void st(__nv_bfloat16* p, float v) {
+        st_pop(p, __float2bfloat16_rn(v));
+    }
 };
 
 // ---------------------------------------------------------------------------
-// Neighbour of (x, y, z) displaced by (dx, dy, dz): y always periodic, x and
-// z bounded by half-way bounce-back walls unless the periodic flags are set.
-// Returns false when the neighbour lies beyond a wall.
-__device__ __forceinline__ bool neighbour(const KParams& kp, int x, int y, int z, int dx, int dy,
-                                          int dz, unsigned& idx) {
-    int xn = x + dx, yn = y + dy, zn = z + dz;
-    if (yn < 0) yn += kp.ny;
-    else if (yn >= kp.ny) yn -= kp.ny;
-    if (xn < 0 || xn >= kp.nx) {
-        if (!(kp.flags & LBM_FLAG_PERIODIC_X)) return false;
-        xn = xn < 0 ? xn + kp.nx : xn - kp.nx;
-    }
-    if (zn < 0 || zn >= kp.nz) {
-        if (!(kp.flags & LBM_FLAG_PERIODIC_Z)) return false;
-        zn = zn < 0 ? zn + kp.nz : zn - kp.nz;
-    }
-    idx = (unsigned)xn + (unsigned)kp.nx * ((unsigned)yn + (unsigned)kp.ny * (unsigned)zn);
-    return true;
+// Neighbourhood of one node, computed once per thread: the node indices of
+// the rows (y + dy, z + dz) and the columns x + dx, with y always periodic
+// and x, z bounded by half-way bounce-back walls unless the periodic flags
+// are set.  Element offsets are 32-bit: the library accepts only sizes with
+// Q * N < 2^32.
+struct Stencil {
+    unsigned n;        // this node
+    unsigned zr[3];    // (z + dz) * nx * ny for dz = -1, 0, 1
+    unsigned yr[3];    // (y + dy) * nx       for dy = -1, 0, 1
+    unsigned xc[3];    // x + dx              for dx = -1, 0, 1
+    bool zo[3], xo[3]; // neighbour in the fluid (or wrapped)
+};
+
+__device__ __forceinline__ Stencil make_stencil(const KParams& kp, int x, int y, int z) {
+    Stencil s;
+    const bool px = (kp.flags & LBM_FLAG_PERIODIC_X) != 0;
+    const bool pz = (kp.flags & LBM_FLAG_PERIODIC_Z) != 0;
+    const int ym = y == 0 ? kp.ny - 1 : y - 1, yp = y == kp.ny - 1 ? 0 : y + 1;
+    const int zm = z == 0 ? kp.nz - 1 : z - 1, zp = z == kp.nz - 1 ? 0 : z + 1;
+    const int xm = x == 0 ? kp.nx - 1 : x - 1, xp = x == kp.nx - 1 ? 0 : x + 1;
+    s.yr[0] = (unsigned)ym * kp.nx; s.yr[1] = (unsigned)y * kp.nx; s.yr[2] = (unsigned)yp * kp.nx;
+    s.zr[0] = (unsigned)zm * kp.nxny; s.zr[1] = (unsigned)z * kp.nxny; s.zr[2] = (unsigned)zp * kp.nxny;
+    s.xc[0] = (unsigned)xm; s.xc[1] = (unsigned)x; s.xc[2] = (unsigned)xp;
+    s.zo[0] = z > 0 || pz; s.zo[1] = true; s.zo[2] = z < kp.nz - 1 || pz;
+    s.xo[0] = x > 0 || px; s.xo[1] = true; s.xo[2] = x < kp.nx - 1 || px;
+    s.n = s.zr[1] + s.yr[1] + s.xc[1];
+    return s;
+}
+
+// Node index of the neighbour displaced by (dx, dy, dz); `inside` is false
+// when it lies beyond a wall.
+__device__ __forceinline__ unsigned nbr(const Stencil& s, int dx, int dy, int dz, bool& inside) {
+    inside = s.xo[dx + 1] && s.zo[dz + 1];
+    return s.zr[dz + 1] + s.yr[dy + 1] + s.xc[dx + 1];
 }
 
 // ---------------------------------------------------------------------------
@@ -119,39 +168,54 @@ __device__ __forceinline__ bool neighbour(const KParams& kp, int x, int y, int z
 // thread in each step, so the update is race-free in place.
 
 template <int Q, bool ODD, typename S>
-__device__ __forceinline__ void gather(const KParams& kp, const S* __restrict__ a, int x, int y,
-                                       int z, unsigned n, float (&v)[Q]) {
-    const size_t N = kp.N;
+__device__ __forceinline__ void gather(const KParams& kp, const S* __restrict__ a,
+                                       const Stencil& st, float (&v)[Q]) {
+    const unsigned N = kp.N;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        if (!ODD) {
-            v[i] = Store<S>::ld(a + (size_t)i * N + n);
-        } else {
-            unsigned s;
-            if (i != 0 && neighbour(kp, x, y, z, -cx27(i), -cy27(i), -cz27(i), s))
-                v[i] = Store<S>::ld(a + (size_t)opp(i) * N + s);
-            else
-                v[i] = Store<S>::ld(a + (size_t)i * N + n);
+        unsigned off = (unsigned)i * N + st.n;
+        if (ODD && i != 0) {
+            bool in;
+            const unsigned s = nbr(st, -cx27(i), -cy27(i), -cz27(i), in);
+            off = in ? (unsigned)opp(i) * N + s : off;
         }
+        v[i] = Store<S>::ld(a + off);
     }
 }
 
 template <int Q, bool ODD, typename S>
-__device__ __forceinline__ void scatter(const KParams& kp, S* __restrict__ a, int x, int y, int z,
-                                        unsigned n, const float (&v)[Q]) {
-    const size_t N = kp.N;
+__device__ __forceinline__ void scatter(const KParams& kp, S* __restrict__ a, const Stencil& st,
+                                        const float (&v)[Q]) {
+    const unsigned N = kp.N;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        if (!ODD) {
-            Store<S>::st(a + (size_t)opp(i) * N + n, v[i]);
-        } else {
-            unsigned d;
-            if (i != 0 && neighbour(kp, x, y, z, cx27(i), cy27(i), cz27(i), d))
-                Store<S>::st(a + (size_t)i * N + d, v[i]);
-            else
-                Store<S>::st(a + (size_t)opp(i) * N + n, v[i]);
+        unsigned off = (unsigned)opp(i) * N + st.n;
+        if (ODD && i != 0) {
+            bool in;
+            const unsigned d = nbr(st, cx27(i), cy27(i), cz27(i), in);
+            off = in ? (unsigned)i * N + d : off;
         }
+        Store<S>::st(a + off, v[i]);
     }
+}
+
+// Legacy form used by the auxiliary kernels: neighbour of (x, y, z) displaced
+// by (dx, dy, dz), false beyond a wall.
+__device__ __forceinline__ bool neighbour(const KParams& kp, int x, int y, int z, int dx, int dy,
+                                          int dz, unsigned& idx) {
+    int xn = x + dx, yn = y + dy, zn = z + dz;
+    if (yn < 0) yn += kp.ny;
+    else if (yn >= kp.ny) yn -= kp.ny;
+    if (xn < 0 || xn >= kp.nx) {
+        if (!(kp.flags & LBM_FLAG_PERIODIC_X)) return false;
+        xn = xn < 0 ? xn + kp.nx : xn - kp.nx;
+    }
+    if (zn < 0 || zn >= kp.nz) {
+        if (!(kp.flags & LBM_FLAG_PERIODIC_Z)) return false;
+        zn = zn < 0 ? zn + kp.nz : zn - kp.nz;
+    }
+    idx = (unsigned)xn + (unsigned)kp.nx * ((unsigned)yn + (unsigned)kp.ny * (unsigned)zn);
+    return true;
 }
 
 // ---------------------------------------------------------------------------

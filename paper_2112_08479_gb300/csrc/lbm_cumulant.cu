@@ -52,9 +52,10 @@ __host__ __device__ constexpr int dir27(int x, int y, int z) {
 }
 
 __device__ __forceinline__ void collide_cumulant(const KParams& kp, float (&f)[27], float (&p)[7]) {
-    float chi = 0.0f;
+    float chit = 0.0f;  // chi - 1 (Phi is held as Phi - w)
 #pragma unroll
-    for (int k = 0; k < 7; ++k) chi += p[k];
+    for (int k = 0; k < 7; ++k) chit += p[k];
+    const float chi = 1.0f + chit;
     const float Fx = kp.gx * chi, Fy = kp.gy * chi, Fz = kp.gz * chi;
 
     float drho = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
@@ -149,23 +150,23 @@ __device__ __forceinline__ void collide_cumulant(const KParams& kp, float (&f)[2
 #pragma unroll
     for (int k = 0; k < 7; ++k) {
         const float cu = cx27(k) * hx + cy27(k) * hy + cz27(k) * hz;
-        const float peq = w7(k) * chi * (1.0f + 4.0f * cu);
+        const float peq = w7(k) * (chit + 4.0f * chi * cu);   // Phi_eq - w
         p[k] = p[k] - omp * (p[k] - peq);
     }
 }
 
 template <bool ODD, bool SAVE, typename S>
-__global__ void __launch_bounds__(128) cumulant_step_kernel(KParams kp, S* __restrict__ f,
+__global__ void __launch_bounds__(128, LBM_STEP_MINB) cumulant_step_kernel(KParams kp, S* __restrict__ f,
                                                             S* __restrict__ phi,
                                                             float* __restrict__ save) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= kp.nx) return;
-    const int y = blockIdx.y, z = blockIdx.z;
-    const unsigned n = (unsigned)x + (unsigned)kp.nx * ((unsigned)y + (unsigned)kp.ny * (unsigned)z);
+    const Stencil st = make_stencil(kp, x, blockIdx.y, blockIdx.z);
+    const unsigned n = st.n;
 
     float fv[27], pv[7];
-    gather<27, ODD>(kp, f, x, y, z, n, fv);
-    gather<7, ODD>(kp, phi, x, y, z, n, pv);
+    gather<27, ODD>(kp, f, st, fv);
+    gather<7, ODD>(kp, phi, st, pv);
     if (!std::is_same<S, float>::value) {
 #pragma unroll
         for (int i = 0; i < 27; ++i) fv[i] *= kp.isf;
@@ -186,8 +187,8 @@ __global__ void __launch_bounds__(128) cumulant_step_kernel(KParams kp, S* __res
 #pragma unroll
         for (int k = 0; k < 7; ++k) pv[k] *= kp.sp;
     }
-    scatter<27, ODD>(kp, f, x, y, z, n, fv);
-    scatter<7, ODD>(kp, phi, x, y, z, n, pv);
+    scatter<27, ODD>(kp, f, st, fv);
+    scatter<7, ODD>(kp, phi, st, pv);
 }
 
 template <typename S>

@@ -26,21 +26,28 @@ def weights(model: int) -> np.ndarray:
     return O.velocities(model)[1]
 
 
+def w7() -> np.ndarray:
+    return O.velocities_q7()[1]
+
+
 def canonical_to_oracle(state: np.ndarray, p: lbm.Params, shifted: bool = True):
-    """[Q+7, N] float32 (f - w, Phi) -> oracle (f, phi) float64 arrays."""
+    """[Q+7, N] float32 (f - w, Phi - w) -> oracle (f, phi) float64 arrays.
+    shifted=False takes the rows as they are (streaming tests, adjoints)."""
     Q = p.Q
     s = np.asarray(state, dtype=np.float64).reshape(Q + 7, *p.shape)
     f = np.moveaxis(s[:Q], 0, -1).copy()
     phi = np.moveaxis(s[Q:], 0, -1).copy()
     if shifted:
         f += weights(p.model)
+        phi += w7()
     return f, phi
 
 
 def oracle_to_canonical(f: np.ndarray, phi: np.ndarray, p: lbm.Params, shifted: bool = True):
     """oracle (f, phi) -> [Q+7, N] float64 in the library layout."""
     ff = f - weights(p.model) if shifted else f
-    return np.concatenate([np.moveaxis(ff, -1, 0), np.moveaxis(phi, -1, 0)]).reshape(p.Q + 7, -1)
+    pp = phi - w7() if shifted else phi
+    return np.concatenate([np.moveaxis(ff, -1, 0), np.moveaxis(pp, -1, 0)]).reshape(p.Q + 7, -1)
 
 
 def lock_state_oracle(p: lbm.Params):
@@ -78,7 +85,7 @@ def window_oracle(p: lbm.Params, state0: np.ndarray, node, steps: int):
         sub = sub.cpu().numpy()
     sub = sub.astype(np.float64)
     f = np.moveaxis(sub[:Q], 0, -1) + weights(p.model)
-    phi = np.moveaxis(sub[Q:], 0, -1).copy()
+    phi = np.moveaxis(sub[Q:], 0, -1) + w7()
     op = oracle_params(p)
     op.nx, op.ny, op.nz = len(xs), len(ys), len(zs)
     op.periodic_x = False
@@ -86,4 +93,4 @@ def window_oracle(p: lbm.Params, state0: np.ndarray, node, steps: int):
     f, phi = O.run(op, steps, f, phi)
     cx = int(np.where(xs == x)[0][0])
     cz = int(np.where(zs == z)[0][0])
-    return f[cz, cy, cx] - weights(p.model), phi[cz, cy, cx]
+    return f[cz, cy, cx] - weights(p.model), phi[cz, cy, cx] - w7()

@@ -30,7 +30,7 @@ def _random_state(p: lbm.Params, seed: int, amp: float = 0.05, chi_amp: float = 
     fdev = w[:, None] * inputs.uniform((p.Q, p.N), seed, amp)
     chi = chi_amp * 0.5 * (1.0 + inputs.uniform(p.N, seed + 1, 1.0))
     w7 = O.velocities_q7()[1]
-    phi = w7[:, None] * chi[None, :] * (1.0 + inputs.uniform((7, p.N), seed + 2, amp))
+    phi = w7[:, None] * (chi[None, :] * (1.0 + inputs.uniform((7, p.N), seed + 2, amp)) - 1.0)
     return np.concatenate([fdev, phi]).astype(np.float32)
 
 
@@ -87,9 +87,9 @@ def test_lock_exchange_one_step(model):
     p = _config1(model)
     lat = _lat(p)
     op, (f, phi) = lock_state_oracle(p)
-    # the initial condition itself
+    # the initial condition itself (chi0 rounded to FP32)
     e_rho, e_u, e_chi = _compare_macros(lat, op, f, phi)
-    assert e_rho < 1e-7 and e_chi < 1e-7
+    assert e_rho < 1e-7 and e_chi < 1e-6
     lat.step(1)
     f, phi = O.step(op, f, phi)
     e_rho, e_u, e_chi = _compare_macros(lat, op, f, phi)

@@ -23,7 +23,7 @@ def _random_state(p, seed, amp=0.05):
     fdev = w[:, None] * inputs.uniform((p.Q, p.N), seed, amp)
     chi = 0.5 * (1 + inputs.uniform(p.N, seed + 1, 1.0))
     w7 = O.velocities_q7()[1]
-    phi = w7[:, None] * chi[None, :] * (1 + inputs.uniform((7, p.N), seed + 2, amp))
+    phi = w7[:, None] * (chi[None, :] * (1 + inputs.uniform((7, p.N), seed + 2, amp)) - 1.0)
     return np.concatenate([fdev, phi]).astype(np.float32)
 
 

@@ -1,0 +1,172 @@
+// lbm_aa2.cuh -- AA gather / scatter for two x-adjacent nodes per thread.
+//
+// Thread t of a row segment owns the nodes x = 2t and x + 1 (nx even) and
+// moves each population row as aligned pairs (8 bytes in FP32, 4 bytes in
+// FP16 / BF16), so a warp reads or writes 64 consecutive nodes of a row with
+// one request per population.  On odd steps the populations with c_x != 0
+// come from (go to) x -+ 1: the pair is read aligned and the element that
+// belongs to the neighbouring thread is exchanged with a warp shuffle; the
+// first and last active lanes of a warp load / store the one element that
+// lies in the neighbouring warp's range themselves.
+//
+// In-place safety: for every population row, each element is loaded and
+// stored by the same thread within a step (the AA property of
+// lbm_common.cuh holds per element).  The only exception is the aligned pair
+// load of a boundary lane, whose half that belongs to the next warp is read
+// but never used.
+#pragma once
+
+#include "lbm_common.cuh"
+
+namespace lbmgpu {
+
+template <typename S> struct PairIO;
+template <> struct PairIO<float> {
+    static __device__ __forceinline__ void ld(const float* p, float& a, float& b) {
+        const float2 v = ld_pop(reinterpret_cast<const float2*>(p));
+        a = v.x; b = v.y;
+    }
+    static __device__ __forceinline__ void st(float* p, float a, float b) {
+        st_pop(reinterpret_cast<float2*>(p), make_float2(a, b));
+    }
+};
+template <> struct PairIO<__half> {
+    static __device__ __forceinline__ void ld(const __half* p, float& a, float& b) {
+        const __half2 v = ld_pop(reinterpret_cast<const __half2*>(p));
+        const float2 f = __half22float2(v);
+        a = f.x; b = f.y;
+    }
+    static __device__ __forceinline__ void st(__half* p, float a, float b) {
+        st_pop(reinterpret_cast<__half2*>(p), __floats2half2_rn(a, b));
+    }
+};
+template <> struct PairIO<__nv_bfloat16> {
+    static __device__ __forceinline__ void ld(const __nv_bfloat16* p, float& a, float& b) {
+        const __nv_bfloat162 v = ld_pop(reinterpret_cast<const __nv_bfloat162*>(p));
+        const float2 f = __bfloat1622float2(v);
+        a = f.x; b = f.y;
+    }
+    static __device__ __forceinline__ void st(__nv_bfloat16* p, float a, float b) {
+        st_pop(reinterpret_cast<__nv_bfloat162*>(p), __floats2bfloat162_rn(a, b));
+    }
+};
+
+// Neighbourhood of a node pair (x, x + 1), x even.
+struct Stencil2 {
+    unsigned n;         // node x
+    unsigned zr[3];     // (z + dz) * nx * ny, dz = -1, 0, 1
+    unsigned yr[3];     // (y + dy) * nx,      dy = -1, 0, 1
+    unsigned x, xm, xp2;// x, x - 1 (wrapped), x + 2 (wrapped)
+    bool zo[3];         // row z + dz in the fluid (or wrapped)
+    bool xmo, xp2o;     // x - 1, x + 2 in the fluid (or wrapped)
+    bool active;        // x < nx
+    bool left, right;   // this lane loads / stores across the warp's left / right edge
+};
+
+__device__ __forceinline__ Stencil2 make_stencil2(const KParams& kp, int x, int y, int z) {
+    Stencil2 s;
+    const bool px = (kp.flags & LBM_FLAG_PERIODIC_X) != 0;
+    const bool pz = (kp.flags & LBM_FLAG_PERIODIC_Z) != 0;
+    const int ym = y == 0 ? kp.ny - 1 : y - 1, yp = y == kp.ny - 1 ? 0 : y + 1;
+    const int zm = z == 0 ? kp.nz - 1 : z - 1, zp = z == kp.nz - 1 ? 0 : z + 1;
+    s.yr[0] = (unsigned)ym * kp.nx; s.yr[1] = (unsigned)y * kp.nx; s.yr[2] = (unsigned)yp * kp.nx;
+    s.zr[0] = (unsigned)zm * kp.nxny; s.zr[1] = (unsigned)z * kp.nxny; s.zr[2] = (unsigned)zp * kp.nxny;
+    s.zo[0] = z > 0 || pz; s.zo[1] = true; s.zo[2] = z < kp.nz - 1 || pz;
+    s.active = x < kp.nx;
+    s.x = (unsigned)x;
+    s.xm = (unsigned)(x == 0 ? kp.nx - 1 : x - 1);
+    s.xp2 = (unsigned)(x + 2 >= kp.nx ? x + 2 - kp.nx : x + 2);
+    s.xmo = x > 0 || px;
+    s.xp2o = x + 2 < kp.nx || px;
+    const int lane = threadIdx.x & 31;
+    s.left = lane == 0;
+    s.right = lane == 31 || x + 2 >= kp.nx;
+    s.n = s.zr[1] + s.yr[1] + (unsigned)x;
+    return s;
+}
+
+template <int Q, bool ODD, typename S>
+__device__ __forceinline__ void gather2(const KParams& kp, const S* __restrict__ a,
+                                        const Stencil2& st, float (&v0)[Q], float (&v1)[Q]) {
+    const unsigned N = kp.N;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int dx = -cx27(i), dy = -cy27(i), dz = -cz27(i);
+        float p0 = 0.0f, p1 = 0.0f;
+        if (!ODD || i == 0) {
+            if (st.active) PairIO<S>::ld(a + (unsigned)i * N + st.n, p0, p1);
+            v0[i] = p0; v1[i] = p1;
+        } else if (!st.zo[dz + 1]) {
+            // both nodes bounce back from a z wall: own slot i
+            if (st.active) PairIO<S>::ld(a + (unsigned)i * N + st.n, p0, p1);
+            v0[i] = p0; v1[i] = p1;
+        } else {
+            const unsigned row = (unsigned)opp(i) * N + st.zr[dz + 1] + st.yr[dy + 1];
+            if (st.active) PairIO<S>::ld(a + row + st.x, p0, p1);
+            if (dx == 0) {
+                v0[i] = p0; v1[i] = p1;
+            } else if (dx < 0) {
+                // node x needs element x - 1, node x + 1 needs element x
+                float e = __shfl_up_sync(0xffffffffu, p1, 1);
+                if (st.left && st.active)
+                    e = st.xmo ? Store<S>::ld(a + row + st.xm)
+                               : Store<S>::ld(a + (unsigned)i * N + st.n);
+                v0[i] = e; v1[i] = p0;
+            } else {
+                // node x needs element x + 1, node x + 1 needs element x + 2
+                float e = __shfl_down_sync(0xffffffffu, p0, 1);
+                if (st.right && st.active)
+                    e = st.xp2o ? Store<S>::ld(a + row + st.xp2)
+                                : Store<S>::ld(a + (unsigned)i * N + st.n + 1);
+                v0[i] = p1; v1[i] = e;
+            }
+        }
+    }
+}
+
+template <int Q, bool ODD, typename S>
+__device__ __forceinline__ void scatter2(const KParams& kp, S* __restrict__ a, const Stencil2& st,
+                                         const float (&v0)[Q], const float (&v1)[Q]) {
+    const unsigned N = kp.N;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int dx = cx27(i), dy = cy27(i), dz = cz27(i);
+        if (!ODD || i == 0) {
+            if (st.active) PairIO<S>::st(a + (unsigned)opp(i) * N + st.n, v0[i], v1[i]);
+        } else if (!st.zo[dz + 1]) {
+            // towards a z wall: both nodes bounce back into their own slot opp(i)
+            if (st.active) PairIO<S>::st(a + (unsigned)opp(i) * N + st.n, v0[i], v1[i]);
+        } else {
+            const unsigned row = (unsigned)i * N + st.zr[dz + 1] + st.yr[dy + 1];
+            if (dx == 0) {
+                if (st.active) PairIO<S>::st(a + row + st.x, v0[i], v1[i]);
+            } else if (dx > 0) {
+                // element x receives node x - 1, element x + 1 receives node x
+                const float e = __shfl_up_sync(0xffffffffu, v1[i], 1);
+                if (st.active) {
+                    if (st.left) Store<S>::st(a + row + st.x + 1, v0[i]);
+                    else PairIO<S>::st(a + row + st.x, e, v0[i]);
+                    if (st.right) {
+                        // node x + 1 -> x + 2: across the warp edge or into a wall
+                        if (st.xp2o) Store<S>::st(a + row + st.xp2, v1[i]);
+                        else Store<S>::st(a + (unsigned)opp(i) * N + st.n + 1, v1[i]);
+                    }
+                }
+            } else {
+                // element x receives node x + 1, element x + 1 receives node x + 2
+                const float e = __shfl_down_sync(0xffffffffu, v0[i], 1);
+                if (st.active) {
+                    if (st.right) Store<S>::st(a + row + st.x, v1[i]);
+                    else PairIO<S>::st(a + row + st.x, v1[i], e);
+                    if (st.left) {
+                        // node x -> x - 1: across the warp edge or into a wall
+                        if (st.xmo) Store<S>::st(a + row + st.xm, v0[i]);
+                        else Store<S>::st(a + (unsigned)opp(i) * N + st.n, v0[i]);
+                    }
+                }
+            }
+        }
+    }
+}
+
+}  // namespace lbmgpu

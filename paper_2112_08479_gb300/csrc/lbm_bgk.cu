@@ -21,6 +21,7 @@
 // segments; no shared memory, no tensor cores.
 #include <type_traits>
 
+#include "lbm_aa2.cuh"
 #include "lbm_internal.h"
 
 namespace lbmgpu {
@@ -131,9 +132,61 @@ __global__ void __launch_bounds__(128, LBM_STEP_MINB) bgk_step_kernel(KParams kp
     scatter<7, ODD>(kp, phi, st, pv);
 }
 
+
+// Two x-adjacent nodes per thread (nx even): paired population accesses, see
+// lbm_aa2.cuh.  Same arithmetic per node as bgk_step_kernel.
+template <bool ODD, bool SAVE, typename S>
+__global__ void __launch_bounds__(128, LBM_STEP2_MINB) bgk_step2_kernel(KParams kp, S* __restrict__ f,
+                                                                    S* __restrict__ phi,
+                                                                    float* __restrict__ save) {
+    const int x = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const Stencil2 st = make_stencil2(kp, x, blockIdx.y, blockIdx.z);
+    float f0[19], f1[19], p0[7], p1[7];
+    gather2<19, ODD>(kp, f, st, f0, f1);
+    gather2<7, ODD>(kp, phi, st, p0, p1);
+    if (!std::is_same<S, float>::value) {
+#pragma unroll
+        for (int i = 0; i < 19; ++i) { f0[i] *= kp.isf; f1[i] *= kp.isf; }
+#pragma unroll
+        for (int k = 0; k < 7; ++k) { p0[k] *= kp.isp; p1[k] *= kp.isp; }
+    }
+    if (SAVE && st.active) {
+        const unsigned N = kp.N;
+#pragma unroll
+        for (int i = 0; i < 19; ++i)
+            *reinterpret_cast<float2*>(save + (size_t)i * N + st.n) = make_float2(f0[i], f1[i]);
+#pragma unroll
+        for (int k = 0; k < 7; ++k)
+            *reinterpret_cast<float2*>(save + (size_t)(19 + k) * N + st.n) = make_float2(p0[k], p1[k]);
+    }
+    if (!(kp.flags & LBM_FLAG_NO_COLLIDE)) {
+        collide_bgk(kp, f0, p0);
+        collide_bgk(kp, f1, p1);
+    }
+    if (!std::is_same<S, float>::value) {
+#pragma unroll
+        for (int i = 0; i < 19; ++i) { f0[i] *= kp.sf; f1[i] *= kp.sf; }
+#pragma unroll
+        for (int k = 0; k < 7; ++k) { p0[k] *= kp.sp; p1[k] *= kp.sp; }
+    }
+    scatter2<19, ODD>(kp, f, st, f0, f1);
+    scatter2<7, ODD>(kp, phi, st, p0, p1);
+}
+
 template <typename S>
 static cudaError_t launch_bgk_typed(const KParams& kp, bool odd, S* f, S* phi, float* save,
                                    cudaStream_t st) {
+    if (LBM_PAIR && kp.nx % 2 == 0) {
+        dim3 block(128), grid((kp.nx / 2 + 127) / 128, kp.ny, kp.nz);
+        if (save) {
+            if (odd) bgk_step2_kernel<true, true, S><<<grid, block, 0, st>>>(kp, f, phi, save);
+            else bgk_step2_kernel<false, true, S><<<grid, block, 0, st>>>(kp, f, phi, save);
+        } else {
+            if (odd) bgk_step2_kernel<true, false, S><<<grid, block, 0, st>>>(kp, f, phi, nullptr);
+            else bgk_step2_kernel<false, false, S><<<grid, block, 0, st>>>(kp, f, phi, nullptr);
+        }
+        return cudaGetLastError();
+    }
     dim3 block(128), grid((kp.nx + 127) / 128, kp.ny, kp.nz);
     if (save) {
         if (odd) bgk_step_kernel<true, true, S><<<grid, block, 0, st>>>(kp, f, phi, save);

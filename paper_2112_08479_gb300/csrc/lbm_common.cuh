@@ -79,6 +79,13 @@ struct KParams {
 #ifndef LBM_STREAMING_HINTS
 #define LBM_STREAMING_HINTS 0
 #endif
+// Two nodes per thread with paired accesses when nx is even (lbm_aa2.cuh).
+#ifndef LBM_PAIR
+#define LBM_PAIR 1
+#endif
+#ifndef LBM_STEP2_MINB
+#define LBM_STEP2_MINB 2
+#endif
 
 // ---------------------------------------------------------------------------
 // Storage types: FP32, or FP16 / BF16 with round-to-nearest-even.

@@ -98,23 +98,43 @@ def test_checkpoint_interval_does_not_change_gradient():
     assert torch.equal(grads[0], grads[1]) and torch.equal(grads[1], grads[2])
 
 
-@pytest.mark.parametrize("seed", [1, 2, 3, 4])
-def test_gradient_vs_central_differences_full_box(seed):
-    """256 x 32 x 64, 2000 steps, K = 100: directional derivative vs central
-    differences of the FP32 forward (J accumulated in FP64)."""
+def test_gradient_vs_central_differences_full_box():
+    """256 x 32 x 64, 2000 steps, K = 100: the adjoint's directional
+    derivatives on 32 seeded unit directions against central differences of
+    the FP32 forward (J accumulated in FP64), and dJ/dC_s.
+
+    The FP32 forward carries round-off noise of a few 1e-8 relative in J; a
+    step of 1.6e-2 per node (eps = 1.6e-2 sqrt(N) along a unit direction)
+    keeps its effect on the difference quotient below 1e-4 of the projected
+    gradient.  Bar: the 32-vector of directional derivatives within 1e-3
+    (relative 2-norm); each direction within 1e-2 of its own value."""
     p = lbm.lock_exchange(256, 32, 64, H=64, x0=64, u_b=0.03, Re=2000.0)
     nsteps = 2000
     lat = lbm.Lattice(p, device="cuda")
-    rho, u, chi = lat.macros()
-    chi0 = chi.reshape(-1).clone()
+    chi0 = lat.macros()[2].reshape(-1).clone()
+    del lat
     x = chi0.clone().requires_grad_(True)
-    friction_objective(x, p.cs_smag, p, nsteps, K=100).backward()
-    d = torch.tensor(inputs.unit_direction(p.N, seed), dtype=torch.float32, device="cuda")
-    eps = 1e-3 * np.sqrt(p.N)
+    cs = torch.tensor(p.cs_smag, dtype=torch.float64, device="cuda", requires_grad=True)
+    friction_objective(x, cs, p, nsteps, K=100).backward()
+    g = x.grad.double()
 
-    def J(c):
-        return friction_objective(c, p.cs_smag, p, nsteps, K=100).item()
+    def J(c, csv=p.cs_smag):
+        with torch.no_grad():
+            return friction_objective(c, csv, p, nsteps, K=100).item()
 
-    fd = (J(chi0 + eps * d) - J(chi0 - eps * d)) / (2 * eps)
-    ad = float((x.grad.double() * d.double()).sum())
-    assert ad == pytest.approx(fd, rel=1e-3), (ad, fd)
+    eps = 1.6e-2 * np.sqrt(p.N)
+    ad, fd = [], []
+    for seed in range(1, 33):
+        d = torch.tensor(inputs.unit_direction(p.N, seed), dtype=torch.float32, device="cuda")
+        ad.append(float((g * d.double()).sum()))
+        fd.append((J(chi0 + eps * d) - J(chi0 - eps * d)) / (2 * eps))
+    ad, fd = np.array(ad), np.array(fd)
+    rel = np.linalg.norm(ad - fd) / np.linalg.norm(fd)
+    per = np.abs(ad - fd) / np.abs(fd)
+    print(f"32 directions: relative 2-norm error {rel:.2e}, median per-direction {np.median(per):.2e}, "
+          f"max {per.max():.2e}")
+    assert rel < 1e-3
+    assert per.max() < 1e-2
+    h = 1e-3
+    fd_cs = (J(chi0, p.cs_smag + h) - J(chi0, p.cs_smag - h)) / (2 * h)
+    assert cs.grad.item() == pytest.approx(fd_cs, rel=1e-4)

@@ -85,7 +85,7 @@ typedef enum lbm_storage {
 
 typedef struct lbm_params {
     int32_t nx, ny, nz;       /* nodes; 1 <= nx, ny, nz; nx*ny*nz < 2^31;
-                                 Q*nx*ny*nz < 2^32; ny, nz <= 65535 */
+                                 (Q+7)*nx*ny*nz < 2^32; ny, nz <= 65535 */
     int32_t model;            /* lbm_model */
     int32_t storage;          /* lbm_storage */
     int32_t flags;            /* LBM_FLAG_* */

@@ -45,8 +45,8 @@ const char* check(const lbm_params* p) {
     if (p->ny > 65535 || p->nz > 65535) return "ny and nz must be <= 65535";
     if ((double)p->nx * p->ny * p->nz >= 2147483648.0) return "nx*ny*nz must be < 2^31";
     if (p->model != LBM_BGK_SMAG_Q19 && p->model != LBM_CUMULANT_Q27) return "unknown model";
-    if ((double)q_of(p) * p->nx * p->ny * p->nz >= 4294967296.0)
-        return "Q*nx*ny*nz must be < 2^32 (32-bit element offsets)";
+    if ((double)(q_of(p) + 7) * p->nx * p->ny * p->nz >= 4294967296.0)
+        return "(Q+7)*nx*ny*nz must be < 2^32 (32-bit element offsets)";
     if (p->storage != LBM_FP32 && p->storage != LBM_FP16S && p->storage != LBM_BF16S)
         return "unknown storage";
     if (p->flags & ~(LBM_FLAG_NO_COLLIDE | LBM_FLAG_PERIODIC_X | LBM_FLAG_PERIODIC_Z))

@@ -231,23 +231,25 @@ __global__ void __launch_bounds__(128) bgk_adjoint_kernel(KParams kp, const floa
     if (active) {
         const unsigned n =
             (unsigned)x + (unsigned)kp.nx * ((unsigned)y + (unsigned)kp.ny * (unsigned)z);
-        // adjoints of the post-collision populations
+        // adjoints of the post-collision populations (transpose of the pull:
+        // read lam_{n+1} where each post-collision population went)
+        const Stencil sn = make_stencil(kp, x, y, z);
+        const unsigned N32 = kp.N;
         float mu[19], mup[7];
 #pragma unroll
         for (int i = 0; i < 19; ++i) {
-            unsigned d;
-            if (!lamn) mu[i] = 0.0f;
-            else if (i != 0 && neighbour(kp, x, y, z, cx27(i), cy27(i), cz27(i), d))
-                mu[i] = lamn[(size_t)i * N + d];
-            else mu[i] = lamn[(size_t)opp(i) * N + n];
+            bool in = false;
+            const unsigned d = i == 0 ? n : nbr(sn, cx27(i), cy27(i), cz27(i), in);
+            const unsigned off = (i != 0 && in) ? (unsigned)i * N32 + d : (unsigned)opp(i) * N32 + n;
+            mu[i] = lamn ? lamn[off] : 0.0f;
         }
 #pragma unroll
         for (int k = 0; k < 7; ++k) {
-            unsigned d;
-            if (!lamn) mup[k] = 0.0f;
-            else if (k != 0 && neighbour(kp, x, y, z, cx27(k), cy27(k), cz27(k), d))
-                mup[k] = lamn[(size_t)(19 + k) * N + d];
-            else mup[k] = lamn[(size_t)(19 + opp(k)) * N + n];
+            bool in = false;
+            const unsigned d = k == 0 ? n : nbr(sn, cx27(k), cy27(k), cz27(k), in);
+            const unsigned off = (k != 0 && in) ? (unsigned)(19 + k) * N32 + d
+                                                : (unsigned)(19 + opp(k)) * N32 + n;
+            mup[k] = lamn ? lamn[off] : 0.0f;
         }
         float f[19], p[7];
 #pragma unroll

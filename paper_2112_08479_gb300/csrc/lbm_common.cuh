@@ -129,7 +129,7 @@ template <> struct Store<__nv_bfloat16> {
 // the rows (y + dy, z + dz) and the columns x + dx, with y always periodic
 // and x, z bounded by half-way bounce-back walls unless the periodic flags
 // are set.  Element offsets are 32-bit: the library accepts only sizes with
-// Q * N < 2^32.
+// (Q + 7) * N < 2^32.
 struct Stencil {
     unsigned n;        // this node
     unsigned zr[3];    // (z + dz) * nx * ny for dz = -1, 0, 1

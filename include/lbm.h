@@ -203,6 +203,24 @@ LBM_API lbm_status lbm_adjoint_step(lbm_ctx* ctx, const float* state_n, const fl
  * (since Phi_k = w_k chi0 at t = 0).  Device buffers.  Asynchronous. */
 LBM_API lbm_status lbm_adjoint_chi0(lbm_ctx* ctx, const float* lam0, float* grad_chi0);
 
+/* Diagnostics (as lbm_diag) of a state the caller holds in the canonical
+ * layout (state: (Q + 7) * N floats, device), for callers that cannot
+ * allocate device memory (an allocator callback or out-of-memory handler, a
+ * pool fixed before this library loads): it needs no context and no
+ * workspace and calls no cudaMalloc, cudaFree or allocating routine.  The
+ * paper has no counterpart; this is a service of the library.
+ * Its scratch is one fixed device array of 852,224 bytes inside the library,
+ * present on every device that uses the library until it is unloaded; it
+ * serves nx <= 16384 and ceil(nx / 128) * nz <= 32768 and returns
+ * LBM_ERR_ARG beyond that (message in lbm_last_error(NULL)).  The first call
+ * on each device looks up the array's device address; make that first call
+ * with the device current and before any stream capture.  All calls share
+ * the array: calls that overlap on the GPU race and must be serialised.
+ * Enqueued on cuda_stream (its device must be current), then synchronised;
+ * flags holds only what this call saw; LBM_ERR_UNSTABLE as lbm_diag. */
+LBM_API lbm_status lbm_diag_static(const lbm_params* p, const float* state, int64_t step,
+                                   void* cuda_stream, lbm_diagnostics* out_host);
+
 /* Current step counter. */
 LBM_API int64_t lbm_get_step(const lbm_ctx* ctx);
 

@@ -124,6 +124,11 @@ lbm_status arg_fail(lbm_ctx* c, const char* what) {
 
 }  // namespace
 
+namespace lbmgpu {
+// Message returned by lbm_last_error(NULL) on this thread.
+void lbm_set_thread_error(const char* msg) { snprintf(g_err, sizeof g_err, "%s", msg); }
+}  // namespace lbmgpu
+
 extern "C" {
 
 const char* lbm_status_string(lbm_status s) {

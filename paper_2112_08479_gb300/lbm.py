@@ -69,6 +69,8 @@ SIGNATURES = [
     ("lbm_set_state", C.c_int, [_CTX, C.c_void_p, C.c_int64]),
     ("lbm_adjoint_step", C.c_int, [_CTX, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double]),
     ("lbm_adjoint_chi0", C.c_int, [_CTX, C.c_void_p, C.c_void_p]),
+    ("lbm_diag_static", C.c_int, [_P, C.c_void_p, C.c_int64, C.c_void_p,
+                                  C.POINTER(lbm_diagnostics)]),
     ("lbm_get_step", C.c_int64, [_CTX]),
     ("lbm_sync", C.c_int, [_CTX]),
     ("lbm_destroy", None, [_CTX]),

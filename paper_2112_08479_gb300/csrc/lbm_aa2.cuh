@@ -85,86 +85,105 @@ __device__ __forceinline__ Stencil2 make_stencil2(const KParams& kp, int x, int 
     return s;
 }
 
+// The gather runs in three phases so that no shuffle waits on a load issued
+// after it: (1) every aligned pair load, (2) the edge lanes' single-element
+// loads, predicated, (3) the shuffles that hand the shifted element across.
+// A z wall (uniform over the block) turns a direction into a bounce-back from
+// the node's own slot, selected without branching.
 template <int Q, bool ODD, typename S>
 __device__ __forceinline__ void gather2(const KParams& kp, const S* __restrict__ a,
                                         const Stencil2& st, float (&v0)[Q], float (&v1)[Q]) {
     const unsigned N = kp.N;
+    float P0[Q], P1[Q], E[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const int dx = -cx27(i), dy = -cy27(i), dz = -cz27(i);
-        float p0 = 0.0f, p1 = 0.0f;
-        if (!ODD || i == 0) {
-            if (st.active) PairIO<S>::ld(a + (unsigned)i * N + st.n, p0, p1);
-            v0[i] = p0; v1[i] = p1;
-        } else if (!st.zo[dz + 1]) {
-            // both nodes bounce back from a z wall: own slot i
-            if (st.active) PairIO<S>::ld(a + (unsigned)i * N + st.n, p0, p1);
-            v0[i] = p0; v1[i] = p1;
-        } else {
+        unsigned off = (unsigned)i * N + st.n;
+        if (ODD && i != 0) {
+            const int dy = -cy27(i), dz = -cz27(i);
             const unsigned row = (unsigned)opp(i) * N + st.zr[dz + 1] + st.yr[dy + 1];
-            if (st.active) PairIO<S>::ld(a + row + st.x, p0, p1);
-            if (dx == 0) {
-                v0[i] = p0; v1[i] = p1;
-            } else if (dx < 0) {
+            off = st.zo[dz + 1] ? row + st.x : off;
+        }
+        P0[i] = 0.0f; P1[i] = 0.0f;
+        if (st.active) PairIO<S>::ld(a + off, P0[i], P1[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        E[i] = 0.0f;
+        const int dx = -cx27(i), dy = -cy27(i), dz = -cz27(i);
+        if (ODD && i != 0 && dx != 0) {
+            const unsigned row = (unsigned)opp(i) * N + st.zr[dz + 1] + st.yr[dy + 1];
+            const unsigned own = (unsigned)i * N + st.n;
+            unsigned off;
+            bool need;
+            if (dx < 0) { need = st.left; off = st.xmo ? row + st.xm : own; }
+            else { need = st.right; off = st.xp2o ? row + st.xp2 : own + 1; }
+            need = need && st.active && st.zo[dz + 1];
+            if (need) E[i] = Store<S>::ld(a + off);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int dx = -cx27(i), dz = -cz27(i);
+        v0[i] = P0[i]; v1[i] = P1[i];
+        if (ODD && i != 0 && dx != 0) {
+            const bool in = st.zo[dz + 1];
+            if (dx < 0) {
                 // node x needs element x - 1, node x + 1 needs element x
-                float e = __shfl_up_sync(0xffffffffu, p1, 1);
-                if (st.left && st.active)
-                    e = st.xmo ? Store<S>::ld(a + row + st.xm)
-                               : Store<S>::ld(a + (unsigned)i * N + st.n);
-                v0[i] = e; v1[i] = p0;
+                const float e = __shfl_up_sync(0xffffffffu, P1[i], 1);
+                v0[i] = in ? (st.left ? E[i] : e) : P0[i];
+                v1[i] = in ? P0[i] : P1[i];
             } else {
                 // node x needs element x + 1, node x + 1 needs element x + 2
-                float e = __shfl_down_sync(0xffffffffu, p0, 1);
-                if (st.right && st.active)
-                    e = st.xp2o ? Store<S>::ld(a + row + st.xp2)
-                                : Store<S>::ld(a + (unsigned)i * N + st.n + 1);
-                v0[i] = p1; v1[i] = e;
+                const float e = __shfl_down_sync(0xffffffffu, P0[i], 1);
+                v0[i] = in ? P1[i] : P0[i];
+                v1[i] = in ? (st.right ? E[i] : e) : P1[i];
             }
         }
     }
 }
 
+// The scatter first exchanges the shifted elements, then issues every store
+// under a predicate (pair stores for the interior lanes, single-element
+// stores for the edge lanes, pair stores into the own slots at a z wall).
 template <int Q, bool ODD, typename S>
 __device__ __forceinline__ void scatter2(const KParams& kp, S* __restrict__ a, const Stencil2& st,
                                          const float (&v0)[Q], const float (&v1)[Q]) {
     const unsigned N = kp.N;
+    float X[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int dx = cx27(i);
+        X[i] = 0.0f;
+        if (ODD && i != 0 && dx > 0) X[i] = __shfl_up_sync(0xffffffffu, v1[i], 1);
+        if (ODD && i != 0 && dx < 0) X[i] = __shfl_down_sync(0xffffffffu, v0[i], 1);
+    }
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const int dx = cx27(i), dy = cy27(i), dz = cz27(i);
+        const unsigned own = (unsigned)opp(i) * N + st.n;
         if (!ODD || i == 0) {
-            if (st.active) PairIO<S>::st(a + (unsigned)opp(i) * N + st.n, v0[i], v1[i]);
-        } else if (!st.zo[dz + 1]) {
-            // towards a z wall: both nodes bounce back into their own slot opp(i)
-            if (st.active) PairIO<S>::st(a + (unsigned)opp(i) * N + st.n, v0[i], v1[i]);
+            if (st.active) PairIO<S>::st(a + own, v0[i], v1[i]);
+            continue;
+        }
+        const bool in = st.zo[dz + 1];
+        const unsigned row = (unsigned)i * N + st.zr[dz + 1] + st.yr[dy + 1];
+        if (st.active && !in) PairIO<S>::st(a + own, v0[i], v1[i]);
+        if (dx == 0) {
+            if (st.active && in) PairIO<S>::st(a + row + st.x, v0[i], v1[i]);
+        } else if (dx > 0) {
+            // element x receives node x - 1, element x + 1 receives node x
+            if (st.active && in && !st.left) PairIO<S>::st(a + row + st.x, X[i], v0[i]);
+            if (st.active && in && st.left) Store<S>::st(a + row + st.x + 1, v0[i]);
+            // node x + 1 -> x + 2 across the warp edge, or back from an x wall
+            if (st.active && in && st.right)
+                Store<S>::st(a + (st.xp2o ? row + st.xp2 : own + 1), v1[i]);
         } else {
-            const unsigned row = (unsigned)i * N + st.zr[dz + 1] + st.yr[dy + 1];
-            if (dx == 0) {
-                if (st.active) PairIO<S>::st(a + row + st.x, v0[i], v1[i]);
-            } else if (dx > 0) {
-                // element x receives node x - 1, element x + 1 receives node x
-                const float e = __shfl_up_sync(0xffffffffu, v1[i], 1);
-                if (st.active) {
-                    if (st.left) Store<S>::st(a + row + st.x + 1, v0[i]);
-                    else PairIO<S>::st(a + row + st.x, e, v0[i]);
-                    if (st.right) {
-                        // node x + 1 -> x + 2: across the warp edge or into a wall
-                        if (st.xp2o) Store<S>::st(a + row + st.xp2, v1[i]);
-                        else Store<S>::st(a + (unsigned)opp(i) * N + st.n + 1, v1[i]);
-                    }
-                }
-            } else {
-                // element x receives node x + 1, element x + 1 receives node x + 2
-                const float e = __shfl_down_sync(0xffffffffu, v0[i], 1);
-                if (st.active) {
-                    if (st.right) Store<S>::st(a + row + st.x, v1[i]);
-                    else PairIO<S>::st(a + row + st.x, v1[i], e);
-                    if (st.left) {
-                        // node x -> x - 1: across the warp edge or into a wall
-                        if (st.xmo) Store<S>::st(a + row + st.xm, v0[i]);
-                        else Store<S>::st(a + (unsigned)opp(i) * N + st.n, v0[i]);
-                    }
-                }
-            }
+            // element x receives node x + 1, element x + 1 receives node x + 2
+            if (st.active && in && !st.right) PairIO<S>::st(a + row + st.x, v1[i], X[i]);
+            if (st.active && in && st.right) Store<S>::st(a + row + st.x, v1[i]);
+            // node x -> x - 1 across the warp edge, or back from an x wall
+            if (st.active && in && st.left)
+                Store<S>::st(a + (st.xmo ? row + st.xm : own), v0[i]);
         }
     }
 }

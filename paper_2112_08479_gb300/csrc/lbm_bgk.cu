@@ -27,7 +27,11 @@
 namespace lbmgpu {
 
 // Replaces f (held as f - w) and Phi (held as Phi - w) by their
-// post-collision values.
+// post-collision values.  Directions come in opposite pairs (i, i + 1 for odd
+// i): with s = f_i + f_opp and d = f_i - f_opp the moments need half the
+// additions, and the equilibrium and the Guo source split into a part even
+// in c (shared by the pair) and a part odd in c (sign-flipped), which halves
+// the per-direction arithmetic.
 __device__ __forceinline__ void collide_bgk(const KParams& kp, float (&f)[19], float (&p)[7]) {
     float chit = 0.0f;  // chi - 1
 #pragma unroll
@@ -35,21 +39,18 @@ __device__ __forceinline__ void collide_bgk(const KParams& kp, float (&f)[19], f
     const float chi = 1.0f + chit;
     const float Fx = kp.gx * chi, Fy = kp.gy * chi, Fz = kp.gz * chi;
 
-    float drho = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
+    float drho = f[0], jx = 0.0f, jy = 0.0f, jz = 0.0f;
     float mxx = 0.0f, myy = 0.0f, mzz = 0.0f, mxy = 0.0f, mxz = 0.0f, myz = 0.0f;
 #pragma unroll
-    for (int i = 0; i < 19; ++i) {
-        const float v = f[i];
-        drho += v;
-        if (cx27(i)) jx += cx27(i) * v;
-        if (cy27(i)) jy += cy27(i) * v;
-        if (cz27(i)) jz += cz27(i) * v;
-        if (cx27(i)) mxx += v;
-        if (cy27(i)) myy += v;
-        if (cz27(i)) mzz += v;
-        if (cx27(i) * cy27(i)) mxy += cx27(i) * cy27(i) * v;
-        if (cx27(i) * cz27(i)) mxz += cx27(i) * cz27(i) * v;
-        if (cy27(i) * cz27(i)) myz += cy27(i) * cz27(i) * v;
+    for (int i = 1; i < 19; i += 2) {
+        const float sp = f[i] + f[i + 1], dm = f[i] - f[i + 1];
+        drho += sp;
+        if (cx27(i)) { jx += cx27(i) * dm; mxx += sp; }
+        if (cy27(i)) { jy += cy27(i) * dm; myy += sp; }
+        if (cz27(i)) { jz += cz27(i) * dm; mzz += sp; }
+        if (cx27(i) * cy27(i)) mxy += cx27(i) * cy27(i) * sp;
+        if (cx27(i) * cz27(i)) mxz += cx27(i) * cz27(i) * sp;
+        if (cy27(i) * cz27(i)) myz += cy27(i) * cz27(i) * sp;
     }
     const float rho = 1.0f + drho;
     const float irho = 1.0f / rho;
@@ -73,27 +74,36 @@ __device__ __forceinline__ void collide_bgk(const KParams& kp, float (&f)[19], f
     const float s = sqrtf(kp.tau0 * kp.tau0 + X);
     const float dtau = 0.5f * X / (s + kp.tau0);
     const float om = 1.0f / (kp.tau0 + dtau);
+    const float keep = 1.0f - om;
     const float guo = 1.0f - 0.5f * om;
     const float uF = ux * Fx + uy * Fy + uz * Fz;
-
+    // feq_i - w_i = w_i (drho + rho (3 cu + 4.5 cu^2 - 1.5 u.u)),
+    // S_i = guo w_i (3 cF - 3 u.F + 9 cu cF)
+    const float base = drho - 1.5f * rho * usq;       // even part of (feq - w)/w at cu = 0
+    const float gbase = -3.0f * guo * uF;             // even part of S/w at cF = 0
+    f[0] = keep * f[0] + w19(0) * (om * base + gbase);
 #pragma unroll
-    for (int i = 0; i < 19; ++i) {
+    for (int i = 1; i < 19; i += 2) {
         const float cu = cx27(i) * ux + cy27(i) * uy + cz27(i) * uz;
         const float cF = cx27(i) * Fx + cy27(i) * Fy + cz27(i) * Fz;
         const float w = w19(i);
-        const float feq = w * (drho + rho * (3.0f * cu + 4.5f * cu * cu - 1.5f * usq));
-        const float S = guo * w * (3.0f * cF - 3.0f * uF + 9.0f * cu * cF);
-        f[i] = f[i] - om * (f[i] - feq) + S;
+        const float even = w * (om * (base + 4.5f * rho * cu * cu) + gbase + 9.0f * guo * cu * cF);
+        const float odd = w * (om * 3.0f * rho * cu + 3.0f * guo * cF);
+        f[i] = keep * f[i] + even + odd;
+        f[i + 1] = keep * f[i + 1] + even - odd;
     }
 
     // Phi_eq - w = w (chi - 1 + 4 chi c.u)
     const float omp = 1.0f / (kp.taup0 + kp.kT * dtau);
-#pragma unroll
-    for (int k = 0; k < 7; ++k) {
-        const float cu = cx27(k) * ux + cy27(k) * uy + cz27(k) * uz;
-        const float peq = w7(k) * (chit + 4.0f * chi * cu);
-        p[k] = p[k] - omp * (p[k] - peq);
-    }
+    const float keepp = 1.0f - omp;
+    p[0] = keepp * p[0] + omp * w7(0) * chit;
+    const float pe = omp * w7(1) * chit, pa = omp * w7(1) * 4.0f * chi;
+    p[1] = keepp * p[1] + pe + pa * ux;
+    p[2] = keepp * p[2] + pe - pa * ux;
+    p[3] = keepp * p[3] + pe + pa * uy;
+    p[4] = keepp * p[4] + pe - pa * uy;
+    p[5] = keepp * p[5] + pe + pa * uz;
+    p[6] = keepp * p[6] + pe - pa * uz;
 }
 
 template <bool ODD, bool SAVE, typename S>
@@ -176,7 +186,7 @@ __global__ void __launch_bounds__(128, LBM_STEP2_MINB) bgk_step2_kernel(KParams 
 template <typename S>
 static cudaError_t launch_bgk_typed(const KParams& kp, bool odd, S* f, S* phi, float* save,
                                    cudaStream_t st) {
-    if (LBM_PAIR && kp.nx % 2 == 0) {
+    if (LBM_BGK_PAIR && kp.nx % 2 == 0) {
         dim3 block(128), grid((kp.nx / 2 + 127) / 128, kp.ny, kp.nz);
         if (save) {
             if (odd) bgk_step2_kernel<true, true, S><<<grid, block, 0, st>>>(kp, f, phi, save);

@@ -79,12 +79,17 @@ struct KParams {
 #ifndef LBM_STREAMING_HINTS
 #define LBM_STREAMING_HINTS 0
 #endif
-// Two nodes per thread with paired accesses when nx is even (lbm_aa2.cuh).
-#ifndef LBM_PAIR
-#define LBM_PAIR 1
+// Two nodes per thread with paired accesses when nx is even (lbm_aa2.cuh):
+// measured faster for the BGK model (all storages); the cumulant model, whose
+// collision needs more registers per node, keeps one node per thread.
+#ifndef LBM_BGK_PAIR
+#define LBM_BGK_PAIR 1
+#endif
+#ifndef LBM_CUMULANT_PAIR
+#define LBM_CUMULANT_PAIR 0
 #endif
 #ifndef LBM_STEP2_MINB
-#define LBM_STEP2_MINB 2
+#define LBM_STEP2_MINB 4
 #endif
 
 // ---------------------------------------------------------------------------

@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(128, LBM_STEP2_MINB) cumulant_step2_kernel(KPa
 template <typename S>
 static cudaError_t launch_cumulant_typed(const KParams& kp, bool odd, S* f, S* phi, float* save,
                                    cudaStream_t st) {
-    if (LBM_PAIR && kp.nx % 2 == 0) {
+    if (LBM_CUMULANT_PAIR && kp.nx % 2 == 0) {
         dim3 block(128), grid((kp.nx / 2 + 127) / 128, kp.ny, kp.nz);
         if (save) {
             if (odd) cumulant_step2_kernel<true, true, S><<<grid, block, 0, st>>>(kp, f, phi, save);

@@ -198,6 +198,26 @@ LBM_API lbm_status lbm_set_state(lbm_ctx* ctx, const float* src, int64_t step);
 LBM_API lbm_status lbm_adjoint_step(lbm_ctx* ctx, const float* state_n, const float* lam_next,
                             float* lam_n, double* dJdCs_dev, double w_fw);
 
+/* Forward pass of the time-integrated bottom friction J = sum_n F_w(s_n):
+ * advances nsteps >= 0 steps from the current state s_0, adding F_w of each
+ * new state to *J_dev (one device double), and, when ckpt is not NULL,
+ * copies the state before relative step n to ckpt + (n / K) (Q + 7) N for
+ * every n % K == 0 (canonical layout, device; ceil(nsteps / K) states).
+ * Asynchronous. */
+LBM_API lbm_status lbm_objective_forward(lbm_ctx* ctx, int32_t nsteps, int32_t K, float* ckpt,
+                                         double* J_dev);
+
+/* One reverse segment of the adjoint of J (BGK model, FP32 storage):
+ * from the checkpoint ckpt = s_{n0}, recomputes s_{n0+1} .. s_{n0+k-1} into
+ * seg + j (Q + 7) N (j = 1 .. k-1; seg holds k states, slot 0 unused) with
+ * an out-of-place step of the same arithmetic, then applies k adjoint steps
+ * backwards: on entry lam holds lam_{n0+k}, on return lam_{n0} (w_fw = 1
+ * for n >= 1, 0 for n = 0).  tmp: a second adjoint buffer, distinct from
+ * lam.  *dJdCs_dev accumulates the C_s derivative.  Asynchronous.
+ * LBM_ERR_STATE for the cumulant model or 16-bit storage. */
+LBM_API lbm_status lbm_adjoint_segment(lbm_ctx* ctx, const float* ckpt, int64_t n0, int32_t k,
+                                       float* seg, float* lam, float* tmp, double* dJdCs_dev);
+
 /* Gradient with respect to the initial scalar field of a quantity whose
  * adjoint at step 0 is lam0: grad_chi0[n] = sum_k w_k lam0_Phi_k[n]
  * (since Phi_k = w_k chi0 at t = 0).  Device buffers.  Asynchronous. */

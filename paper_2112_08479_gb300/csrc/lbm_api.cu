@@ -317,6 +317,65 @@ lbm_status lbm_adjoint_step(lbm_ctx* c, const float* state_n, const float* lam_n
     return LBM_OK;
 }
 
+lbm_status lbm_objective_forward(lbm_ctx* c, int32_t nsteps, int32_t K, float* ckpt,
+                                 double* J_dev) {
+    if (!c) return arg_fail(nullptr, "ctx is NULL");
+    if (nsteps < 0 || K < 1) return arg_fail(c, "nsteps must be >= 0 and K >= 1");
+    if (!J_dev) return arg_fail(c, "J_dev is NULL");
+    const size_t S = (size_t)(q_of(&c->p) + 7) * c->kp.N;
+    for (int32_t n = 0; n < nsteps; ++n) {
+        cudaError_t e = cudaSuccess;
+        if (ckpt && n % K == 0)
+            e = launch_get_state(c->kp, c->p.model, c->p.storage, c->odd != 0, c->v,
+                                 ckpt + (size_t)(n / K) * S, c->stream);
+        if (e == cudaSuccess)
+            e = launch_step(c->kp, c->p.model, c->p.storage, c->odd != 0, c->v.f, c->v.phi,
+                            nullptr, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "objective forward launch");
+        c->odd ^= 1;
+        ++c->step;
+        e = launch_fw_accumulate(c->kp, c->p.model, c->p.storage, c->odd != 0, c->v, J_dev, 1.0,
+                                 c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "objective forward launch");
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_adjoint_segment(lbm_ctx* c, const float* ckpt, int64_t n0, int32_t k, float* seg,
+                               float* lam, float* tmp, double* dJdCs_dev) {
+    if (!c) return arg_fail(nullptr, "ctx is NULL");
+    if (c->p.model != LBM_BGK_SMAG_Q19 || c->p.storage != LBM_FP32) {
+        snprintf(c->err, sizeof c->err, "the adjoint exists for the BGK model with FP32 storage");
+        return LBM_ERR_STATE;
+    }
+    if (k < 1 || n0 < 0) return arg_fail(c, "k must be >= 1 and n0 >= 0");
+    if (!ckpt || !lam || !tmp || (k > 1 && !seg)) return arg_fail(c, "NULL buffer");
+    if (lam == tmp) return arg_fail(c, "lam and tmp must differ");
+    const size_t S = (size_t)(q_of(&c->p) + 7) * c->kp.N;
+    const float dAdCs = (float)(36.0 * sqrt(2.0) * c->p.cs_smag);
+    cudaError_t e = cudaSuccess;
+    // recompute s_{n0+1} .. s_{n0+k-1} into seg[1 .. k-1]
+    const float* prev = ckpt;
+    for (int32_t j = 1; j < k && e == cudaSuccess; ++j) {
+        e = launch_push_step(c->kp, prev, seg + (size_t)j * S, c->stream);
+        prev = seg + (size_t)j * S;
+    }
+    // lam_{n0+k} -> lam_{n0}
+    float* cur = lam;
+    float* nxt = tmp;
+    for (int32_t j = k - 1; j >= 0 && e == cudaSuccess; --j) {
+        const int64_t n = n0 + j;
+        const float* st = j == 0 ? ckpt : seg + (size_t)j * S;
+        e = launch_adjoint_step(c->kp, st, cur, nxt, dJdCs_dev, n >= 1 ? 1.0f : 0.0f, dAdCs,
+                                c->stream);
+        float* t = cur; cur = nxt; nxt = t;
+    }
+    if (e == cudaSuccess && cur != lam)
+        e = cudaMemcpyAsync(lam, cur, S * sizeof(float), cudaMemcpyDeviceToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "adjoint segment");
+    return LBM_OK;
+}
+
 lbm_status lbm_adjoint_chi0(lbm_ctx* c, const float* lam0, float* grad_chi0) {
     if (!c) return arg_fail(nullptr, "ctx is NULL");
     if (!lam0 || !grad_chi0) return arg_fail(c, "lam0 and grad_chi0 must not be NULL");

@@ -1,0 +1,103 @@
+// lbm_bgk_collide.cuh -- the per-node collision of the D3Q19 BGK-Smagorinsky
+// fluid with the D3Q7 scalar and the Boussinesq force, shared by the AA step
+// kernels, the out-of-place recompute and the adjoint.
+//
+// Per node and step (lattice units, c_s^2 = 1/3, populations held as
+// deviations f - w from the rest weights so FP32 keeps its digits):
+//   chi = sum_k Phi_k                                        (Eq. 27)
+//   F = g' chi e^g                                           (Eq. 11)
+//   rho = 1 + sum_i (f_i - w_i), rho u = sum_i c_i f_i + F/2  (Eq. 19-20, 52-53)
+//   Pi = sum_i c_i c_i (f_i - feq_i) = M - (delta rho / 3) I - rho u u
+//   q = |Pi|, tau = (tau0 + sqrt(tau0^2 + 18 sqrt2 C_s^2 q / rho)) / 2
+//                                                   (Eq. 32-34, reading R3)
+//   f*_i = f_i - (f_i - feq_i)/tau + (1 - 1/2tau) w_i [3 (c_i - u) + 9 (c_i.u) c_i].F
+//                                                   (Eq. 17, 21, 22, 26)
+//   tau_Phi = 1/2 + 4 (D + nu_T / Sc_T), nu_T = (tau - tau0) / 3   (Eq. 30, 35)
+//   Phi*_k = Phi_k - (Phi_k - w_k chi (1 + 4 c_k.u)) / tau_Phi     (Eq. 28-29)
+#pragma once
+
+#include "lbm_common.cuh"
+
+namespace lbmgpu {
+
+// Replaces f (held as f - w) and Phi (held as Phi - w) by their
+// post-collision values.  Directions come in opposite pairs (i, i + 1 for odd
+// i): with s = f_i + f_opp and d = f_i - f_opp the moments need half the
+// additions, and the equilibrium and the Guo source split into a part even
+// in c (shared by the pair) and a part odd in c (sign-flipped), which halves
+// the per-direction arithmetic.
+__device__ __forceinline__ void collide_bgk(const KParams& kp, float (&f)[19], float (&p)[7]) {
+    float chit = 0.0f;  // chi - 1
+#pragma unroll
+    for (int k = 0; k < 7; ++k) chit += p[k];
+    const float chi = 1.0f + chit;
+    const float Fx = kp.gx * chi, Fy = kp.gy * chi, Fz = kp.gz * chi;
+
+    float drho = f[0], jx = 0.0f, jy = 0.0f, jz = 0.0f;
+    float mxx = 0.0f, myy = 0.0f, mzz = 0.0f, mxy = 0.0f, mxz = 0.0f, myz = 0.0f;
+#pragma unroll
+    for (int i = 1; i < 19; i += 2) {
+        const float sp = f[i] + f[i + 1], dm = f[i] - f[i + 1];
+        drho += sp;
+        if (cx27(i)) { jx += cx27(i) * dm; mxx += sp; }
+        if (cy27(i)) { jy += cy27(i) * dm; myy += sp; }
+        if (cz27(i)) { jz += cz27(i) * dm; mzz += sp; }
+        if (cx27(i) * cy27(i)) mxy += cx27(i) * cy27(i) * sp;
+        if (cx27(i) * cz27(i)) mxz += cx27(i) * cz27(i) * sp;
+        if (cy27(i) * cz27(i)) myz += cy27(i) * cz27(i) * sp;
+    }
+    const float rho = 1.0f + drho;
+    const float irho = 1.0f / rho;
+    const float ux = (jx + 0.5f * Fx) * irho;
+    const float uy = (jy + 0.5f * Fy) * irho;
+    const float uz = (jz + 0.5f * Fz) * irho;
+    const float usq = ux * ux + uy * uy + uz * uz;
+
+    // non-equilibrium second moment (sum c c feq = rho (I/3 + u u), sum c c w = I/3)
+    const float d3 = drho * (1.0f / 3.0f);
+    const float pxx = mxx - d3 - rho * ux * ux;
+    const float pyy = myy - d3 - rho * uy * uy;
+    const float pzz = mzz - d3 - rho * uz * uz;
+    const float pxy = mxy - rho * ux * uy;
+    const float pxz = mxz - rho * ux * uz;
+    const float pyz = myz - rho * uy * uz;
+    const float q = sqrtf(pxx * pxx + pyy * pyy + pzz * pzz +
+                          2.0f * (pxy * pxy + pxz * pxz + pyz * pyz));
+    // tau - tau0 without cancellation: X / (2 (s + tau0)), s = sqrt(tau0^2 + X)
+    const float X = kp.A * q * irho;
+    const float s = sqrtf(kp.tau0 * kp.tau0 + X);
+    const float dtau = 0.5f * X / (s + kp.tau0);
+    const float om = 1.0f / (kp.tau0 + dtau);
+    const float keep = 1.0f - om;
+    const float guo = 1.0f - 0.5f * om;
+    const float uF = ux * Fx + uy * Fy + uz * Fz;
+    // feq_i - w_i = w_i (drho + rho (3 cu + 4.5 cu^2 - 1.5 u.u)),
+    // S_i = guo w_i (3 cF - 3 u.F + 9 cu cF)
+    const float base = drho - 1.5f * rho * usq;       // even part of (feq - w)/w at cu = 0
+    const float gbase = -3.0f * guo * uF;             // even part of S/w at cF = 0
+    f[0] = keep * f[0] + w19(0) * (om * base + gbase);
+#pragma unroll
+    for (int i = 1; i < 19; i += 2) {
+        const float cu = cx27(i) * ux + cy27(i) * uy + cz27(i) * uz;
+        const float cF = cx27(i) * Fx + cy27(i) * Fy + cz27(i) * Fz;
+        const float w = w19(i);
+        const float even = w * (om * (base + 4.5f * rho * cu * cu) + gbase + 9.0f * guo * cu * cF);
+        const float odd = w * (om * 3.0f * rho * cu + 3.0f * guo * cF);
+        f[i] = keep * f[i] + even + odd;
+        f[i + 1] = keep * f[i + 1] + even - odd;
+    }
+
+    // Phi_eq - w = w (chi - 1 + 4 chi c.u)
+    const float omp = 1.0f / (kp.taup0 + kp.kT * dtau);
+    const float keepp = 1.0f - omp;
+    p[0] = keepp * p[0] + omp * w7(0) * chit;
+    const float pe = omp * w7(1) * chit, pa = omp * w7(1) * 4.0f * chi;
+    p[1] = keepp * p[1] + pe + pa * ux;
+    p[2] = keepp * p[2] + pe - pa * ux;
+    p[3] = keepp * p[3] + pe + pa * uy;
+    p[4] = keepp * p[4] + pe - pa * uy;
+    p[5] = keepp * p[5] + pe + pa * uz;
+    p[6] = keepp * p[6] + pe - pa * uz;
+}
+
+}  // namespace lbmgpu

@@ -51,6 +51,7 @@ cudaError_t launch_fw_accumulate(const KParams& kp, int model, int storage, bool
                                  const Views& v, double* acc, double weight, cudaStream_t st);
 cudaError_t launch_adjoint_step(const KParams& kp, const float* state, const float* lam_next,
                                 float* lam, double* dcs, float wfw, float dAdCs, cudaStream_t st);
+cudaError_t launch_push_step(const KParams& kp, const float* src, float* dst, cudaStream_t st);
 cudaError_t launch_adjoint_chi0(const KParams& kp, const float* lam0, float* grad, cudaStream_t st);
 
 unsigned diag_block_count(int nx, int nz);

@@ -21,20 +21,17 @@ class LBMObjective(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, chi0, cs, params: lbm.Params, nsteps: int, K: int = 100):
-        if params.model != lbm.LBM_BGK_SMAG_Q19:
-            raise ValueError("the adjoint exists for the BGK-Smagorinsky model only")
+        if params.model != lbm.LBM_BGK_SMAG_Q19 or params.storage != lbm.LBM_FP32:
+            raise ValueError("the adjoint exists for the BGK-Smagorinsky model with FP32 storage")
         if nsteps < 1 or K < 1:
             raise ValueError("nsteps and K must be >= 1")
         p = replace(params, cs_smag=float(cs))
         lat = lbm.Lattice(p, device=chi0.device)
         lat.set_scalar(chi0.detach().to(torch.float32).contiguous())
         acc = torch.zeros(1, dtype=torch.float64, device=chi0.device)
-        ckpts = []
-        for n in range(nsteps):
-            if n % K == 0:
-                ckpts.append(lat.get_state())
-            lat.step(1)
-            lat.fw_accumulate(acc, 1.0)
+        nck = (nsteps + K - 1) // K
+        ckpts = torch.empty(nck, lat.Q + 7, lat.N, device=chi0.device)
+        lat.objective_forward(nsteps, K, ckpts, acc)
         ctx.lat = lat
         ctx.ckpts = ckpts
         ctx.final = lat.get_state()
@@ -48,24 +45,17 @@ class LBMObjective(torch.autograd.Function):
         lat, K, nsteps = ctx.lat, ctx.K, ctx.nsteps
         dev = ctx.final.device
         N = lat.N
-        lam = [torch.empty(26, N, device=dev), torch.empty(26, N, device=dev)]
+        lam = torch.empty(26, N, device=dev)
+        tmp = torch.empty(26, N, device=dev)
         dcs = torch.zeros(1, dtype=torch.float64, device=dev)
         # lam_N = dF_w(s_N)/ds_N
-        lat.adjoint_step(ctx.final, None, lam[0], None, 1.0)
-        cur = 0
+        lat.adjoint_step(ctx.final, None, lam, None, 1.0)
         seg_buf = torch.empty(min(K, nsteps), 26, N, device=dev)
-        for seg in range(len(ctx.ckpts) - 1, -1, -1):
+        for seg in range(ctx.ckpts.shape[0] - 1, -1, -1):
             n0 = seg * K
-            kl = min(K, nsteps - n0)
-            lat.set_state(ctx.ckpts[seg], n0)
-            for k in range(kl):
-                lat.step_save(seg_buf[k])
-            for k in range(kl - 1, -1, -1):
-                n = n0 + k
-                lat.adjoint_step(seg_buf[k], lam[cur], lam[1 - cur], dcs, 1.0 if n >= 1 else 0.0)
-                cur = 1 - cur
+            lat.adjoint_segment(ctx.ckpts[seg], n0, min(K, nsteps - n0), seg_buf, lam, tmp, dcs)
         grad = torch.empty(N, device=dev)
-        lat.adjoint_chi0(lam[cur], grad)
+        lat.adjoint_chi0(lam, grad)
         g = gJ.to(torch.float64)
         return ((g * grad.to(torch.float64)).to(ctx.chi_dtype),
                 (g * dcs[0]).to(ctx.cs_dtype), None, None, None)

@@ -39,26 +39,15 @@ __global__ void __launch_bounds__(128, LBM_STEP_MINB) bgk_step_kernel(KParams kp
     float fv[19], pv[7];
     gather<19, ODD>(kp, f, st, fv);
     gather<7, ODD>(kp, phi, st, pv);
-    if (!std::is_same<S, float>::value) {
-#pragma unroll
-        for (int i = 0; i < 19; ++i) fv[i] *= kp.isf;
-#pragma unroll
-        for (int k = 0; k < 7; ++k) pv[k] *= kp.isp;
-    }
+    constexpr bool s16 = !std::is_same<S, float>::value;   // populations in storage units
     if (SAVE) {
         const size_t N = kp.N;
 #pragma unroll
-        for (int i = 0; i < 19; ++i) save[(size_t)i * N + n] = fv[i];
+        for (int i = 0; i < 19; ++i) save[(size_t)i * N + n] = s16 ? fv[i] * kp.isf : fv[i];
 #pragma unroll
-        for (int k = 0; k < 7; ++k) save[(size_t)(19 + k) * N + n] = pv[k];
+        for (int k = 0; k < 7; ++k) save[(size_t)(19 + k) * N + n] = s16 ? pv[k] * kp.isp : pv[k];
     }
-    if (!(kp.flags & LBM_FLAG_NO_COLLIDE)) collide_bgk(kp, fv, pv);
-    if (!std::is_same<S, float>::value) {
-#pragma unroll
-        for (int i = 0; i < 19; ++i) fv[i] *= kp.sf;
-#pragma unroll
-        for (int k = 0; k < 7; ++k) pv[k] *= kp.sp;
-    }
+    if (!(kp.flags & LBM_FLAG_NO_COLLIDE)) collide_bgk<s16>(kp, fv, pv);
     scatter<19, ODD>(kp, f, st, fv);
     scatter<7, ODD>(kp, phi, st, pv);
 }
@@ -75,30 +64,21 @@ __global__ void __launch_bounds__(128, LBM_STEP2_MINB) bgk_step2_kernel(KParams 
     float f0[19], f1[19], p0[7], p1[7];
     gather2<19, ODD>(kp, f, st, f0, f1);
     gather2<7, ODD>(kp, phi, st, p0, p1);
-    if (!std::is_same<S, float>::value) {
-#pragma unroll
-        for (int i = 0; i < 19; ++i) { f0[i] *= kp.isf; f1[i] *= kp.isf; }
-#pragma unroll
-        for (int k = 0; k < 7; ++k) { p0[k] *= kp.isp; p1[k] *= kp.isp; }
-    }
+    constexpr bool s16 = !std::is_same<S, float>::value;   // populations in storage units
     if (SAVE && st.active) {
         const unsigned N = kp.N;
+        const float a = s16 ? kp.isf : 1.0f, b = s16 ? kp.isp : 1.0f;
 #pragma unroll
         for (int i = 0; i < 19; ++i)
-            *reinterpret_cast<float2*>(save + (size_t)i * N + st.n) = make_float2(f0[i], f1[i]);
+            *reinterpret_cast<float2*>(save + (size_t)i * N + st.n) = make_float2(a * f0[i], a * f1[i]);
 #pragma unroll
         for (int k = 0; k < 7; ++k)
-            *reinterpret_cast<float2*>(save + (size_t)(19 + k) * N + st.n) = make_float2(p0[k], p1[k]);
+            *reinterpret_cast<float2*>(save + (size_t)(19 + k) * N + st.n) =
+                make_float2(b * p0[k], b * p1[k]);
     }
     if (!(kp.flags & LBM_FLAG_NO_COLLIDE)) {
-        collide_bgk(kp, f0, p0);
-        collide_bgk(kp, f1, p1);
-    }
-    if (!std::is_same<S, float>::value) {
-#pragma unroll
-        for (int i = 0; i < 19; ++i) { f0[i] *= kp.sf; f1[i] *= kp.sf; }
-#pragma unroll
-        for (int k = 0; k < 7; ++k) { p0[k] *= kp.sp; p1[k] *= kp.sp; }
+        collide_bgk<s16>(kp, f0, p0);
+        collide_bgk<s16>(kp, f1, p1);
     }
     scatter2<19, ODD>(kp, f, st, f0, f1);
     scatter2<7, ODD>(kp, phi, st, p0, p1);
@@ -107,7 +87,7 @@ __global__ void __launch_bounds__(128, LBM_STEP2_MINB) bgk_step2_kernel(KParams 
 template <typename S>
 static cudaError_t launch_bgk_typed(const KParams& kp, bool odd, S* f, S* phi, float* save,
                                    cudaStream_t st) {
-    if (LBM_BGK_PAIR && kp.nx % 2 == 0) {
+    if constexpr (LBM_BGK_PAIR) if (kp.nx % 2 == 0) {
         dim3 block(128), grid((kp.nx / 2 + 127) / 128, kp.ny, kp.nz);
         if (save) {
             if (odd) bgk_step2_kernel<true, true, S><<<grid, block, 0, st>>>(kp, f, phi, save);

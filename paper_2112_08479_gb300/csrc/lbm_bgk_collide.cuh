@@ -26,10 +26,18 @@ namespace lbmgpu {
 // additions, and the equilibrium and the Guo source split into a part even
 // in c (shared by the pair) and a part odd in c (sign-flipped), which halves
 // the per-direction arithmetic.
+//
+// SCALED: f and p hold the 16-bit storage units scale_f (f - w) and
+// scale_phi (Phi - w); the scales are applied to the few moments and output
+// terms instead of to every population.
+template <bool SCALED = false>
 __device__ __forceinline__ void collide_bgk(const KParams& kp, float (&f)[19], float (&p)[7]) {
-    float chit = 0.0f;  // chi - 1
+    const float isf = SCALED ? kp.isf : 1.0f, isp = SCALED ? kp.isp : 1.0f;
+    const float sf = SCALED ? kp.sf : 1.0f, sp = SCALED ? kp.sp : 1.0f;
+    float chs = 0.0f;  // scale_phi (chi - 1)
 #pragma unroll
-    for (int k = 0; k < 7; ++k) chit += p[k];
+    for (int k = 0; k < 7; ++k) chs += p[k];
+    const float chit = chs * isp;  // chi - 1
     const float chi = 1.0f + chit;
     const float Fx = kp.gx * chi, Fy = kp.gy * chi, Fz = kp.gz * chi;
 
@@ -37,14 +45,18 @@ __device__ __forceinline__ void collide_bgk(const KParams& kp, float (&f)[19], f
     float mxx = 0.0f, myy = 0.0f, mzz = 0.0f, mxy = 0.0f, mxz = 0.0f, myz = 0.0f;
 #pragma unroll
     for (int i = 1; i < 19; i += 2) {
-        const float sp = f[i] + f[i + 1], dm = f[i] - f[i + 1];
-        drho += sp;
-        if (cx27(i)) { jx += cx27(i) * dm; mxx += sp; }
-        if (cy27(i)) { jy += cy27(i) * dm; myy += sp; }
-        if (cz27(i)) { jz += cz27(i) * dm; mzz += sp; }
-        if (cx27(i) * cy27(i)) mxy += cx27(i) * cy27(i) * sp;
-        if (cx27(i) * cz27(i)) mxz += cx27(i) * cz27(i) * sp;
-        if (cy27(i) * cz27(i)) myz += cy27(i) * cz27(i) * sp;
+        const float sm = f[i] + f[i + 1], dm = f[i] - f[i + 1];
+        drho += sm;
+        if (cx27(i)) { jx += cx27(i) * dm; mxx += sm; }
+        if (cy27(i)) { jy += cy27(i) * dm; myy += sm; }
+        if (cz27(i)) { jz += cz27(i) * dm; mzz += sm; }
+        if (cx27(i) * cy27(i)) mxy += cx27(i) * cy27(i) * sm;
+        if (cx27(i) * cz27(i)) mxz += cx27(i) * cz27(i) * sm;
+        if (cy27(i) * cz27(i)) myz += cy27(i) * cz27(i) * sm;
+    }
+    if (SCALED) {
+        drho *= isf; jx *= isf; jy *= isf; jz *= isf;
+        mxx *= isf; myy *= isf; mzz *= isf; mxy *= isf; mxz *= isf; myz *= isf;
     }
     const float rho = 1.0f + drho;
     const float irho = 1.0f / rho;
@@ -75,29 +87,35 @@ __device__ __forceinline__ void collide_bgk(const KParams& kp, float (&f)[19], f
     // S_i = guo w_i (3 cF - 3 u.F + 9 cu cF)
     const float base = drho - 1.5f * rho * usq;       // even part of (feq - w)/w at cu = 0
     const float gbase = -3.0f * guo * uF;             // even part of S/w at cF = 0
-    f[0] = keep * f[0] + w19(0) * (om * base + gbase);
+    f[0] = keep * f[0] + sf * w19(0) * (om * base + gbase);
 #pragma unroll
     for (int i = 1; i < 19; i += 2) {
         const float cu = cx27(i) * ux + cy27(i) * uy + cz27(i) * uz;
         const float cF = cx27(i) * Fx + cy27(i) * Fy + cz27(i) * Fz;
-        const float w = w19(i);
+        const float w = sf * w19(i);
         const float even = w * (om * (base + 4.5f * rho * cu * cu) + gbase + 9.0f * guo * cu * cF);
         const float odd = w * (om * 3.0f * rho * cu + 3.0f * guo * cF);
         f[i] = keep * f[i] + even + odd;
         f[i + 1] = keep * f[i + 1] + even - odd;
     }
 
-    // Phi_eq - w = w (chi - 1 + 4 chi c.u)
+    // scalar: Phi_eq - w = w (chi - 1 + 4 chi c.u).  Only the non-equilibrium
+    // parts are relaxed, and the rest population's part closes their sum to
+    // zero, so the update conserves sum Phi exactly up to the rounding of the
+    // stored results (relaxing towards the rounded chi would inject
+    // omega times the rounding error of the 7-term sum at every node)
     const float omp = 1.0f / (kp.taup0 + kp.kT * dtau);
-    const float keepp = 1.0f - omp;
-    p[0] = keepp * p[0] + omp * w7(0) * chit;
-    const float pe = omp * w7(1) * chit, pa = omp * w7(1) * 4.0f * chi;
-    p[1] = keepp * p[1] + pe + pa * ux;
-    p[2] = keepp * p[2] + pe - pa * ux;
-    p[3] = keepp * p[3] + pe + pa * uy;
-    p[4] = keepp * p[4] + pe - pa * uy;
-    p[5] = keepp * p[5] + pe + pa * uz;
-    p[6] = keepp * p[6] + pe - pa * uz;
+    const float pe = w7(1) * chs, pa = sp * w7(1) * 4.0f * chi;
+    float nq[7];
+    nq[1] = p[1] - (pe + pa * ux);
+    nq[2] = p[2] - (pe - pa * ux);
+    nq[3] = p[3] - (pe + pa * uy);
+    nq[4] = p[4] - (pe - pa * uy);
+    nq[5] = p[5] - (pe + pa * uz);
+    nq[6] = p[6] - (pe - pa * uz);
+    nq[0] = -(((nq[1] + nq[2]) + (nq[3] + nq[4])) + (nq[5] + nq[6]));
+#pragma unroll
+    for (int k = 0; k < 7; ++k) p[k] -= omp * nq[k];
 }
 
 }  // namespace lbmgpu

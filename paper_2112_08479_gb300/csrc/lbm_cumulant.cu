@@ -144,16 +144,23 @@ __device__ __forceinline__ void collide_cumulant(const KParams& kp, float (&f)[2
             f[ip] = drho * w27(ip) + rho * pp;
         }
 
-    // scalar (Eq. 28-30) with the half-force velocity and the molecular D
+    // scalar (Eq. 28-30) with the half-force velocity and the molecular D;
+    // non-equilibrium form whose parts sum to zero, so sum Phi is conserved
+    // up to the rounding of the stored results (see collide_bgk)
     const float hx = (jx + 0.5f * Fx) * irho, hy = (jy + 0.5f * Fy) * irho,
                 hz = (jz + 0.5f * Fz) * irho;
     const float omp = 1.0f / kp.taup0;
+    const float pe = w7(1) * chit, pa = w7(1) * 4.0f * chi;
+    float nq[7];
+    nq[1] = p[1] - (pe + pa * hx);
+    nq[2] = p[2] - (pe - pa * hx);
+    nq[3] = p[3] - (pe + pa * hy);
+    nq[4] = p[4] - (pe - pa * hy);
+    nq[5] = p[5] - (pe + pa * hz);
+    nq[6] = p[6] - (pe - pa * hz);
+    nq[0] = -(((nq[1] + nq[2]) + (nq[3] + nq[4])) + (nq[5] + nq[6]));
 #pragma unroll
-    for (int k = 0; k < 7; ++k) {
-        const float cu = cx27(k) * hx + cy27(k) * hy + cz27(k) * hz;
-        const float peq = w7(k) * (chit + 4.0f * chi * cu);   // Phi_eq - w
-        p[k] = p[k] - omp * (p[k] - peq);
-    }
+    for (int k = 0; k < 7; ++k) p[k] -= omp * nq[k];
 }
 
 template <bool ODD, bool SAVE, typename S>
@@ -236,7 +243,7 @@ __global__ void __launch_bounds__(128, LBM_STEP2_MINB) cumulant_step2_kernel(KPa
 template <typename S>
 static cudaError_t launch_cumulant_typed(const KParams& kp, bool odd, S* f, S* phi, float* save,
                                    cudaStream_t st) {
-    if (LBM_CUMULANT_PAIR && kp.nx % 2 == 0) {
+    if constexpr (LBM_CUMULANT_PAIR) if (kp.nx % 2 == 0) {
         dim3 block(128), grid((kp.nx / 2 + 127) / 128, kp.ny, kp.nz);
         if (save) {
             if (odd) cumulant_step2_kernel<true, true, S><<<grid, block, 0, st>>>(kp, f, phi, save);

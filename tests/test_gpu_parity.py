@@ -184,8 +184,9 @@ def test_set_scalar_host_and_device():
     sb = b.get_state()
     for lat in (c, d):
         assert torch.equal(lat.get_state(), sb)
-    # lbm_init draws the noise in FP64; chi0 given as FP32 differs by one rounding
-    assert (a.get_state() - sb).abs().max().item() < 1e-7
+    # lbm_init draws the noise in FP64; chi0 given as FP32 differs by one
+    # rounding of 1 + noise (ulp(1) = 1.2e-7), carried through three steps
+    assert (a.get_state() - sb).abs().max().item() < 1e-6
 
 
 def test_state_round_trip_fp32():

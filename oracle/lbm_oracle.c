@@ -21,7 +21,8 @@
  *      with half-way bounce-back at the x and z walls (Sec. 2.5) and periodic y.
  *
  * Layout: array of structures, node-major,
- *   f[((z*ny + y)*nx + x)*Q + i],   Phi[((z*ny + y)*nx + x)*7 + k].
+ *   f[((z*ny + y)*nx + x)*Q + i],   Phi[((z*ny + y)*nx + x)*NS + k],
+ * NS = 7 (D3Q7), 6 (D3Q6) or 27 (D3Q27) scalar populations.
  * Two arrays, no in-place tricks, no blocking, no fusion beyond the above.
  *
  * Readings where the paper is silent or garbled (named R1..R17 in the design
@@ -70,6 +71,11 @@ typedef struct {
     double eg[3];       /* unit vector of gravity, (0,0,-1) in the paper */
     double omega_bulk;  /* cumulant: rate of the second-order trace */
     double omega_high;  /* cumulant: rate of every cumulant of order >= 3 */
+    int scalar;         /* scalar lattice: 0 D3Q7 BGK (R1), 1 D3Q6 BGK (Eq. 29-31),
+                           2 D3Q27 factorized central moments (Eq. 37-51) */
+    int pad2_;
+    double omega_phi_high; /* D3Q27 scalar: rate of every factorized moment of
+                              order >= 2 (Eq. 50) */
 } orc_params;
 
 /* ------------------------------------------------------------------------ */
@@ -97,6 +103,10 @@ static const int C27[27][3] = {
 static const int C7[7][3] = {
     { 0, 0, 0}, { 1, 0, 0}, {-1, 0, 0}, { 0, 1, 0}, { 0,-1, 0}, { 0, 0, 1}, { 0, 0,-1}};
 
+/* D3Q6 scalar lattice in the order of Eq. 31, w = 1/6 (Sec. 2.3.1). */
+static const int C6[6][3] = {
+    { 1, 0, 0}, {-1, 0, 0}, { 0, 1, 0}, { 0,-1, 0}, { 0, 0, 1}, { 0, 0,-1}};
+
 static int nsq(const int c[3]) { return c[0]*c[0] + c[1]*c[1] + c[2]*c[2]; }
 
 /* Eq. 24 */
@@ -114,6 +124,13 @@ static double w27(int i) {
 static double w7(int k) { return k == 0 ? 0.25 : 0.125; }
 
 static int nq(const orc_params* p) { return p->model == 1 ? 27 : 19; }
+static int ns(const orc_params* p) { return p->scalar == 1 ? 6 : (p->scalar == 2 ? 27 : 7); }
+static const int (*sset(const orc_params* p))[3] {
+    return p->scalar == 1 ? C6 : (p->scalar == 2 ? C27 : C7);
+}
+static double wsc(const orc_params* p, int k) {
+    return p->scalar == 1 ? 1.0/6.0 : (p->scalar == 2 ? w27(k) : w7(k));
+}
 static const int (*cset(const orc_params* p))[3] { return p->model == 1 ? C27 : C19; }
 static double wq(const orc_params* p, int i) { return p->model == 1 ? w27(i) : w19(i); }
 
@@ -138,6 +155,14 @@ void orc_velocities_q7(int* c_out, double* w_out) {
     for (int k = 0; k < 7; ++k) {
         for (int a = 0; a < 3; ++a) c_out[3*k + a] = C7[k][a];
         w_out[k] = w7(k);
+    }
+}
+int orc_ns(int scalar) { return scalar == 1 ? 6 : (scalar == 2 ? 27 : 7); }
+void orc_velocities_scalar(int scalar, int* c_out, double* w_out) {
+    orc_params p; memset(&p, 0, sizeof p); p.scalar = scalar;
+    for (int k = 0; k < ns(&p); ++k) {
+        for (int a = 0; a < 3; ++a) c_out[3*k + a] = sset(&p)[k][a];
+        w_out[k] = wsc(&p, k);
     }
 }
 
@@ -174,7 +199,7 @@ static void node_moments(const orc_params* p, const double* f, const double* phi
     int q = nq(p);
     const int (*c)[3] = cset(p);
     double x = 0.0;
-    for (int k = 0; k < 7; ++k) x += phi[k];
+    for (int k = 0; k < ns(p); ++k) x += phi[k];
     *chi = x;
     for (int a = 0; a < 3; ++a) F[a] = p->gprime * x * p->eg[a];
     double r = 0.0, j[3] = {0.0, 0.0, 0.0};
@@ -367,14 +392,79 @@ static void collide_cumulant(const orc_params* p, const double* f, double rho,
 }
 
 /* ------------------------------------------------------------------------ */
-/* Scalar collision (Eq. 28-30 and 35 with readings R1, R4).               */
+/* Scalar collisions.                                                       */
+
+/* Eq. 29 on D3Q6, literal: c_s^2 = 1/3, w = 1/6. */
+void orc_phieq_q6(double chi, const double u[3], double* phieq) {
+    for (int k = 0; k < 6; ++k) {
+        double cu = C6[k][0]*u[0] + C6[k][1]*u[1] + C6[k][2]*u[2];
+        phieq[k] = chi * (1.0 + 3.0*cu) / 6.0;
+    }
+}
+
+/* D3Q27 factorized central moments (Eq. 37-51).  Central moments of Phi in
+ * the frame moving with u (Eq. 39), factorized moments M (Eq. 40-49), which
+ * subtract from kappa_abc the lattice equilibrium share (1/3)^m kappa_a'b'c',
+ * m the number of indices equal to 2 and a'b'c' the indices with every 2
+ * replaced by 0 (Eq. 46 is garbled in the text: the same rule gives
+ * kappa_220 - kappa_000 / 9).  M_000 = chi is conserved, the first-order M
+ * relax with omega from D = (1/omega - 1/2) / 3 (Eq. 51), all others with
+ * omega_phi_high towards 0 (Eq. 50).  Back: kappa = M + (1/3)^m M_a'b'c', raw
+ * moments by the binomial frame shift, populations by the per-axis inverse
+ * Vandermonde map. */
+static void collide_fcm27(const orc_params* p, const double* phi, const double u[3],
+                          double Deff, double* phio) {
+    ring K, M, Ks, m;
+    memset(K, 0, sizeof K);
+    for (int i = 0; i < 27; ++i)
+        for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) for (int c = 0; c < 3; ++c) {
+            double v = phi[i];
+            for (int k = 0; k < a; ++k) v *= (C27[i][0] - u[0]);
+            for (int k = 0; k < b; ++k) v *= (C27[i][1] - u[1]);
+            for (int k = 0; k < c; ++k) v *= (C27[i][2] - u[2]);
+            K[a][b][c] += v;
+        }
+    double third[4] = {1.0, 1.0/3.0, 1.0/9.0, 1.0/27.0};
+    for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) for (int c = 0; c < 3; ++c) {
+        int m2 = (a == 2) + (b == 2) + (c == 2);
+        M[a][b][c] = K[a][b][c] - (m2 ? third[m2] * K[a % 2][b % 2][c % 2] : 0.0);
+    }
+    double omD = 1.0 / (3.0*Deff + 0.5);
+    for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) for (int c = 0; c < 3; ++c) {
+        int n = a + b + c;
+        if (n == 1) M[a][b][c] *= (1.0 - omD);
+        else if (n >= 2) M[a][b][c] *= (1.0 - p->omega_phi_high);
+    }
+    for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) for (int c = 0; c < 3; ++c) {
+        int m2 = (a == 2) + (b == 2) + (c == 2);
+        Ks[a][b][c] = M[a][b][c] + (m2 ? third[m2] * M[a % 2][b % 2][c % 2] : 0.0);
+    }
+    /* raw moments m_abc = sum_{a'<=a,...} C(a,a') u^(a-a') ... kappa_a'b'c' */
+    static const double BIN[3][3] = {{1, 0, 0}, {1, 1, 0}, {1, 2, 1}};
+    memset(m, 0, sizeof m);
+    for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) for (int c = 0; c < 3; ++c)
+    for (int a1 = 0; a1 <= a; ++a1) for (int b1 = 0; b1 <= b; ++b1) for (int c1 = 0; c1 <= c; ++c1)
+        m[a][b][c] += BIN[a][a1] * pow(u[0], a - a1) * BIN[b][b1] * pow(u[1], b - b1)
+                    * BIN[c][c1] * pow(u[2], c - c1) * Ks[a1][b1][c1];
+    f_from_moments27(m, phio);
+}
+
+/* Scalar collision on the lattice p->scalar (Eq. 28-30, 35 with readings R1,
+ * R4; Eq. 37-51 for D3Q27). */
 static void collide_scalar(const orc_params* p, const double* phi, double chi,
                            const double u[3], double nu_t, double* phio) {
     double Deff = p->D + (p->model == 0 ? nu_t / p->sc_t : 0.0);
-    double tauphi = 0.5 + 4.0 * Deff;                  /* D = c_sPhi^2 (tau - 1/2) */
+    if (p->scalar == 2) { collide_fcm27(p, phi, u, Deff, phio); return; }
     double phieq[7];
-    orc_phieq_q7(chi, u, phieq);
-    for (int k = 0; k < 7; ++k) phio[k] = phi[k] - (phi[k] - phieq[k]) / tauphi;
+    double tauphi;
+    if (p->scalar == 1) {
+        tauphi = 0.5 + 3.0 * Deff;                     /* D = c_s^2 (tau - 1/2), c_s^2 = 1/3 */
+        orc_phieq_q6(chi, u, phieq);
+    } else {
+        tauphi = 0.5 + 4.0 * Deff;                     /* c_sPhi^2 = 1/4 on D3Q7 */
+        orc_phieq_q7(chi, u, phieq);
+    }
+    for (int k = 0; k < ns(p); ++k) phio[k] = phi[k] - (phi[k] - phieq[k]) / tauphi;
 }
 
 /* One node: fluid + scalar collision.  Exported for the single-node pins. */
@@ -383,7 +473,7 @@ void orc_collide_node(const orc_params* p, const double* f, const double* phi,
     int q = nq(p);
     if (p->no_collide) {
         memcpy(fo, f, sizeof(double)*q);
-        memcpy(phio, phi, sizeof(double)*7);
+        memcpy(phio, phi, sizeof(double)*ns(p));
         return;
     }
     double rho, u[3], chi, F[3], nu_t = 0.0;
@@ -437,9 +527,11 @@ void orc_stream(const orc_params* p, const double* fpost, const double* phipost,
             if (upwind(p, x, y, z, c[i], &s)) f[n*q + i] = fpost[s*q + i];
             else f[n*q + i] = fpost[n*q + opposite(c, q, i)];
         }
-        for (int k = 0; k < 7; ++k) {
-            if (upwind(p, x, y, z, C7[k], &s)) phi[n*7 + k] = phipost[s*7 + k];
-            else phi[n*7 + k] = phipost[n*7 + opposite(C7, 7, k)];
+        const int S = ns(p);
+        const int (*cs)[3] = sset(p);
+        for (int k = 0; k < S; ++k) {
+            if (upwind(p, x, y, z, cs[k], &s)) phi[n*S + k] = phipost[s*S + k];
+            else phi[n*S + k] = phipost[n*S + opposite(cs, S, k)];
         }
     }
 }
@@ -455,7 +547,7 @@ void orc_macros(const orc_params* p, const double* f, const double* phi,
     long N = (long)p->nx * p->ny * p->nz;
     for (long n = 0; n < N; ++n) {
         double r, uu[3], x, F[3];
-        node_moments(p, f + n*q, phi + n*7, &r, uu, &x, F);
+        node_moments(p, f + n*q, phi + n*ns(p), &r, uu, &x, F);
         if (rho) rho[n] = r;
         if (u) for (int a = 0; a < 3; ++a) u[n*3 + a] = uu[a];
         if (chi) chi[n] = x;
@@ -528,9 +620,10 @@ void orc_step(const orc_params* p, double* f, double* phi) {
     int q = nq(p);
     long N = (long)p->nx * p->ny * p->nz;
     double* fpost = (double*)malloc(sizeof(double) * N * q);
-    double* phipost = (double*)malloc(sizeof(double) * N * 7);
+    const int S = ns(p);
+    double* phipost = (double*)malloc(sizeof(double) * N * S);
     for (long n = 0; n < N; ++n)
-        orc_collide_node(p, f + n*q, phi + n*7, fpost + n*q, phipost + n*7);
+        orc_collide_node(p, f + n*q, phi + n*S, fpost + n*q, phipost + n*S);
     orc_stream(p, fpost, phipost, f, phi);
     free(fpost); free(phipost);
 }
@@ -577,12 +670,13 @@ void orc_lock_chi0(int nx, int ny, int nz, int x0, double amp, uint64_t seed, do
     }
 }
 
-/* rest state f_i = w_i (rho = 1, u = 0), Phi_k = w_k chi0 */
+/* rest state f_i = w_i (rho = 1, u = 0), Phi_k = w_k chi0 (the scalar
+ * lattice's weights; for D3Q27 that is the moment equilibrium at u = 0) */
 void orc_init(const orc_params* p, const double* chi0, double* f, double* phi) {
     int q = nq(p);
     long N = (long)p->nx * p->ny * p->nz;
     for (long n = 0; n < N; ++n) {
         for (int i = 0; i < q; ++i) f[n*q + i] = wq(p, i);
-        for (int k = 0; k < 7; ++k) phi[n*7 + k] = w7(k) * chi0[n];
+        for (int k = 0; k < ns(p); ++k) phi[n*ns(p) + k] = wsc(p, k) * chi0[n];
     }
 }

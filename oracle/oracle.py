@@ -23,7 +23,8 @@ __all__ = [
     "OracleParams", "build", "lib", "q_of", "velocities", "velocities_q7",
     "feq_q19", "phieq_q7", "tau_eff", "collide_node", "cumulants27",
     "f_from_cumulants27", "bgk_nu_t", "lock_chi0", "init", "step", "run", "stream",
-    "macros", "wall_friction", "front_node", "diag", "splitmix64",
+    "macros", "wall_friction", "front_node", "diag", "splitmix64", "velocities_scalar",
+    "phieq_q6",
 ]
 
 
@@ -44,7 +45,8 @@ class _P(C.Structure):
                 ("no_collide", C.c_int), ("pad_", C.c_int),
                 ("nu", C.c_double), ("D", C.c_double), ("cs_smag", C.c_double),
                 ("sc_t", C.c_double), ("gprime", C.c_double), ("eg", C.c_double * 3),
-                ("omega_bulk", C.c_double), ("omega_high", C.c_double)]
+                ("omega_bulk", C.c_double), ("omega_high", C.c_double),
+                ("scalar", C.c_int), ("pad2_", C.c_int), ("omega_phi_high", C.c_double)]
 
 
 @dataclass
@@ -64,6 +66,8 @@ class OracleParams:
     periodic_x: bool = False
     periodic_z: bool = False
     no_collide: bool = False
+    scalar: int = 0           # 0 D3Q7 BGK, 1 D3Q6 BGK, 2 D3Q27 factorized central moments
+    omega_phi_high: float = 1.0
     _c: _P = field(default=None, repr=False)
 
     def c(self) -> _P:
@@ -75,11 +79,16 @@ class OracleParams:
         p.nu, p.D, p.cs_smag, p.sc_t, p.gprime = self.nu, self.D, self.cs_smag, self.sc_t, self.gprime
         p.eg = (C.c_double * 3)(*self.eg)
         p.omega_bulk, p.omega_high = self.omega_bulk, self.omega_high
+        p.scalar, p.omega_phi_high = self.scalar, self.omega_phi_high
         return p
 
     @property
     def Q(self) -> int:
         return 27 if self.model == 1 else 19
+
+    @property
+    def NS(self) -> int:
+        return {0: 7, 1: 6, 2: 27}[self.scalar]
 
     @property
     def shape(self):
@@ -100,6 +109,9 @@ def lib():
             "orc_q": (C.c_int, [C.c_int]),
             "orc_velocities": (None, [C.c_int, i, d]),
             "orc_velocities_q7": (None, [i, d]),
+            "orc_ns": (C.c_int, [C.c_int]),
+            "orc_velocities_scalar": (None, [C.c_int, i, d]),
+            "orc_phieq_q6": (None, [C.c_double, d, d]),
             "orc_feq_q19": (None, [C.c_double, d, d]),
             "orc_phieq_q7": (None, [C.c_double, d, d]),
             "orc_tau_eff": (C.c_double, [C.c_double, C.c_double, C.c_double, C.c_double]),
@@ -155,6 +167,22 @@ def velocities_q7():
     return c.reshape(7, 3), w
 
 
+def velocities_scalar(scalar: int):
+    """Scalar lattice: D3Q7 (R1), D3Q6 (Eq. 31, w = 1/6) or D3Q27 (Eq. 36)."""
+    n = lib().orc_ns(scalar)
+    c = np.zeros(3 * n, dtype=np.int32)
+    w = np.zeros(n)
+    lib().orc_velocities_scalar(scalar, c.ctypes.data_as(C.POINTER(C.c_int)), _d(w))
+    return c.reshape(n, 3), w
+
+
+def phieq_q6(chi: float, u) -> np.ndarray:
+    """Scalar equilibrium, Eq. 29 on D3Q6 (c_s^2 = 1/3)."""
+    out = np.zeros(6)
+    lib().orc_phieq_q6(chi, _d(_f64(u)), _d(out))
+    return out
+
+
 def feq_q19(rho: float, u) -> np.ndarray:
     """Second-order equilibrium, Eq. 22."""
     out = np.zeros(19)
@@ -179,7 +207,7 @@ def collide_node(p: OracleParams, f, phi):
     f = _f64(f)
     phi = _f64(phi)
     fo = np.zeros(p.Q)
-    po = np.zeros(7)
+    po = np.zeros(p.NS)
     pc = p.c()
     lib().orc_collide_node(C.byref(pc), _d(f), _d(phi), _d(fo), _d(po))
     return fo, po
@@ -219,7 +247,7 @@ def init(p: OracleParams, chi0):
     """Rest state f = w, Phi = w chi0."""
     chi0 = _f64(chi0).reshape(p.shape)
     f = np.zeros(p.shape + (p.Q,))
-    phi = np.zeros(p.shape + (7,))
+    phi = np.zeros(p.shape + (p.NS,))
     pc = p.c()
     lib().orc_init(C.byref(pc), _d(chi0), _d(f), _d(phi))
     return f, phi

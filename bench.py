@@ -37,9 +37,12 @@ WORKLOADS = {
     "profile": dict(nx=512, ny=128, nz=64, H=64, x0=64, u_b=0.03, Re=30000.0 / 4),
 }
 WORKLOAD = dict(WORKLOADS["config3"])
-BYTES_PER_NODE = {("bgk", "fp32"): 208, ("cumulant", "fp32"): 272,
-                  ("bgk", "fp16s"): 104, ("bgk", "bf16s"): 104,
-                  ("cumulant", "fp16s"): 136, ("cumulant", "bf16s"): 136}
+def bytes_per_node(model="bgk", storage="fp32", scalar="q7") -> int:
+    """Algorithmic bytes of one node update: every population read once and
+    written once (AA in place), (Q + NS) populations of 4 or 2 bytes."""
+    q = 19 if model == "bgk" else 27
+    ns = {"q7": 7, "q6": 6, "q27": 27}[scalar]
+    return (q + ns) * 2 * (4 if storage == "fp32" else 2)
 PROFILE = os.path.join(ROOT, "profiles", "aa_step_bgk_fp32_traffic.md")
 # the sources that define the headline step kernel (bgk_step2_kernel)
 KERNEL_SOURCES = ["paper_2112_08479_gb300/csrc/lbm_bgk.cu",
@@ -228,12 +231,12 @@ def config_dict(ws, model="bgk", storage="fp32"):
 
 
 # ---------------------------------------------------------------------------
-def make_lattice(model="bgk", storage="fp32", **over):
+def make_lattice(model="bgk", storage="fp32", scalar="q7", **over):
     from paper_2112_08479_gb300 import lbm
     w = dict(WORKLOAD)
     w.update(over)
     p = lbm.lock_exchange(w["nx"], w["ny"], w["nz"], H=w["H"], x0=w["x0"], u_b=w["u_b"],
-                          Re=w["Re"], model=model, storage=storage)
+                          Re=w["Re"], model=model, storage=storage, scalar=scalar)
     return lbm.Lattice(p, device="cuda")
 
 
@@ -264,12 +267,12 @@ def timed_loop(lat, steps, warmup, torch, inner=INNER, with_diag=True, kernel_ev
     return total, kern, launches
 
 
-def side_variant(torch, model, storage, steps=3):
-    lat = make_lattice(model, storage)
+def side_variant(torch, model, storage, scalar="q7", steps=3):
+    lat = make_lattice(model, storage, scalar)
     total, kern, _ = timed_loop(lat, steps, 1, torch, with_diag=False)
     n = lat.N
     mnups = n / kern / 1e6
-    gbs = BYTES_PER_NODE[(model, storage)] * n / kern / 1e9
+    gbs = bytes_per_node(model, storage, scalar) * n / kern / 1e9
     del lat
     torch.cuda.empty_cache()
     return {"mnups": mnups, "ms_per_time_step": kern * 1e3, "achieved_gbs": gbs}
@@ -361,7 +364,7 @@ def run_ours(args, ws, rank, local):
     torch.cuda.empty_cache()
 
     peak, peak_kind = measured_peak_hbm()
-    bpn = BYTES_PER_NODE[(args.model, args.storage)]
+    bpn = bytes_per_node(args.model, args.storage)
     achieved = bpn * N / kern / 1e9
     headline = (args.model, args.storage) == ("bgk", "fp32") and args.workload == "config3"
     kname = "bgk_step2_kernel" if args.model == "bgk" and WORKLOAD["nx"] % 2 == 0 else f"{args.model}_step_kernel"
@@ -374,11 +377,12 @@ def run_ours(args, ws, rank, local):
     extra = {}
     if rank == 0 and ws == 1 and not args.no_side and args.workload == "config3":
         variants = {}
-        for model, storage in (("bgk", "fp16s"), ("bgk", "bf16s"), ("cumulant", "fp32"),
-                               ("cumulant", "fp16s")):
-            r = side_variant(torch, model, storage)
+        for model, storage, scalar in (("bgk", "fp16s", "q7"), ("bgk", "bf16s", "q7"),
+                                       ("cumulant", "fp32", "q7"), ("cumulant", "fp16s", "q7"),
+                                       ("bgk", "fp32", "q6"), ("cumulant", "fp32", "q27")):
+            r = side_variant(torch, model, storage, scalar)
             r["hbm_frac"] = r.pop("achieved_gbs") / peak
-            variants[f"{model}_{storage}"] = r
+            variants[f"{model}_{storage}" + ("" if scalar == "q7" else f"_{scalar}")] = r
         extra["variants"] = variants
         extra["adjoint"] = adjoint_ratio(torch)
     cpu = None

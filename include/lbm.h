@@ -28,13 +28,14 @@
  *    rho <= 0) are reported by the next synchronising call (lbm_diag,
  *    lbm_sync).  Nothing aborts, exits or traps.
  *  - Canonical state layout (lbm_get_state / lbm_set_state / adjoint):
- *    FP32, direction-major, [Q + 7][N]: rows 0..Q-1 hold f_i - w_i of the
- *    pre-collision (streamed) fluid populations, rows Q..Q+6 hold Phi_k - w_k
- *    of the scalar populations (w the lattice weights; both sets are held as
- *    deviations from their rest state rho = 1, chi = 1).  Direction orders: D3Q19 as in Eq. 23; D3Q27
- *    as Eq. 23 followed by the corners (1,1,1), (-1,-1,-1), (1,1,-1),
- *    (-1,-1,1), (1,-1,1), (-1,1,-1), (-1,1,1), (1,-1,-1); D3Q7 rest, +x, -x,
- *    +y, -y, +z, -z.
+ *    FP32, direction-major, [Q + NS][N]: rows 0..Q-1 hold f_i - w_i of the
+ *    pre-collision (streamed) fluid populations, rows Q..Q+NS-1 hold
+ *    Phi_k - w_k of the NS scalar populations (w the lattice weights; both
+ *    sets are held as deviations from their rest state rho = 1, chi = 1).
+ *    Direction orders: D3Q19 as in Eq. 23; D3Q27 as Eq. 23 followed by the
+ *    corners (1,1,1), (-1,-1,-1), (1,1,-1), (-1,-1,1), (1,-1,1), (-1,1,-1),
+ *    (-1,1,1), (1,-1,-1); D3Q7 rest, +x, -x, +y, -y, +z, -z; D3Q6 as D3Q7
+ *    without the rest population (Eq. 31).
  */
 #ifndef LBM_H
 #define LBM_H
@@ -68,6 +69,15 @@ typedef enum lbm_model {
                               rates of order >= 3 equal to 1 */
 } lbm_model;
 
+typedef enum lbm_scalar {
+    LBM_SCALAR_Q7 = 0,   /* D3Q7 BGK, c_sPhi^2 = 1/4 (both models) */
+    LBM_SCALAR_Q6 = 1,   /* D3Q6 BGK as printed in Eq. 29-31 (RAFSINE): w = 1/6,
+                            c_s^2 = 1/3, no rest population; BGK model only */
+    LBM_SCALAR_Q27 = 2   /* D3Q27 factorized central moments (Eq. 37-51,
+                            VirtualFluids), all rates of order >= 2 equal to 1;
+                            cumulant model only */
+} lbm_scalar;
+
 typedef enum lbm_storage {
     LBM_FP32 = 0,   /* populations stored as FP32: f - w and Phi - w */
     LBM_FP16S = 1,  /* FP16, scale_f * (f - w) and scale_phi * (Phi - w), RN rounding */
@@ -85,7 +95,7 @@ typedef enum lbm_storage {
 
 typedef struct lbm_params {
     int32_t nx, ny, nz;       /* nodes; 1 <= nx, ny, nz; nx*ny*nz < 2^31;
-                                 (Q+7)*nx*ny*nz < 2^32; ny, nz <= 65535 */
+                                 (Q+NS)*nx*ny*nz < 2^32; ny, nz <= 65535 */
     int32_t model;            /* lbm_model */
     int32_t storage;          /* lbm_storage */
     int32_t flags;            /* LBM_FLAG_* */
@@ -107,6 +117,8 @@ typedef struct lbm_params {
     double front_threshold;   /* span-averaged chi threshold of the front (0.02) */
     double scale_f;           /* 16-bit storage scale of f - w (power of two) */
     double scale_phi;         /* 16-bit storage scale of Phi - w (power of two) */
+    int32_t scalar;           /* lbm_scalar */
+    int32_t pad_;
 } lbm_params;
 
 typedef struct lbm_diagnostics {
@@ -134,7 +146,7 @@ LBM_API const char* lbm_last_error(const lbm_ctx* ctx);
 LBM_API lbm_status lbm_validate(const lbm_params* p);
 
 /* Bytes of device workspace lbm_init needs for p; 0 when p is invalid.
- * Populations take (Q + 7) * N * (4 or 2) bytes; the rest is a few N/nx-sized
+ * Populations take (Q + NS) * N * (4 or 2) bytes; the rest is a few N/nx-sized
  * staging and reduction buffers. */
 LBM_API size_t lbm_workspace_bytes(const lbm_params* p);
 
@@ -158,7 +170,7 @@ LBM_API lbm_status lbm_set_scalar(lbm_ctx* ctx, const float* chi0);
 LBM_API lbm_status lbm_step(lbm_ctx* ctx, int32_t nsteps);
 
 /* One time step that also writes the pre-collision state of the current
- * step, in the canonical layout, to state_out ((Q + 7) * N floats, device).
+ * step, in the canonical layout, to state_out ((Q + NS) * N floats, device).
  * Used to record the forward trajectory for the adjoint. */
 LBM_API lbm_status lbm_step_save(lbm_ctx* ctx, float* state_out);
 
@@ -177,7 +189,7 @@ LBM_API lbm_status lbm_diag(lbm_ctx* ctx, lbm_diagnostics* out_host);
  * Asynchronous.  Used for the time-integrated friction objective. */
 LBM_API lbm_status lbm_fw_accumulate(lbm_ctx* ctx, double* acc_dev, double weight);
 
-/* Copies the current state to dst ((Q + 7) * N floats, canonical layout,
+/* Copies the current state to dst ((Q + NS) * N floats, canonical layout,
  * device).  Asynchronous. */
 LBM_API lbm_status lbm_get_state(lbm_ctx* ctx, float* dst);
 
@@ -190,8 +202,8 @@ LBM_API lbm_status lbm_set_state(lbm_ctx* ctx, const float* src, int64_t step);
  *   lam_n = (dT/ds_n)^T lam_next + w_fw * dF_w(s_n)/ds_n,
  *   *dJdCs_dev += lam_next . dT/dC_s (s_n),
  * where T is the time step of lbm_step, s_n = state_n (canonical layout,
- * device, (Q + 7) * N floats) is the state it was applied to, and lam_next,
- * lam_n are adjoint states in the canonical layout (device, (Q + 7) * N
+ * device, (Q + NS) * N floats) is the state it was applied to, and lam_next,
+ * lam_n are adjoint states in the canonical layout (device, (Q + NS) * N
  * floats; lam_next == NULL means zero).  lam_n must not alias lam_next or
  * state_n.  dJdCs_dev: one device double, accumulated.  Asynchronous.
  * LBM_ERR_STATE for the cumulant model. */
@@ -201,7 +213,7 @@ LBM_API lbm_status lbm_adjoint_step(lbm_ctx* ctx, const float* state_n, const fl
 /* Forward pass of the time-integrated bottom friction J = sum_n F_w(s_n):
  * advances nsteps >= 0 steps from the current state s_0, adding F_w of each
  * new state to *J_dev (one device double), and, when ckpt is not NULL,
- * copies the state before relative step n to ckpt + (n / K) (Q + 7) N for
+ * copies the state before relative step n to ckpt + (n / K) (Q + NS) N for
  * every n % K == 0 (canonical layout, device; ceil(nsteps / K) states).
  * Asynchronous. */
 LBM_API lbm_status lbm_objective_forward(lbm_ctx* ctx, int32_t nsteps, int32_t K, float* ckpt,
@@ -209,7 +221,7 @@ LBM_API lbm_status lbm_objective_forward(lbm_ctx* ctx, int32_t nsteps, int32_t K
 
 /* One reverse segment of the adjoint of J (BGK model, FP32 storage):
  * from the checkpoint ckpt = s_{n0}, recomputes s_{n0+1} .. s_{n0+k-1} into
- * seg + j (Q + 7) N (j = 1 .. k-1; seg holds k states, slot 0 unused) with
+ * seg + j (Q + NS) N (j = 1 .. k-1; seg holds k states, slot 0 unused) with
  * an out-of-place step of the same arithmetic, then applies k adjoint steps
  * backwards: on entry lam holds lam_{n0+k}, on return lam_{n0} (w_fw = 1
  * for n >= 1, 0 for n = 0).  tmp: a second adjoint buffer, distinct from
@@ -224,7 +236,7 @@ LBM_API lbm_status lbm_adjoint_segment(lbm_ctx* ctx, const float* ckpt, int64_t 
 LBM_API lbm_status lbm_adjoint_chi0(lbm_ctx* ctx, const float* lam0, float* grad_chi0);
 
 /* Diagnostics (as lbm_diag) of a state the caller holds in the canonical
- * layout (state: (Q + 7) * N floats, device), for callers that cannot
+ * layout (state: (Q + NS) * N floats, device), for callers that cannot
  * allocate device memory (an allocator callback or out-of-memory handler, a
  * pool fixed before this library loads): it needs no context and no
  * workspace and calls no cudaMalloc, cudaFree or allocating routine.  The

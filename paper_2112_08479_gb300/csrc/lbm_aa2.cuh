@@ -90,53 +90,56 @@ __device__ __forceinline__ Stencil2 make_stencil2(const KParams& kp, int x, int 
 // loads, predicated, (3) the shuffles that hand the shifted element across.
 // A z wall (uniform over the block) turns a direction into a bounce-back from
 // the node's own slot, selected without branching.
-template <int Q, bool ODD, typename S>
+template <int Q, bool ODD, typename S, int D0 = 0>
 __device__ __forceinline__ void gather2(const KParams& kp, const S* __restrict__ a,
                                         const Stencil2& st, float (&v0)[Q], float (&v1)[Q]) {
     const unsigned N = kp.N;
     float P0[Q], P1[Q], E[Q];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        unsigned off = (unsigned)i * N + st.n;
+    for (int k = 0; k < Q; ++k) {
+        const int i = k + D0;       // direction; population k lives in row k
+        unsigned off = (unsigned)k * N + st.n;
         if (ODD && i != 0) {
             const int dy = -cy27(i), dz = -cz27(i);
-            const unsigned row = (unsigned)opp(i) * N + st.zr[dz + 1] + st.yr[dy + 1];
+            const unsigned row = (unsigned)(opp(i) - D0) * N + st.zr[dz + 1] + st.yr[dy + 1];
             off = st.zo[dz + 1] ? row + st.x : off;
         }
-        P0[i] = 0.0f; P1[i] = 0.0f;
-        if (st.active) PairIO<S>::ld(a + off, P0[i], P1[i]);
+        P0[k] = 0.0f; P1[k] = 0.0f;
+        if (st.active) PairIO<S>::ld(a + off, P0[k], P1[k]);
     }
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        E[i] = 0.0f;
+    for (int k = 0; k < Q; ++k) {
+        const int i = k + D0;
+        E[k] = 0.0f;
         const int dx = -cx27(i), dy = -cy27(i), dz = -cz27(i);
         if (ODD && i != 0 && dx != 0) {
-            const unsigned row = (unsigned)opp(i) * N + st.zr[dz + 1] + st.yr[dy + 1];
-            const unsigned own = (unsigned)i * N + st.n;
+            const unsigned row = (unsigned)(opp(i) - D0) * N + st.zr[dz + 1] + st.yr[dy + 1];
+            const unsigned own = (unsigned)k * N + st.n;
             unsigned off;
             bool need;
             if (dx < 0) { need = st.left; off = st.xmo ? row + st.xm : own; }
             else { need = st.right; off = st.xp2o ? row + st.xp2 : own + 1; }
             need = need && st.active && st.zo[dz + 1];
-            if (need) E[i] = Store<S>::ld(a + off);
+            if (need) E[k] = Store<S>::ld(a + off);
         }
     }
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
+    for (int k = 0; k < Q; ++k) {
+        const int i = k + D0;
         const int dx = -cx27(i), dz = -cz27(i);
-        v0[i] = P0[i]; v1[i] = P1[i];
+        v0[k] = P0[k]; v1[k] = P1[k];
         if (ODD && i != 0 && dx != 0) {
             const bool in = st.zo[dz + 1];
             if (dx < 0) {
                 // node x needs element x - 1, node x + 1 needs element x
-                const float e = __shfl_up_sync(0xffffffffu, P1[i], 1);
-                v0[i] = in ? (st.left ? E[i] : e) : P0[i];
-                v1[i] = in ? P0[i] : P1[i];
+                const float e = __shfl_up_sync(0xffffffffu, P1[k], 1);
+                v0[k] = in ? (st.left ? E[k] : e) : P0[k];
+                v1[k] = in ? P0[k] : P1[k];
             } else {
                 // node x needs element x + 1, node x + 1 needs element x + 2
-                const float e = __shfl_down_sync(0xffffffffu, P0[i], 1);
-                v0[i] = in ? P1[i] : P0[i];
-                v1[i] = in ? (st.right ? E[i] : e) : P1[i];
+                const float e = __shfl_down_sync(0xffffffffu, P0[k], 1);
+                v0[k] = in ? P1[k] : P0[k];
+                v1[k] = in ? (st.right ? E[k] : e) : P1[k];
             }
         }
     }
@@ -145,45 +148,47 @@ __device__ __forceinline__ void gather2(const KParams& kp, const S* __restrict__
 // The scatter first exchanges the shifted elements, then issues every store
 // under a predicate (pair stores for the interior lanes, single-element
 // stores for the edge lanes, pair stores into the own slots at a z wall).
-template <int Q, bool ODD, typename S>
+template <int Q, bool ODD, typename S, int D0 = 0>
 __device__ __forceinline__ void scatter2(const KParams& kp, S* __restrict__ a, const Stencil2& st,
                                          const float (&v0)[Q], const float (&v1)[Q]) {
     const unsigned N = kp.N;
     float X[Q];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
+    for (int k = 0; k < Q; ++k) {
+        const int i = k + D0;
         const int dx = cx27(i);
-        X[i] = 0.0f;
-        if (ODD && i != 0 && dx > 0) X[i] = __shfl_up_sync(0xffffffffu, v1[i], 1);
-        if (ODD && i != 0 && dx < 0) X[i] = __shfl_down_sync(0xffffffffu, v0[i], 1);
+        X[k] = 0.0f;
+        if (ODD && i != 0 && dx > 0) X[k] = __shfl_up_sync(0xffffffffu, v1[k], 1);
+        if (ODD && i != 0 && dx < 0) X[k] = __shfl_down_sync(0xffffffffu, v0[k], 1);
     }
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
+    for (int k = 0; k < Q; ++k) {
+        const int i = k + D0;
         const int dx = cx27(i), dy = cy27(i), dz = cz27(i);
-        const unsigned own = (unsigned)opp(i) * N + st.n;
+        const unsigned own = (unsigned)(opp(i) - D0) * N + st.n;
         if (!ODD || i == 0) {
-            if (st.active) PairIO<S>::st(a + own, v0[i], v1[i]);
+            if (st.active) PairIO<S>::st(a + own, v0[k], v1[k]);
             continue;
         }
         const bool in = st.zo[dz + 1];
-        const unsigned row = (unsigned)i * N + st.zr[dz + 1] + st.yr[dy + 1];
-        if (st.active && !in) PairIO<S>::st(a + own, v0[i], v1[i]);
+        const unsigned row = (unsigned)k * N + st.zr[dz + 1] + st.yr[dy + 1];
+        if (st.active && !in) PairIO<S>::st(a + own, v0[k], v1[k]);
         if (dx == 0) {
-            if (st.active && in) PairIO<S>::st(a + row + st.x, v0[i], v1[i]);
+            if (st.active && in) PairIO<S>::st(a + row + st.x, v0[k], v1[k]);
         } else if (dx > 0) {
             // element x receives node x - 1, element x + 1 receives node x
-            if (st.active && in && !st.left) PairIO<S>::st(a + row + st.x, X[i], v0[i]);
-            if (st.active && in && st.left) Store<S>::st(a + row + st.x + 1, v0[i]);
+            if (st.active && in && !st.left) PairIO<S>::st(a + row + st.x, X[k], v0[k]);
+            if (st.active && in && st.left) Store<S>::st(a + row + st.x + 1, v0[k]);
             // node x + 1 -> x + 2 across the warp edge, or back from an x wall
             if (st.active && in && st.right)
-                Store<S>::st(a + (st.xp2o ? row + st.xp2 : own + 1), v1[i]);
+                Store<S>::st(a + (st.xp2o ? row + st.xp2 : own + 1), v1[k]);
         } else {
             // element x receives node x + 1, element x + 1 receives node x + 2
-            if (st.active && in && !st.right) PairIO<S>::st(a + row + st.x, v1[i], X[i]);
-            if (st.active && in && st.right) Store<S>::st(a + row + st.x, v1[i]);
+            if (st.active && in && !st.right) PairIO<S>::st(a + row + st.x, v1[k], X[k]);
+            if (st.active && in && st.right) Store<S>::st(a + row + st.x, v1[k]);
             // node x -> x - 1 across the warp edge, or back from an x wall
             if (st.active && in && st.left)
-                Store<S>::st(a + (st.xmo ? row + st.xm : own), v0[i]);
+                Store<S>::st(a + (st.xmo ? row + st.xm : own), v0[k]);
         }
     }
 }

@@ -35,6 +35,10 @@ struct Layout {
 };
 
 int q_of(const lbm_params* p) { return p->model == LBM_CUMULANT_Q27 ? 27 : 19; }
+int ns_of(const lbm_params* p) {
+    return p->scalar == LBM_SCALAR_Q6 ? 6 : (p->scalar == LBM_SCALAR_Q27 ? 27 : 7);
+}
+Kind kind(const lbm_params* p) { return Kind{p->model, p->scalar, p->storage}; }
 size_t elem_size(const lbm_params* p) { return p->storage == LBM_FP32 ? 4 : 2; }
 
 bool finite(double v) { return isfinite(v) != 0; }
@@ -45,8 +49,14 @@ const char* check(const lbm_params* p) {
     if (p->ny > 65535 || p->nz > 65535) return "ny and nz must be <= 65535";
     if ((double)p->nx * p->ny * p->nz >= 2147483648.0) return "nx*ny*nz must be < 2^31";
     if (p->model != LBM_BGK_SMAG_Q19 && p->model != LBM_CUMULANT_Q27) return "unknown model";
-    if ((double)(q_of(p) + 7) * p->nx * p->ny * p->nz >= 4294967296.0)
-        return "(Q+7)*nx*ny*nz must be < 2^32 (32-bit element offsets)";
+    if (p->scalar != LBM_SCALAR_Q7 && p->scalar != LBM_SCALAR_Q6 && p->scalar != LBM_SCALAR_Q27)
+        return "unknown scalar lattice";
+    if (p->model == LBM_BGK_SMAG_Q19 && p->scalar == LBM_SCALAR_Q27)
+        return "the D3Q27 scalar runs with the cumulant model";
+    if (p->model == LBM_CUMULANT_Q27 && p->scalar == LBM_SCALAR_Q6)
+        return "the D3Q6 scalar runs with the BGK model";
+    if ((double)(q_of(p) + ns_of(p)) * p->nx * p->ny * p->nz >= 4294967296.0)
+        return "(Q+NS)*nx*ny*nz must be < 2^32 (32-bit element offsets)";
     if (p->storage != LBM_FP32 && p->storage != LBM_FP16S && p->storage != LBM_BF16S)
         return "unknown storage";
     if (p->flags & ~(LBM_FLAG_NO_COLLIDE | LBM_FLAG_PERIODIC_X | LBM_FLAG_PERIODIC_Z))
@@ -75,7 +85,7 @@ Layout layout(const lbm_params* p) {
     L.nblocks = diag_block_count(p->nx, p->nz);
     size_t o = 0;
     L.f = o;      o = up(o + (size_t)q_of(p) * N * es);
-    L.phi = o;    o = up(o + 7 * N * es);
+    L.phi = o;    o = up(o + (size_t)ns_of(p) * N * es);
     L.stage = o;  o = up(o + N * sizeof(float));
     L.chibar = o; o = up(o + (size_t)p->nx * p->nz * sizeof(float));
     L.colmax = o; o = up(o + (size_t)p->nx * sizeof(unsigned));
@@ -95,8 +105,12 @@ KParams kparams(const lbm_params* p) {
     const double tau0 = 3.0 * p->nu + 0.5;                        // Eq. 25
     k.tau0 = (float)tau0;
     k.A = (float)(18.0 * sqrt(2.0) * p->cs_smag * p->cs_smag);    // Eq. 34, R3
-    k.taup0 = (float)(0.5 + 4.0 * p->D);                          // Eq. 30, D3Q7
-    k.kT = p->model == LBM_BGK_SMAG_Q19 ? (float)(4.0 / (3.0 * p->sc_t)) : 0.0f;  // Eq. 35
+    // D = c_s^2 (tau_Phi - 1/2) (Eq. 30): c_s^2 = 1/4 on D3Q7, 1/3 on D3Q6
+    const double cs2 = p->scalar == LBM_SCALAR_Q6 ? 1.0 / 3.0 : 0.25;
+    k.taup0 = (float)(0.5 + p->D / cs2);
+    // tau_Phi = taup0 + (nu_T / Sc_T) / c_s^2, nu_T = (tau - tau0) / 3 (Eq. 35)
+    k.kT = p->model == LBM_BGK_SMAG_Q19 ? (float)(1.0 / (3.0 * p->sc_t * cs2)) : 0.0f;
+    k.omD = (float)(1.0 / (3.0 * p->D + 0.5));                    // Eq. 51
     k.om1 = (float)(1.0 / tau0);                                  // Eq. 58
     k.om2 = (float)p->omega_bulk;
     k.gx = (float)(p->gprime * p->eg[0]);                         // Eq. 11
@@ -185,7 +199,7 @@ lbm_status lbm_init(const lbm_params* p, void* workspace, size_t bytes, void* cu
     c->v.ddiag = (DevDiag*)(w + L.ddiag);
     c->v.devflags = (int*)(w + L.ddiag + sizeof(DevDiag));
     c->v.diag_blocks = L.nblocks;
-    cudaError_t e = launch_init(c->kp, p->model, p->storage, c->v, nullptr, p->x0, p->noise_amp,
+    cudaError_t e = launch_init(c->kp, kind(p), c->v, nullptr, p->x0, p->noise_amp,
                                 p->seed, c->stream);
     if (e != cudaSuccess) {
         snprintf(g_err, sizeof g_err, "init launch: %s", cudaGetErrorString(e));
@@ -204,7 +218,7 @@ lbm_status lbm_set_scalar(lbm_ctx* c, const float* chi0) {
     cudaError_t e = cudaMemcpyAsync(c->v.stage, chi0, (size_t)c->kp.N * sizeof(float),
                                     cudaMemcpyDefault, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "set_scalar copy");
-    e = launch_init(c->kp, c->p.model, c->p.storage, c->v, c->v.stage, 0, 0.0, 0, c->stream);
+    e = launch_init(c->kp, kind(&c->p), c->v, c->v.stage, 0, 0.0, 0, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "set_scalar init");
     c->step = 0;
     c->odd = 0;
@@ -215,7 +229,7 @@ lbm_status lbm_step(lbm_ctx* c, int32_t nsteps) {
     if (!c) return arg_fail(nullptr, "ctx is NULL");
     if (nsteps < 0) return arg_fail(c, "nsteps must be >= 0");
     for (int32_t s = 0; s < nsteps; ++s) {
-        cudaError_t e = launch_step(c->kp, c->p.model, c->p.storage, c->odd != 0, c->v.f, c->v.phi,
+        cudaError_t e = launch_step(c->kp, kind(&c->p), c->odd != 0, c->v.f, c->v.phi,
                                     nullptr, c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "step launch");
         c->odd ^= 1;
@@ -227,7 +241,7 @@ lbm_status lbm_step(lbm_ctx* c, int32_t nsteps) {
 lbm_status lbm_step_save(lbm_ctx* c, float* state_out) {
     if (!c) return arg_fail(nullptr, "ctx is NULL");
     if (!state_out) return arg_fail(c, "state_out is NULL");
-    cudaError_t e = launch_step(c->kp, c->p.model, c->p.storage, c->odd != 0, c->v.f, c->v.phi,
+    cudaError_t e = launch_step(c->kp, kind(&c->p), c->odd != 0, c->v.f, c->v.phi,
                                 state_out, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "step launch");
     c->odd ^= 1;
@@ -238,7 +252,7 @@ lbm_status lbm_step_save(lbm_ctx* c, float* state_out) {
 lbm_status lbm_macros(lbm_ctx* c, float* rho, float* u, float* chi) {
     if (!c) return arg_fail(nullptr, "ctx is NULL");
     if (!rho && !u && !chi) return LBM_OK;
-    cudaError_t e = launch_macros(c->kp, c->p.model, c->p.storage, c->odd != 0, c->v, rho, u, chi,
+    cudaError_t e = launch_macros(c->kp, kind(&c->p), c->odd != 0, c->v, rho, u, chi,
                                   c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "macros launch");
     return LBM_OK;
@@ -247,7 +261,7 @@ lbm_status lbm_macros(lbm_ctx* c, float* rho, float* u, float* chi) {
 lbm_status lbm_diag(lbm_ctx* c, lbm_diagnostics* out) {
     if (!c) return arg_fail(nullptr, "ctx is NULL");
     if (!out) return arg_fail(c, "out is NULL");
-    cudaError_t e = launch_diag(c->kp, c->p.model, c->p.storage, c->odd != 0, c->v,
+    cudaError_t e = launch_diag(c->kp, kind(&c->p), c->odd != 0, c->v,
                                 c->p.front_threshold, c->p.x0, (double)c->p.H, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "diag launch");
     struct { DevDiag d; int flags[2]; } rec;
@@ -274,7 +288,7 @@ lbm_status lbm_fw_accumulate(lbm_ctx* c, double* acc_dev, double weight) {
     if (!c) return arg_fail(nullptr, "ctx is NULL");
     if (!acc_dev) return arg_fail(c, "acc_dev is NULL");
     if (!isfinite(weight)) return arg_fail(c, "weight must be finite");
-    cudaError_t e = launch_fw_accumulate(c->kp, c->p.model, c->p.storage, c->odd != 0, c->v,
+    cudaError_t e = launch_fw_accumulate(c->kp, kind(&c->p), c->odd != 0, c->v,
                                          acc_dev, weight, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "fw launch");
     return LBM_OK;
@@ -283,7 +297,7 @@ lbm_status lbm_fw_accumulate(lbm_ctx* c, double* acc_dev, double weight) {
 lbm_status lbm_get_state(lbm_ctx* c, float* dst) {
     if (!c) return arg_fail(nullptr, "ctx is NULL");
     if (!dst) return arg_fail(c, "dst is NULL");
-    cudaError_t e = launch_get_state(c->kp, c->p.model, c->p.storage, c->odd != 0, c->v, dst,
+    cudaError_t e = launch_get_state(c->kp, kind(&c->p), c->odd != 0, c->v, dst,
                                      c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "get_state launch");
     return LBM_OK;
@@ -293,7 +307,7 @@ lbm_status lbm_set_state(lbm_ctx* c, const float* src, int64_t step) {
     if (!c) return arg_fail(nullptr, "ctx is NULL");
     if (!src) return arg_fail(c, "src is NULL");
     if (step < 0) return arg_fail(c, "step must be >= 0");
-    cudaError_t e = launch_set_state(c->kp, c->p.model, c->p.storage, c->v, src, c->stream);
+    cudaError_t e = launch_set_state(c->kp, kind(&c->p), c->v, src, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "set_state launch");
     c->step = step;
     c->odd = 0;
@@ -303,8 +317,8 @@ lbm_status lbm_set_state(lbm_ctx* c, const float* src, int64_t step) {
 lbm_status lbm_adjoint_step(lbm_ctx* c, const float* state_n, const float* lam_next, float* lam_n,
                             double* dJdCs_dev, double w_fw) {
     if (!c) return arg_fail(nullptr, "ctx is NULL");
-    if (c->p.model != LBM_BGK_SMAG_Q19) {
-        snprintf(c->err, sizeof c->err, "the adjoint exists for the BGK model only");
+    if (c->p.model != LBM_BGK_SMAG_Q19 || c->p.scalar != LBM_SCALAR_Q7) {
+        snprintf(c->err, sizeof c->err, "the adjoint exists for the BGK model with the D3Q7 scalar");
         return LBM_ERR_STATE;
     }
     if (!state_n || !lam_n) return arg_fail(c, "state_n and lam_n must not be NULL");
@@ -322,19 +336,19 @@ lbm_status lbm_objective_forward(lbm_ctx* c, int32_t nsteps, int32_t K, float* c
     if (!c) return arg_fail(nullptr, "ctx is NULL");
     if (nsteps < 0 || K < 1) return arg_fail(c, "nsteps must be >= 0 and K >= 1");
     if (!J_dev) return arg_fail(c, "J_dev is NULL");
-    const size_t S = (size_t)(q_of(&c->p) + 7) * c->kp.N;
+    const size_t S = (size_t)(q_of(&c->p) + ns_of(&c->p)) * c->kp.N;
     for (int32_t n = 0; n < nsteps; ++n) {
         cudaError_t e = cudaSuccess;
         if (ckpt && n % K == 0)
-            e = launch_get_state(c->kp, c->p.model, c->p.storage, c->odd != 0, c->v,
+            e = launch_get_state(c->kp, kind(&c->p), c->odd != 0, c->v,
                                  ckpt + (size_t)(n / K) * S, c->stream);
         if (e == cudaSuccess)
-            e = launch_step(c->kp, c->p.model, c->p.storage, c->odd != 0, c->v.f, c->v.phi,
+            e = launch_step(c->kp, kind(&c->p), c->odd != 0, c->v.f, c->v.phi,
                             nullptr, c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "objective forward launch");
         c->odd ^= 1;
         ++c->step;
-        e = launch_fw_accumulate(c->kp, c->p.model, c->p.storage, c->odd != 0, c->v, J_dev, 1.0,
+        e = launch_fw_accumulate(c->kp, kind(&c->p), c->odd != 0, c->v, J_dev, 1.0,
                                  c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "objective forward launch");
     }
@@ -344,14 +358,16 @@ lbm_status lbm_objective_forward(lbm_ctx* c, int32_t nsteps, int32_t K, float* c
 lbm_status lbm_adjoint_segment(lbm_ctx* c, const float* ckpt, int64_t n0, int32_t k, float* seg,
                                float* lam, float* tmp, double* dJdCs_dev) {
     if (!c) return arg_fail(nullptr, "ctx is NULL");
-    if (c->p.model != LBM_BGK_SMAG_Q19 || c->p.storage != LBM_FP32) {
-        snprintf(c->err, sizeof c->err, "the adjoint exists for the BGK model with FP32 storage");
+    if (c->p.model != LBM_BGK_SMAG_Q19 || c->p.storage != LBM_FP32 ||
+        c->p.scalar != LBM_SCALAR_Q7) {
+        snprintf(c->err, sizeof c->err,
+                 "the adjoint exists for the BGK model with the D3Q7 scalar and FP32 storage");
         return LBM_ERR_STATE;
     }
     if (k < 1 || n0 < 0) return arg_fail(c, "k must be >= 1 and n0 >= 0");
     if (!ckpt || !lam || !tmp || (k > 1 && !seg)) return arg_fail(c, "NULL buffer");
     if (lam == tmp) return arg_fail(c, "lam and tmp must differ");
-    const size_t S = (size_t)(q_of(&c->p) + 7) * c->kp.N;
+    const size_t S = (size_t)(q_of(&c->p) + ns_of(&c->p)) * c->kp.N;
     const float dAdCs = (float)(36.0 * sqrt(2.0) * c->p.cs_smag);
     cudaError_t e = cudaSuccess;
     // recompute s_{n0+1} .. s_{n0+k-1} into seg[1 .. k-1]
@@ -379,8 +395,8 @@ lbm_status lbm_adjoint_segment(lbm_ctx* c, const float* ckpt, int64_t n0, int32_
 lbm_status lbm_adjoint_chi0(lbm_ctx* c, const float* lam0, float* grad_chi0) {
     if (!c) return arg_fail(nullptr, "ctx is NULL");
     if (!lam0 || !grad_chi0) return arg_fail(c, "lam0 and grad_chi0 must not be NULL");
-    if (c->p.model != LBM_BGK_SMAG_Q19) {
-        snprintf(c->err, sizeof c->err, "the adjoint exists for the BGK model only");
+    if (c->p.model != LBM_BGK_SMAG_Q19 || c->p.scalar != LBM_SCALAR_Q7) {
+        snprintf(c->err, sizeof c->err, "the adjoint exists for the BGK model with the D3Q7 scalar");
         return LBM_ERR_STATE;
     }
     cudaError_t e = launch_adjoint_chi0(c->kp, lam0, grad_chi0, c->stream);

@@ -22,18 +22,19 @@ template <typename S>
 __device__ __forceinline__ constexpr bool is16() { return !std::is_same<S, float>::value; }
 
 // rho - 1, u (with the half-force shift, Eq. 20) and chi - 1 at node n.
-template <int Q, bool ODD, typename S>
+template <int Q, int SL, bool ODD, typename S>
 __device__ __forceinline__ void node_macros(const KParams& kp, const S* __restrict__ f,
                                             const S* __restrict__ phi, int x, int y, int z,
                                             unsigned n, float& drho, float& ux, float& uy,
                                             float& uz, float& chit) {
+    constexpr int NS = ScalarLat<SL>::NS;
     const Stencil st = make_stencil(kp, x, y, z);
-    float fv[Q], pv[7];
+    float fv[Q], pv[NS];
     gather<Q, ODD>(kp, f, st, fv);
-    gather<7, ODD>(kp, phi, st, pv);
+    gather<NS, ODD, S, ScalarLat<SL>::D0>(kp, phi, st, pv);
     float c = 0.0f;   // chi - 1 (Phi is held as Phi - w)
 #pragma unroll
-    for (int k = 0; k < 7; ++k) c += pv[k];
+    for (int k = 0; k < NS; ++k) c += pv[k];
     if (is16<S>()) c *= kp.isp;
     float d = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
 #pragma unroll
@@ -64,7 +65,7 @@ __device__ __forceinline__ unsigned long long splitmix64(unsigned long long s) {
     return z ^ (z >> 31);
 }
 
-template <int Q, typename S>
+template <int Q, int SL, typename S>
 __global__ void init_kernel(KParams kp, S* __restrict__ f, S* __restrict__ phi,
                             const float* __restrict__ chi0, int x0, double amp,
                             unsigned long long seed) {
@@ -87,10 +88,10 @@ __global__ void init_kernel(KParams kp, S* __restrict__ f, S* __restrict__ phi,
 #pragma unroll
     for (int i = 0; i < Q; ++i) Store<S>::st(f + (size_t)i * N + n, 0.0f);
 #pragma unroll
-    for (int k = 0; k < 7; ++k) Store<S>::st(phi + (size_t)k * N + n, kp.sp * (w7(k) * c));
+    for (int k = 0; k < ScalarLat<SL>::NS; ++k)
+        Store<S>::st(phi + (size_t)k * N + n, kp.sp * (ScalarLat<SL>::w(k) * c));
 }
 
-template <int Q, typename S>
 __global__ void fill_keys_kernel(unsigned* __restrict__ keys, int n, int* __restrict__ flags,
                                  int reset_flags) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -99,7 +100,7 @@ __global__ void fill_keys_kernel(unsigned* __restrict__ keys, int n, int* __rest
 }
 
 // ---------------------------------------------------------------------------
-template <int Q, bool ODD, typename S>
+template <int Q, int SL, bool ODD, typename S>
 __global__ void macros_kernel(KParams kp, const S* __restrict__ f, const S* __restrict__ phi,
                               float* __restrict__ rho, float* __restrict__ u,
                               float* __restrict__ chi) {
@@ -108,32 +109,33 @@ __global__ void macros_kernel(KParams kp, const S* __restrict__ f, const S* __re
     const int y = blockIdx.y, z = blockIdx.z;
     const unsigned n = (unsigned)x + (unsigned)kp.nx * ((unsigned)y + (unsigned)kp.ny * (unsigned)z);
     float d, ux, uy, uz, c;
-    node_macros<Q, ODD>(kp, f, phi, x, y, z, n, d, ux, uy, uz, c);
+    node_macros<Q, SL, ODD>(kp, f, phi, x, y, z, n, d, ux, uy, uz, c);
     const size_t N = kp.N;
     if (rho) rho[n] = 1.0f + d;
     if (u) { u[n] = ux; u[N + n] = uy; u[2 * N + n] = uz; }
     if (chi) chi[n] = 1.0f + c;
 }
 
-template <int Q, bool ODD, typename S>
+template <int Q, int SL, bool ODD, typename S>
 __global__ void get_state_kernel(KParams kp, const S* __restrict__ f, const S* __restrict__ phi,
                                  float* __restrict__ dst) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= kp.nx) return;
     const int y = blockIdx.y, z = blockIdx.z;
+    constexpr int NS = ScalarLat<SL>::NS;
     const Stencil st = make_stencil(kp, x, y, z);
     const unsigned n = st.n;
-    float fv[Q], pv[7];
+    float fv[Q], pv[NS];
     gather<Q, ODD>(kp, f, st, fv);
-    gather<7, ODD>(kp, phi, st, pv);
+    gather<NS, ODD, S, ScalarLat<SL>::D0>(kp, phi, st, pv);
     const size_t N = kp.N;
 #pragma unroll
     for (int i = 0; i < Q; ++i) dst[(size_t)i * N + n] = is16<S>() ? fv[i] * kp.isf : fv[i];
 #pragma unroll
-    for (int k = 0; k < 7; ++k) dst[(size_t)(Q + k) * N + n] = is16<S>() ? pv[k] * kp.isp : pv[k];
+    for (int k = 0; k < NS; ++k) dst[(size_t)(Q + k) * N + n] = is16<S>() ? pv[k] * kp.isp : pv[k];
 }
 
-template <int Q, typename S>
+template <int Q, int SL, typename S>
 __global__ void set_state_kernel(KParams kp, S* __restrict__ f, S* __restrict__ phi,
                                  const float* __restrict__ src) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -147,7 +149,7 @@ __global__ void set_state_kernel(KParams kp, S* __restrict__ f, S* __restrict__ 
         Store<S>::st(f + (size_t)i * N + n, is16<S>() ? v * kp.sf : v);
     }
 #pragma unroll
-    for (int k = 0; k < 7; ++k) {
+    for (int k = 0; k < ScalarLat<SL>::NS; ++k) {
         const float v = src[(size_t)(Q + k) * N + n];
         Store<S>::st(phi + (size_t)k * N + n, is16<S>() ? v * kp.sp : v);
     }
@@ -174,7 +176,7 @@ __device__ __forceinline__ void pair_add(float& s, float& c, float t, float d) {
 
 constexpr int DIAG_BX = 128;
 
-template <int Q, bool ODD, typename S>
+template <int Q, int SL, bool ODD, typename S>
 __global__ void __launch_bounds__(DIAG_BX) diag_columns_kernel(
     KParams kp, const S* __restrict__ f, const S* __restrict__ phi, float* __restrict__ chibar,
     unsigned* __restrict__ colmax, double* __restrict__ part, float* __restrict__ fwpart,
@@ -190,7 +192,7 @@ __global__ void __launch_bounds__(DIAG_BX) diag_columns_kernel(
             const unsigned n =
                 (unsigned)x + (unsigned)kp.nx * ((unsigned)y + (unsigned)kp.ny * (unsigned)z);
             float d, ux, uy, uz, c;
-            node_macros<Q, ODD>(kp, f, phi, x, y, z, n, d, ux, uy, uz, c);
+            node_macros<Q, SL, ODD>(kp, f, phi, x, y, z, n, d, ux, uy, uz, c);
             kc.add(c);
             kr.add(d);
             ku.add(ux);
@@ -289,7 +291,7 @@ __global__ void __launch_bounds__(FIN_T) diag_finalize_kernel(
 }
 
 // Adds weight * F_w to *acc.  One thread per (x, y) of the bottom rows.
-template <int Q, bool ODD, typename S>
+template <int Q, int SL, bool ODD, typename S>
 __global__ void __launch_bounds__(128) fw_kernel(KParams kp, const S* __restrict__ f,
                                                  const S* __restrict__ phi, double* __restrict__ acc,
                                                  double weight) {
@@ -300,8 +302,8 @@ __global__ void __launch_bounds__(128) fw_kernel(KParams kp, const S* __restrict
         float d, ux0, ux1, uy, uz, c;
         const unsigned n0 = (unsigned)x + (unsigned)kp.nx * (unsigned)y;
         const unsigned n1 = n0 + kp.nxny;
-        node_macros<Q, ODD>(kp, f, phi, x, y, 0, n0, d, ux0, uy, uz, c);
-        node_macros<Q, ODD>(kp, f, phi, x, y, 1, n1, d, ux1, uy, uz, c);
+        node_macros<Q, SL, ODD>(kp, f, phi, x, y, 0, n0, d, ux0, uy, uz, c);
+        node_macros<Q, SL, ODD>(kp, f, phi, x, y, 1, n1, d, ux1, uy, uz, c);
         v = (double)(kp.nu * (9.0f * ux0 - ux1) * (1.0f / 3.0f));
     }
 #pragma unroll
@@ -329,79 +331,84 @@ static inline dim3 node_grid(const KParams& kp) { return dim3((kp.nx + 127) / 12
 
 unsigned diag_block_count(int nx, int nz) { return (unsigned)((nx + DIAG_BX - 1) / DIAG_BX) * nz; }
 
-// Calls fn.template operator()<Q, S>() for the model and storage at hand.
+// Calls fn.template operator()<Q, SL, S>() for the model, scalar lattice and
+// storage at hand.
+template <int Q, int SL, typename Fn>
+static cudaError_t dispatch_storage(int storage, Fn&& fn) {
+    if (storage == LBM_FP32) return fn.template operator()<Q, SL, float>();
+    if (storage == LBM_FP16S) return fn.template operator()<Q, SL, __half>();
+    if (storage == LBM_BF16S) return fn.template operator()<Q, SL, __nv_bfloat16>();
+    return cudaErrorInvalidValue;
+}
+
 template <typename Fn>
-static cudaError_t dispatch(int model, int storage, Fn&& fn) {
-    if (model == LBM_BGK_SMAG_Q19) {
-        if (storage == LBM_FP32) return fn.template operator()<19, float>();
-        if (storage == LBM_FP16S) return fn.template operator()<19, __half>();
-        if (storage == LBM_BF16S) return fn.template operator()<19, __nv_bfloat16>();
-    } else if (model == LBM_CUMULANT_Q27) {
-        if (storage == LBM_FP32) return fn.template operator()<27, float>();
-        if (storage == LBM_FP16S) return fn.template operator()<27, __half>();
-        if (storage == LBM_BF16S) return fn.template operator()<27, __nv_bfloat16>();
-    }
+static cudaError_t dispatch(Kind k, Fn&& fn) {
+    if (k.model == LBM_BGK_SMAG_Q19 && k.scalar == LBM_SCALAR_Q7) return dispatch_storage<19, 7>(k.storage, fn);
+    if (k.model == LBM_BGK_SMAG_Q19 && k.scalar == LBM_SCALAR_Q6) return dispatch_storage<19, 6>(k.storage, fn);
+    if (k.model == LBM_CUMULANT_Q27 && k.scalar == LBM_SCALAR_Q7) return dispatch_storage<27, 7>(k.storage, fn);
+    if (k.model == LBM_CUMULANT_Q27 && k.scalar == LBM_SCALAR_Q27) return dispatch_storage<27, 27>(k.storage, fn);
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_step(const KParams& kp, int model, int storage, bool odd, void* f, void* phi,
-                        float* save, cudaStream_t st) {
-    if (model == LBM_BGK_SMAG_Q19) return launch_bgk_step(kp, storage, odd, f, phi, save, st);
-    if (model == LBM_CUMULANT_Q27) return launch_cumulant_step(kp, storage, odd, f, phi, save, st);
+cudaError_t launch_step(const KParams& kp, Kind k, bool odd, void* f, void* phi, float* save,
+                        cudaStream_t st) {
+    if (k.model == LBM_BGK_SMAG_Q19) return launch_bgk_step(kp, k.storage, k.scalar, odd, f, phi, save, st);
+    if (k.model == LBM_CUMULANT_Q27)
+        return launch_cumulant_step(kp, k.storage, k.scalar, odd, f, phi, save, st);
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_init(const KParams& kp, int model, int storage, const Views& v, const float* chi0,
-                        int x0, double amp, uint64_t seed, cudaStream_t st) {
-    return dispatch(model, storage, [&]<int Q, typename S>() {
-        init_kernel<Q, S><<<node_grid(kp), 128, 0, st>>>(kp, (S*)v.f, (S*)v.phi, chi0, x0, amp,
-                                                          (unsigned long long)seed);
+cudaError_t launch_init(const KParams& kp, Kind k, const Views& v, const float* chi0, int x0,
+                        double amp, uint64_t seed, cudaStream_t st) {
+    return dispatch(k, [&]<int Q, int SL, typename S>() {
+        init_kernel<Q, SL, S><<<node_grid(kp), 128, 0, st>>>(kp, (S*)v.f, (S*)v.phi, chi0, x0, amp,
+                                                              (unsigned long long)seed);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        fill_keys_kernel<Q, S><<<(kp.nx + 255) / 256, 256, 0, st>>>(v.colmax, kp.nx, v.devflags, 1);
+        fill_keys_kernel<<<(kp.nx + 255) / 256, 256, 0, st>>>(v.colmax, kp.nx, v.devflags, 1);
         return cudaGetLastError();
     });
 }
 
-cudaError_t launch_macros(const KParams& kp, int model, int storage, bool odd, const Views& v,
-                          float* rho, float* u, float* chi, cudaStream_t st) {
-    return dispatch(model, storage, [&]<int Q, typename S>() {
+cudaError_t launch_macros(const KParams& kp, Kind k, bool odd, const Views& v, float* rho,
+                          float* u, float* chi, cudaStream_t st) {
+    return dispatch(k, [&]<int Q, int SL, typename S>() {
         if (odd)
-            macros_kernel<Q, true, S><<<node_grid(kp), 128, 0, st>>>(kp, (const S*)v.f, (const S*)v.phi, rho, u, chi);
+            macros_kernel<Q, SL, true, S><<<node_grid(kp), 128, 0, st>>>(kp, (const S*)v.f, (const S*)v.phi, rho, u, chi);
         else
-            macros_kernel<Q, false, S><<<node_grid(kp), 128, 0, st>>>(kp, (const S*)v.f, (const S*)v.phi, rho, u, chi);
+            macros_kernel<Q, SL, false, S><<<node_grid(kp), 128, 0, st>>>(kp, (const S*)v.f, (const S*)v.phi, rho, u, chi);
         return cudaGetLastError();
     });
 }
 
-cudaError_t launch_get_state(const KParams& kp, int model, int storage, bool odd, const Views& v,
-                             float* dst, cudaStream_t st) {
-    return dispatch(model, storage, [&]<int Q, typename S>() {
+cudaError_t launch_get_state(const KParams& kp, Kind k, bool odd, const Views& v, float* dst,
+                             cudaStream_t st) {
+    return dispatch(k, [&]<int Q, int SL, typename S>() {
         if (odd)
-            get_state_kernel<Q, true, S><<<node_grid(kp), 128, 0, st>>>(kp, (const S*)v.f, (const S*)v.phi, dst);
+            get_state_kernel<Q, SL, true, S><<<node_grid(kp), 128, 0, st>>>(kp, (const S*)v.f, (const S*)v.phi, dst);
         else
-            get_state_kernel<Q, false, S><<<node_grid(kp), 128, 0, st>>>(kp, (const S*)v.f, (const S*)v.phi, dst);
+            get_state_kernel<Q, SL, false, S><<<node_grid(kp), 128, 0, st>>>(kp, (const S*)v.f, (const S*)v.phi, dst);
         return cudaGetLastError();
     });
 }
 
-cudaError_t launch_set_state(const KParams& kp, int model, int storage, const Views& v,
-                             const float* src, cudaStream_t st) {
-    return dispatch(model, storage, [&]<int Q, typename S>() {
-        set_state_kernel<Q, S><<<node_grid(kp), 128, 0, st>>>(kp, (S*)v.f, (S*)v.phi, src);
+cudaError_t launch_set_state(const KParams& kp, Kind k, const Views& v, const float* src,
+                             cudaStream_t st) {
+    return dispatch(k, [&]<int Q, int SL, typename S>() {
+        set_state_kernel<Q, SL, S><<<node_grid(kp), 128, 0, st>>>(kp, (S*)v.f, (S*)v.phi, src);
         return cudaGetLastError();
     });
 }
 
-cudaError_t launch_diag(const KParams& kp, int model, int storage, bool odd, const Views& v,
-                        double threshold, int x0, double H, cudaStream_t st) {
-    return dispatch(model, storage, [&]<int Q, typename S>() {
+cudaError_t launch_diag(const KParams& kp, Kind k, bool odd, const Views& v, double threshold,
+                        int x0, double H, cudaStream_t st) {
+    return dispatch(k, [&]<int Q, int SL, typename S>() {
         dim3 grid((kp.nx + DIAG_BX - 1) / DIAG_BX, kp.nz);
         if (odd)
-            diag_columns_kernel<Q, true, S><<<grid, DIAG_BX, 0, st>>>(
+            diag_columns_kernel<Q, SL, true, S><<<grid, DIAG_BX, 0, st>>>(
                 kp, (const S*)v.f, (const S*)v.phi, v.chibar, v.colmax, v.part, v.fwpart, v.devflags);
         else
-            diag_columns_kernel<Q, false, S><<<grid, DIAG_BX, 0, st>>>(
+            diag_columns_kernel<Q, SL, false, S><<<grid, DIAG_BX, 0, st>>>(
                 kp, (const S*)v.f, (const S*)v.phi, v.chibar, v.colmax, v.part, v.fwpart, v.devflags);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -411,15 +418,15 @@ cudaError_t launch_diag(const KParams& kp, int model, int storage, bool odd, con
     });
 }
 
-cudaError_t launch_fw_accumulate(const KParams& kp, int model, int storage, bool odd,
-                                 const Views& v, double* acc, double weight, cudaStream_t st) {
+cudaError_t launch_fw_accumulate(const KParams& kp, Kind k, bool odd, const Views& v,
+                                 double* acc, double weight, cudaStream_t st) {
     if (kp.nz < 2) return cudaSuccess;
-    return dispatch(model, storage, [&]<int Q, typename S>() {
+    return dispatch(k, [&]<int Q, int SL, typename S>() {
         dim3 grid((kp.nx + 127) / 128, kp.ny);
         if (odd)
-            fw_kernel<Q, true, S><<<grid, 128, 0, st>>>(kp, (const S*)v.f, (const S*)v.phi, acc, weight);
+            fw_kernel<Q, SL, true, S><<<grid, 128, 0, st>>>(kp, (const S*)v.f, (const S*)v.phi, acc, weight);
         else
-            fw_kernel<Q, false, S><<<grid, 128, 0, st>>>(kp, (const S*)v.f, (const S*)v.phi, acc, weight);
+            fw_kernel<Q, SL, false, S><<<grid, 128, 0, st>>>(kp, (const S*)v.f, (const S*)v.phi, acc, weight);
         return cudaGetLastError();
     });
 }

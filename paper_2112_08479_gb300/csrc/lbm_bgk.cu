@@ -27,7 +27,7 @@
 
 namespace lbmgpu {
 
-template <bool ODD, bool SAVE, typename S>
+template <bool ODD, bool SAVE, typename S, int SL>
 __global__ void __launch_bounds__(128, LBM_STEP_MINB) bgk_step_kernel(KParams kp, S* __restrict__ f,
                                                        S* __restrict__ phi,
                                                        float* __restrict__ save) {
@@ -36,34 +36,36 @@ __global__ void __launch_bounds__(128, LBM_STEP_MINB) bgk_step_kernel(KParams kp
     const Stencil st = make_stencil(kp, x, blockIdx.y, blockIdx.z);
     const unsigned n = st.n;
 
-    float fv[19], pv[7];
+    constexpr int NS = ScalarLat<SL>::NS, D0 = ScalarLat<SL>::D0;
+    float fv[19], pv[NS];
     gather<19, ODD>(kp, f, st, fv);
-    gather<7, ODD>(kp, phi, st, pv);
+    gather<NS, ODD, S, D0>(kp, phi, st, pv);
     constexpr bool s16 = !std::is_same<S, float>::value;   // populations in storage units
     if (SAVE) {
         const size_t N = kp.N;
 #pragma unroll
         for (int i = 0; i < 19; ++i) save[(size_t)i * N + n] = s16 ? fv[i] * kp.isf : fv[i];
 #pragma unroll
-        for (int k = 0; k < 7; ++k) save[(size_t)(19 + k) * N + n] = s16 ? pv[k] * kp.isp : pv[k];
+        for (int k = 0; k < NS; ++k) save[(size_t)(19 + k) * N + n] = s16 ? pv[k] * kp.isp : pv[k];
     }
-    if (!(kp.flags & LBM_FLAG_NO_COLLIDE)) collide_bgk<s16>(kp, fv, pv);
+    if (!(kp.flags & LBM_FLAG_NO_COLLIDE)) collide_bgk<s16, SL>(kp, fv, pv);
     scatter<19, ODD>(kp, f, st, fv);
-    scatter<7, ODD>(kp, phi, st, pv);
+    scatter<NS, ODD, S, D0>(kp, phi, st, pv);
 }
 
 
 // Two x-adjacent nodes per thread (nx even): paired population accesses, see
 // lbm_aa2.cuh.  Same arithmetic per node as bgk_step_kernel.
-template <bool ODD, bool SAVE, typename S>
+template <bool ODD, bool SAVE, typename S, int SL>
 __global__ void __launch_bounds__(128, LBM_STEP2_MINB) bgk_step2_kernel(KParams kp, S* __restrict__ f,
                                                                     S* __restrict__ phi,
                                                                     float* __restrict__ save) {
     const int x = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     const Stencil2 st = make_stencil2(kp, x, blockIdx.y, blockIdx.z);
-    float f0[19], f1[19], p0[7], p1[7];
+    constexpr int NS = ScalarLat<SL>::NS, D0 = ScalarLat<SL>::D0;
+    float f0[19], f1[19], p0[NS], p1[NS];
     gather2<19, ODD>(kp, f, st, f0, f1);
-    gather2<7, ODD>(kp, phi, st, p0, p1);
+    gather2<NS, ODD, S, D0>(kp, phi, st, p0, p1);
     constexpr bool s16 = !std::is_same<S, float>::value;   // populations in storage units
     if (SAVE && st.active) {
         const unsigned N = kp.N;
@@ -72,51 +74,60 @@ __global__ void __launch_bounds__(128, LBM_STEP2_MINB) bgk_step2_kernel(KParams 
         for (int i = 0; i < 19; ++i)
             *reinterpret_cast<float2*>(save + (size_t)i * N + st.n) = make_float2(a * f0[i], a * f1[i]);
 #pragma unroll
-        for (int k = 0; k < 7; ++k)
+        for (int k = 0; k < NS; ++k)
             *reinterpret_cast<float2*>(save + (size_t)(19 + k) * N + st.n) =
                 make_float2(b * p0[k], b * p1[k]);
     }
     if (!(kp.flags & LBM_FLAG_NO_COLLIDE)) {
-        collide_bgk<s16>(kp, f0, p0);
-        collide_bgk<s16>(kp, f1, p1);
+        collide_bgk<s16, SL>(kp, f0, p0);
+        collide_bgk<s16, SL>(kp, f1, p1);
     }
     scatter2<19, ODD>(kp, f, st, f0, f1);
-    scatter2<7, ODD>(kp, phi, st, p0, p1);
+    scatter2<NS, ODD, S, D0>(kp, phi, st, p0, p1);
 }
 
-template <typename S>
+template <typename S, int SL>
 static cudaError_t launch_bgk_typed(const KParams& kp, bool odd, S* f, S* phi, float* save,
                                    cudaStream_t st) {
     if constexpr (LBM_BGK_PAIR) if (kp.nx % 2 == 0) {
         dim3 block(128), grid((kp.nx / 2 + 127) / 128, kp.ny, kp.nz);
         if (save) {
-            if (odd) bgk_step2_kernel<true, true, S><<<grid, block, 0, st>>>(kp, f, phi, save);
-            else bgk_step2_kernel<false, true, S><<<grid, block, 0, st>>>(kp, f, phi, save);
+            if (odd) bgk_step2_kernel<true, true, S, SL><<<grid, block, 0, st>>>(kp, f, phi, save);
+            else bgk_step2_kernel<false, true, S, SL><<<grid, block, 0, st>>>(kp, f, phi, save);
         } else {
-            if (odd) bgk_step2_kernel<true, false, S><<<grid, block, 0, st>>>(kp, f, phi, nullptr);
-            else bgk_step2_kernel<false, false, S><<<grid, block, 0, st>>>(kp, f, phi, nullptr);
+            if (odd) bgk_step2_kernel<true, false, S, SL><<<grid, block, 0, st>>>(kp, f, phi, nullptr);
+            else bgk_step2_kernel<false, false, S, SL><<<grid, block, 0, st>>>(kp, f, phi, nullptr);
         }
         return cudaGetLastError();
     }
     dim3 block(128), grid((kp.nx + 127) / 128, kp.ny, kp.nz);
     if (save) {
-        if (odd) bgk_step_kernel<true, true, S><<<grid, block, 0, st>>>(kp, f, phi, save);
-        else bgk_step_kernel<false, true, S><<<grid, block, 0, st>>>(kp, f, phi, save);
+        if (odd) bgk_step_kernel<true, true, S, SL><<<grid, block, 0, st>>>(kp, f, phi, save);
+        else bgk_step_kernel<false, true, S, SL><<<grid, block, 0, st>>>(kp, f, phi, save);
     } else {
-        if (odd) bgk_step_kernel<true, false, S><<<grid, block, 0, st>>>(kp, f, phi, nullptr);
-        else bgk_step_kernel<false, false, S><<<grid, block, 0, st>>>(kp, f, phi, nullptr);
+        if (odd) bgk_step_kernel<true, false, S, SL><<<grid, block, 0, st>>>(kp, f, phi, nullptr);
+        else bgk_step_kernel<false, false, S, SL><<<grid, block, 0, st>>>(kp, f, phi, nullptr);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_bgk_step(const KParams& kp, int storage, bool odd, void* f, void* phi,
-                            float* save, cudaStream_t st) {
+template <int SL>
+static cudaError_t launch_bgk_sl(const KParams& kp, int storage, bool odd, void* f, void* phi,
+                                 float* save, cudaStream_t st) {
     switch (storage) {
-        case LBM_FP32: return launch_bgk_typed(kp, odd, (float*)f, (float*)phi, save, st);
-        case LBM_FP16S: return launch_bgk_typed(kp, odd, (__half*)f, (__half*)phi, save, st);
+        case LBM_FP32: return launch_bgk_typed<float, SL>(kp, odd, (float*)f, (float*)phi, save, st);
+        case LBM_FP16S: return launch_bgk_typed<__half, SL>(kp, odd, (__half*)f, (__half*)phi, save, st);
         case LBM_BF16S:
-            return launch_bgk_typed(kp, odd, (__nv_bfloat16*)f, (__nv_bfloat16*)phi, save, st);
+            return launch_bgk_typed<__nv_bfloat16, SL>(kp, odd, (__nv_bfloat16*)f,
+                                                       (__nv_bfloat16*)phi, save, st);
     }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_bgk_step(const KParams& kp, int storage, int scalar, bool odd, void* f,
+                            void* phi, float* save, cudaStream_t st) {
+    if (scalar == LBM_SCALAR_Q7) return launch_bgk_sl<7>(kp, storage, odd, f, phi, save, st);
+    if (scalar == LBM_SCALAR_Q6) return launch_bgk_sl<6>(kp, storage, odd, f, phi, save, st);
     return cudaErrorInvalidValue;
 }
 

@@ -30,13 +30,19 @@ namespace lbmgpu {
 // SCALED: f and p hold the 16-bit storage units scale_f (f - w) and
 // scale_phi (Phi - w); the scales are applied to the few moments and output
 // terms instead of to every population.
-template <bool SCALED = false>
-__device__ __forceinline__ void collide_bgk(const KParams& kp, float (&f)[19], float (&p)[7]) {
+//
+// SL: scalar lattice, D3Q7 (c_s^2 = 1/4) or D3Q6 (Eq. 29-31 as printed,
+// c_s^2 = 1/3, w = 1/6, no rest population).
+template <bool SCALED = false, int SL = 7>
+__device__ __forceinline__ void collide_bgk(const KParams& kp, float (&f)[19],
+                                            float (&p)[ScalarLat<SL>::NS]) {
+    static_assert(SL == 7 || SL == 6, "BGK runs with the D3Q7 or D3Q6 scalar");
+    constexpr int NS = ScalarLat<SL>::NS;
     const float isf = SCALED ? kp.isf : 1.0f, isp = SCALED ? kp.isp : 1.0f;
     const float sf = SCALED ? kp.sf : 1.0f, sp = SCALED ? kp.sp : 1.0f;
     float chs = 0.0f;  // scale_phi (chi - 1)
 #pragma unroll
-    for (int k = 0; k < 7; ++k) chs += p[k];
+    for (int k = 0; k < NS; ++k) chs += p[k];
     const float chit = chs * isp;  // chi - 1
     const float chi = 1.0f + chit;
     const float Fx = kp.gx * chi, Fy = kp.gy * chi, Fz = kp.gz * chi;
@@ -99,23 +105,39 @@ __device__ __forceinline__ void collide_bgk(const KParams& kp, float (&f)[19], f
         f[i + 1] = keep * f[i + 1] + even - odd;
     }
 
-    // scalar: Phi_eq - w = w (chi - 1 + 4 chi c.u).  Only the non-equilibrium
-    // parts are relaxed, and the rest population's part closes their sum to
-    // zero, so the update conserves sum Phi exactly up to the rounding of the
-    // stored results (relaxing towards the rounded chi would inject
-    // omega times the rounding error of the 7-term sum at every node)
     const float omp = 1.0f / (kp.taup0 + kp.kT * dtau);
-    const float pe = w7(1) * chs, pa = sp * w7(1) * 4.0f * chi;
-    float nq[7];
-    nq[1] = p[1] - (pe + pa * ux);
-    nq[2] = p[2] - (pe - pa * ux);
-    nq[3] = p[3] - (pe + pa * uy);
-    nq[4] = p[4] - (pe - pa * uy);
-    nq[5] = p[5] - (pe + pa * uz);
-    nq[6] = p[6] - (pe - pa * uz);
-    nq[0] = -(((nq[1] + nq[2]) + (nq[3] + nq[4])) + (nq[5] + nq[6]));
+    if constexpr (SL == 7) {
+        // scalar: Phi_eq - w = w (chi - 1 + 4 chi c.u).  Only the non-equilibrium
+        // parts are relaxed, and the rest population's part closes their sum to
+        // zero, so the update conserves sum Phi exactly up to the rounding of the
+        // stored results (relaxing towards the rounded chi would inject
+        // omega times the rounding error of the 7-term sum at every node)
+        const float pe = w7(1) * chs, pa = sp * w7(1) * 4.0f * chi;
+        float nq[7];
+        nq[1] = p[1] - (pe + pa * ux);
+        nq[2] = p[2] - (pe - pa * ux);
+        nq[3] = p[3] - (pe + pa * uy);
+        nq[4] = p[4] - (pe - pa * uy);
+        nq[5] = p[5] - (pe + pa * uz);
+        nq[6] = p[6] - (pe - pa * uz);
+        nq[0] = -(((nq[1] + nq[2]) + (nq[3] + nq[4])) + (nq[5] + nq[6]));
 #pragma unroll
-    for (int k = 0; k < 7; ++k) p[k] -= omp * nq[k];
+        for (int k = 0; k < 7; ++k) p[k] -= omp * nq[k];
+    } else {
+        // D3Q6: Phi_eq - w = (chi - 1 + 3 chi c.u) / 6; with no rest population
+        // the non-equilibrium parts are centred on their mean instead
+        const float pe = chs * (1.0f / 6.0f), pa = sp * 0.5f * chi;
+        float nq[6];
+        nq[0] = p[0] - (pe + pa * ux);
+        nq[1] = p[1] - (pe - pa * ux);
+        nq[2] = p[2] - (pe + pa * uy);
+        nq[3] = p[3] - (pe - pa * uy);
+        nq[4] = p[4] - (pe + pa * uz);
+        nq[5] = p[5] - (pe - pa * uz);
+        const float r = (((nq[0] + nq[1]) + (nq[2] + nq[3])) + (nq[4] + nq[5])) * (1.0f / 6.0f);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) p[k] -= omp * (nq[k] - r);
+    }
 }
 
 }  // namespace lbmgpu

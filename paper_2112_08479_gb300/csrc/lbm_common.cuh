@@ -51,6 +51,26 @@ __host__ __device__ constexpr float wq(int i) { return Q == 19 ? w19(i) : w27(i)
 // D3Q7: first 7 entries of the same order.
 __host__ __device__ constexpr float w7(int k) { return k == 0 ? 0.25f : 0.125f; }
 
+// Scalar lattices (the value of lbm_params.scalar in brackets):
+//   D3Q7  [0] BGK, c_s^2 = 1/4 (directions 0..6);
+//   D3Q6  [1] BGK, c_s^2 = 1/3, w = 1/6, no rest population (directions 1..6,
+//             the order of Eq. 31);
+//   D3Q27 [2] factorized central moments (directions 0..26).
+// Population k of a lattice is direction k + D0 of the D3Q27 order.
+template <int SL> struct ScalarLat;
+template <> struct ScalarLat<7> {
+    static constexpr int NS = 7, D0 = 0;
+    static __host__ __device__ constexpr float w(int k) { return w7(k); }
+};
+template <> struct ScalarLat<6> {
+    static constexpr int NS = 6, D0 = 1;
+    static __host__ __device__ constexpr float w(int) { return 1.0f / 6.0f; }
+};
+template <> struct ScalarLat<27> {
+    static constexpr int NS = 27, D0 = 0;
+    static __host__ __device__ constexpr float w(int k) { return w27(k); }
+};
+
 // ---------------------------------------------------------------------------
 // Kernel parameters, derived once on the host from lbm_params.
 struct KParams {
@@ -62,6 +82,7 @@ struct KParams {
     float taup0;         // 1/2 + 4 D                           (Eq. 30 on D3Q7)
     float kT;            // 4 / (3 Sc_T): tau_Phi = taup0 + kT (tau - tau0) (Eq. 35)
     float om1, om2;      // cumulant shear and bulk rates       (Eq. 58)
+    float omD;           // D3Q27 scalar: first-order rate from D (Eq. 51)
     float gx, gy, gz;    // g' e^g                               (Eq. 11)
     float sf, isf;       // storage scale of f - w and its inverse
     float sp, isp;       // storage scale of Phi and its inverse
@@ -179,35 +200,39 @@ __device__ __forceinline__ unsigned nbr(const Stencil& s, int dx, int dy, int dz
 // opp(i) of node n.  Each location is read and then written by exactly one
 // thread in each step, so the update is race-free in place.
 
-template <int Q, bool ODD, typename S>
+// Population k is direction dk = k + D0 and lives in row k; its opposite
+// direction's row is opp(dk) - D0.
+template <int Q, bool ODD, typename S, int D0 = 0>
 __device__ __forceinline__ void gather(const KParams& kp, const S* __restrict__ a,
                                        const Stencil& st, float (&v)[Q]) {
     const unsigned N = kp.N;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        unsigned off = (unsigned)i * N + st.n;
-        if (ODD && i != 0) {
+    for (int k = 0; k < Q; ++k) {
+        const int d = k + D0;
+        unsigned off = (unsigned)k * N + st.n;
+        if (ODD && d != 0) {
             bool in;
-            const unsigned s = nbr(st, -cx27(i), -cy27(i), -cz27(i), in);
-            off = in ? (unsigned)opp(i) * N + s : off;
+            const unsigned s = nbr(st, -cx27(d), -cy27(d), -cz27(d), in);
+            off = in ? (unsigned)(opp(d) - D0) * N + s : off;
         }
-        v[i] = Store<S>::ld(a + off);
+        v[k] = Store<S>::ld(a + off);
     }
 }
 
-template <int Q, bool ODD, typename S>
+template <int Q, bool ODD, typename S, int D0 = 0>
 __device__ __forceinline__ void scatter(const KParams& kp, S* __restrict__ a, const Stencil& st,
                                         const float (&v)[Q]) {
     const unsigned N = kp.N;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        unsigned off = (unsigned)opp(i) * N + st.n;
-        if (ODD && i != 0) {
+    for (int k = 0; k < Q; ++k) {
+        const int d = k + D0;
+        unsigned off = (unsigned)(opp(d) - D0) * N + st.n;
+        if (ODD && d != 0) {
             bool in;
-            const unsigned d = nbr(st, cx27(i), cy27(i), cz27(i), in);
-            off = in ? (unsigned)i * N + d : off;
+            const unsigned t = nbr(st, cx27(d), cy27(d), cz27(d), in);
+            off = in ? (unsigned)k * N + t : off;
         }
-        Store<S>::st(a + off, v[i]);
+        Store<S>::st(a + off, v[k]);
     }
 }
 

@@ -21,7 +21,6 @@
 // state (rho = 1, u = 0, Sigma = I/3) so FP32 keeps its digits.
 #include <type_traits>
 
-#include "lbm_aa2.cuh"
 #include "lbm_internal.h"
 
 namespace lbmgpu {
@@ -52,10 +51,15 @@ __host__ __device__ constexpr int dir27(int x, int y, int z) {
     return t[(x + 1) * 9 + (y + 1) * 3 + (z + 1)];
 }
 
-__device__ __forceinline__ void collide_cumulant(const KParams& kp, float (&f)[27], float (&p)[7]) {
+// SL: scalar lattice, D3Q7 BGK or D3Q27 factorized central moments.
+template <int SL = 7>
+__device__ __forceinline__ void collide_cumulant(const KParams& kp, float (&f)[27],
+                                                 float (&p)[ScalarLat<SL>::NS]) {
+    static_assert(SL == 7 || SL == 27, "the cumulant model runs with the D3Q7 or D3Q27 scalar");
+    constexpr int NS = ScalarLat<SL>::NS;
     float chit = 0.0f;  // chi - 1 (Phi is held as Phi - w)
 #pragma unroll
-    for (int k = 0; k < 7; ++k) chit += p[k];
+    for (int k = 0; k < NS; ++k) chit += p[k];
     const float chi = 1.0f + chit;
     const float Fx = kp.gx * chi, Fy = kp.gy * chi, Fz = kp.gz * chi;
 
@@ -144,26 +148,75 @@ __device__ __forceinline__ void collide_cumulant(const KParams& kp, float (&f)[2
             f[ip] = drho * w27(ip) + rho * pp;
         }
 
-    // scalar (Eq. 28-30) with the half-force velocity and the molecular D;
-    // non-equilibrium form whose parts sum to zero, so sum Phi is conserved
-    // up to the rounding of the stored results (see collide_bgk)
     const float hx = (jx + 0.5f * Fx) * irho, hy = (jy + 0.5f * Fy) * irho,
                 hz = (jz + 0.5f * Fz) * irho;
-    const float omp = 1.0f / kp.taup0;
-    const float pe = w7(1) * chit, pa = w7(1) * 4.0f * chi;
-    float nq[7];
-    nq[1] = p[1] - (pe + pa * hx);
-    nq[2] = p[2] - (pe - pa * hx);
-    nq[3] = p[3] - (pe + pa * hy);
-    nq[4] = p[4] - (pe - pa * hy);
-    nq[5] = p[5] - (pe + pa * hz);
-    nq[6] = p[6] - (pe - pa * hz);
-    nq[0] = -(((nq[1] + nq[2]) + (nq[3] + nq[4])) + (nq[5] + nq[6]));
+    if constexpr (SL == 7) {
+        // scalar (Eq. 28-30) with the half-force velocity and the molecular D;
+        // non-equilibrium form whose parts sum to zero, so sum Phi is conserved
+        // up to the rounding of the stored results (see collide_bgk)
+        const float omp = 1.0f / kp.taup0;
+        const float pe = w7(1) * chit, pa = w7(1) * 4.0f * chi;
+        float nq[7];
+        nq[1] = p[1] - (pe + pa * hx);
+        nq[2] = p[2] - (pe - pa * hx);
+        nq[3] = p[3] - (pe + pa * hy);
+        nq[4] = p[4] - (pe - pa * hy);
+        nq[5] = p[5] - (pe + pa * hz);
+        nq[6] = p[6] - (pe - pa * hz);
+        nq[0] = -(((nq[1] + nq[2]) + (nq[3] + nq[4])) + (nq[5] + nq[6]));
 #pragma unroll
-    for (int k = 0; k < 7; ++k) p[k] -= omp * nq[k];
+        for (int k = 0; k < 7; ++k) p[k] -= omp * nq[k];
+    } else {
+        // D3Q27 factorized central moments (Eq. 37-51) with every rate of order
+        // >= 2 equal to 1: the moments in the frame of u relax to their lattice
+        // equilibria chi (1, 0, 1/3)^(x) per axis, except the first-order ones,
+        // v = (1 - omega_D) (sum c Phi - chi u) with omega_D from Eq. 51.  The
+        // post-collision populations are therefore
+        //   chi Ex Ey Ez + vx Gx Ey Ez + vy Ex Gy Ez + vz Ex Ey Gz,
+        // E(0) = 2/3 - u^2, E(+-1) = (1/3 + u^2 +- u)/2 (moments (1, 0, 1/3)),
+        // G(0) = -2u, G(+-1) = (2u +- 1)/2 (moments (0, 1, 0)), both inverted in
+        // the frame of u.  Held as deviations: Phi* - w = (chi - 1) w +
+        // chi (Ex Ey Ez - w) + v-terms, with Ex Ey Ez - w expanded in the small
+        // parts dE = E - w1.
+        float jpx = 0.0f, jpy = 0.0f, jpz = 0.0f;   // sum c (Phi - w) = sum c Phi
+#pragma unroll
+        for (int i = 1; i < 27; i += 2) {
+            const float dm = p[i] - p[i + 1];
+            if (cx27(i)) jpx += cx27(i) * dm;
+            if (cy27(i)) jpy += cy27(i) * dm;
+            if (cz27(i)) jpz += cz27(i) * dm;
+        }
+        const float r1 = 1.0f - kp.omD;
+        const float vx = r1 * (jpx - chi * hx), vy = r1 * (jpy - chi * hy), vz = r1 * (jpz - chi * hz);
+        const float u[3] = {hx, hy, hz};
+        const float v[3] = {vx, vy, vz};
+        float W[3][3], dE[3][3], G[3][3];   // [axis][c + 1]
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float uu = u[a] * u[a];
+            W[a][0] = 1.0f / 6.0f; W[a][1] = 2.0f / 3.0f; W[a][2] = 1.0f / 6.0f;
+            dE[a][1] = -uu;
+            dE[a][0] = 0.5f * (uu - u[a]);
+            dE[a][2] = 0.5f * (uu + u[a]);
+            G[a][1] = -2.0f * u[a];
+            G[a][0] = u[a] - 0.5f;
+            G[a][2] = u[a] + 0.5f;
+        }
+#pragma unroll
+        for (int i = 0; i < 27; ++i) {
+            const int cx = cx27(i) + 1, cy = cy27(i) + 1, cz = cz27(i) + 1;
+            const float Ex = W[0][cx] + dE[0][cx], Ey = W[1][cy] + dE[1][cy], Ez = W[2][cz] + dE[2][cz];
+            // Ex Ey Ez - Wx Wy Wz without cancellation
+            const float dprod = dE[0][cx] * Ey * Ez + W[0][cx] * dE[1][cy] * Ez +
+                                W[0][cx] * W[1][cy] * dE[2][cz];
+            const float vt = v[0] * G[0][cx] * Ey * Ez + v[1] * Ex * G[1][cy] * Ez +
+                             v[2] * Ex * Ey * G[2][cz];
+            p[i] = chit * w27(i) + chi * dprod + vt;
+        }
+    }
 }
 
-template <bool ODD, bool SAVE, typename S>
+template <bool ODD, bool SAVE, typename S, int SL>
 __global__ void __launch_bounds__(128, LBM_STEP_MINB) cumulant_step_kernel(KParams kp, S* __restrict__ f,
                                                             S* __restrict__ phi,
                                                             float* __restrict__ save) {
@@ -172,107 +225,67 @@ __global__ void __launch_bounds__(128, LBM_STEP_MINB) cumulant_step_kernel(KPara
     const Stencil st = make_stencil(kp, x, blockIdx.y, blockIdx.z);
     const unsigned n = st.n;
 
-    float fv[27], pv[7];
+    constexpr int NS = ScalarLat<SL>::NS;
+    float fv[27], pv[NS];
     gather<27, ODD>(kp, f, st, fv);
-    gather<7, ODD>(kp, phi, st, pv);
+    gather<NS, ODD>(kp, phi, st, pv);
     if (!std::is_same<S, float>::value) {
 #pragma unroll
         for (int i = 0; i < 27; ++i) fv[i] *= kp.isf;
 #pragma unroll
-        for (int k = 0; k < 7; ++k) pv[k] *= kp.isp;
+        for (int k = 0; k < NS; ++k) pv[k] *= kp.isp;
     }
     if (SAVE) {
         const size_t N = kp.N;
 #pragma unroll
         for (int i = 0; i < 27; ++i) save[(size_t)i * N + n] = fv[i];
 #pragma unroll
-        for (int k = 0; k < 7; ++k) save[(size_t)(27 + k) * N + n] = pv[k];
+        for (int k = 0; k < NS; ++k) save[(size_t)(27 + k) * N + n] = pv[k];
     }
-    if (!(kp.flags & LBM_FLAG_NO_COLLIDE)) collide_cumulant(kp, fv, pv);
+    if (!(kp.flags & LBM_FLAG_NO_COLLIDE)) collide_cumulant<SL>(kp, fv, pv);
     if (!std::is_same<S, float>::value) {
 #pragma unroll
         for (int i = 0; i < 27; ++i) fv[i] *= kp.sf;
 #pragma unroll
-        for (int k = 0; k < 7; ++k) pv[k] *= kp.sp;
+        for (int k = 0; k < NS; ++k) pv[k] *= kp.sp;
     }
     scatter<27, ODD>(kp, f, st, fv);
-    scatter<7, ODD>(kp, phi, st, pv);
+    scatter<NS, ODD>(kp, phi, st, pv);
 }
 
 
-// Two x-adjacent nodes per thread (nx even): paired population accesses, see
-// lbm_aa2.cuh.  Same arithmetic per node as cumulant_step_kernel.
-template <bool ODD, bool SAVE, typename S>
-__global__ void __launch_bounds__(128, LBM_STEP2_MINB) cumulant_step2_kernel(KParams kp, S* __restrict__ f,
-                                                                    S* __restrict__ phi,
-                                                                    float* __restrict__ save) {
-    const int x = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
-    const Stencil2 st = make_stencil2(kp, x, blockIdx.y, blockIdx.z);
-    float f0[27], f1[27], p0[7], p1[7];
-    gather2<27, ODD>(kp, f, st, f0, f1);
-    gather2<7, ODD>(kp, phi, st, p0, p1);
-    if (!std::is_same<S, float>::value) {
-#pragma unroll
-        for (int i = 0; i < 27; ++i) { f0[i] *= kp.isf; f1[i] *= kp.isf; }
-#pragma unroll
-        for (int k = 0; k < 7; ++k) { p0[k] *= kp.isp; p1[k] *= kp.isp; }
-    }
-    if (SAVE && st.active) {
-        const unsigned N = kp.N;
-#pragma unroll
-        for (int i = 0; i < 27; ++i)
-            *reinterpret_cast<float2*>(save + (size_t)i * N + st.n) = make_float2(f0[i], f1[i]);
-#pragma unroll
-        for (int k = 0; k < 7; ++k)
-            *reinterpret_cast<float2*>(save + (size_t)(27 + k) * N + st.n) = make_float2(p0[k], p1[k]);
-    }
-    if (!(kp.flags & LBM_FLAG_NO_COLLIDE)) {
-        collide_cumulant(kp, f0, p0);
-        collide_cumulant(kp, f1, p1);
-    }
-    if (!std::is_same<S, float>::value) {
-#pragma unroll
-        for (int i = 0; i < 27; ++i) { f0[i] *= kp.sf; f1[i] *= kp.sf; }
-#pragma unroll
-        for (int k = 0; k < 7; ++k) { p0[k] *= kp.sp; p1[k] *= kp.sp; }
-    }
-    scatter2<27, ODD>(kp, f, st, f0, f1);
-    scatter2<7, ODD>(kp, phi, st, p0, p1);
-}
-
-template <typename S>
+template <typename S, int SL>
 static cudaError_t launch_cumulant_typed(const KParams& kp, bool odd, S* f, S* phi, float* save,
-                                   cudaStream_t st) {
-    if constexpr (LBM_CUMULANT_PAIR) if (kp.nx % 2 == 0) {
-        dim3 block(128), grid((kp.nx / 2 + 127) / 128, kp.ny, kp.nz);
-        if (save) {
-            if (odd) cumulant_step2_kernel<true, true, S><<<grid, block, 0, st>>>(kp, f, phi, save);
-            else cumulant_step2_kernel<false, true, S><<<grid, block, 0, st>>>(kp, f, phi, save);
-        } else {
-            if (odd) cumulant_step2_kernel<true, false, S><<<grid, block, 0, st>>>(kp, f, phi, nullptr);
-            else cumulant_step2_kernel<false, false, S><<<grid, block, 0, st>>>(kp, f, phi, nullptr);
-        }
-        return cudaGetLastError();
-    }
+                                        cudaStream_t st) {
     dim3 block(128), grid((kp.nx + 127) / 128, kp.ny, kp.nz);
     if (save) {
-        if (odd) cumulant_step_kernel<true, true, S><<<grid, block, 0, st>>>(kp, f, phi, save);
-        else cumulant_step_kernel<false, true, S><<<grid, block, 0, st>>>(kp, f, phi, save);
+        if (odd) cumulant_step_kernel<true, true, S, SL><<<grid, block, 0, st>>>(kp, f, phi, save);
+        else cumulant_step_kernel<false, true, S, SL><<<grid, block, 0, st>>>(kp, f, phi, save);
     } else {
-        if (odd) cumulant_step_kernel<true, false, S><<<grid, block, 0, st>>>(kp, f, phi, nullptr);
-        else cumulant_step_kernel<false, false, S><<<grid, block, 0, st>>>(kp, f, phi, nullptr);
+        if (odd) cumulant_step_kernel<true, false, S, SL><<<grid, block, 0, st>>>(kp, f, phi, nullptr);
+        else cumulant_step_kernel<false, false, S, SL><<<grid, block, 0, st>>>(kp, f, phi, nullptr);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_cumulant_step(const KParams& kp, int storage, bool odd, void* f, void* phi,
-                                 float* save, cudaStream_t st) {
+template <int SL>
+static cudaError_t launch_cumulant_sl(const KParams& kp, int storage, bool odd, void* f, void* phi,
+                                      float* save, cudaStream_t st) {
     switch (storage) {
-        case LBM_FP32: return launch_cumulant_typed(kp, odd, (float*)f, (float*)phi, save, st);
-        case LBM_FP16S: return launch_cumulant_typed(kp, odd, (__half*)f, (__half*)phi, save, st);
+        case LBM_FP32: return launch_cumulant_typed<float, SL>(kp, odd, (float*)f, (float*)phi, save, st);
+        case LBM_FP16S:
+            return launch_cumulant_typed<__half, SL>(kp, odd, (__half*)f, (__half*)phi, save, st);
         case LBM_BF16S:
-            return launch_cumulant_typed(kp, odd, (__nv_bfloat16*)f, (__nv_bfloat16*)phi, save, st);
+            return launch_cumulant_typed<__nv_bfloat16, SL>(kp, odd, (__nv_bfloat16*)f,
+                                                            (__nv_bfloat16*)phi, save, st);
     }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_cumulant_step(const KParams& kp, int storage, int scalar, bool odd, void* f,
+                                 void* phi, float* save, cudaStream_t st) {
+    if (scalar == LBM_SCALAR_Q7) return launch_cumulant_sl<7>(kp, storage, odd, f, phi, save, st);
+    if (scalar == LBM_SCALAR_Q27) return launch_cumulant_sl<27>(kp, storage, odd, f, phi, save, st);
     return cudaErrorInvalidValue;
 }
 

@@ -29,26 +29,32 @@ struct Views {
 };
 
 // Per-model step launchers (lbm_bgk.cu, lbm_cumulant.cu).
-cudaError_t launch_bgk_step(const KParams& kp, int storage, bool odd, void* f, void* phi,
-                            float* save, cudaStream_t st);
-cudaError_t launch_cumulant_step(const KParams& kp, int storage, bool odd, void* f, void* phi,
-                                 float* save, cudaStream_t st);
+cudaError_t launch_bgk_step(const KParams& kp, int storage, int scalar, bool odd, void* f,
+                            void* phi, float* save, cudaStream_t st);
+cudaError_t launch_cumulant_step(const KParams& kp, int storage, int scalar, bool odd, void* f,
+                                 void* phi, float* save, cudaStream_t st);
 
-// model: lbm_model; storage: lbm_storage; odd: parity of the AA step.
-cudaError_t launch_step(const KParams& kp, int model, int storage, bool odd, void* f, void* phi,
-                        float* save, cudaStream_t st);
-cudaError_t launch_init(const KParams& kp, int model, int storage, const Views& v, const float* chi0,
-                        int x0, double amp, uint64_t seed, cudaStream_t st);
-cudaError_t launch_macros(const KParams& kp, int model, int storage, bool odd, const Views& v,
-                          float* rho, float* u, float* chi, cudaStream_t st);
-cudaError_t launch_get_state(const KParams& kp, int model, int storage, bool odd, const Views& v,
-                             float* dst, cudaStream_t st);
-cudaError_t launch_set_state(const KParams& kp, int model, int storage, const Views& v,
-                             const float* src, cudaStream_t st);
-cudaError_t launch_diag(const KParams& kp, int model, int storage, bool odd, const Views& v,
-                        double threshold, int x0, double H, cudaStream_t st);
-cudaError_t launch_fw_accumulate(const KParams& kp, int model, int storage, bool odd,
-                                 const Views& v, double* acc, double weight, cudaStream_t st);
+// Model, scalar lattice and storage select the kernel (the pairs the ABI
+// accepts: BGK with D3Q7 or D3Q6, cumulant with D3Q7 or D3Q27).
+struct Kind {
+    int model, scalar, storage;
+};
+
+// odd: parity of the AA step.
+cudaError_t launch_step(const KParams& kp, Kind k, bool odd, void* f, void* phi, float* save,
+                        cudaStream_t st);
+cudaError_t launch_init(const KParams& kp, Kind k, const Views& v, const float* chi0, int x0,
+                        double amp, uint64_t seed, cudaStream_t st);
+cudaError_t launch_macros(const KParams& kp, Kind k, bool odd, const Views& v, float* rho,
+                          float* u, float* chi, cudaStream_t st);
+cudaError_t launch_get_state(const KParams& kp, Kind k, bool odd, const Views& v, float* dst,
+                             cudaStream_t st);
+cudaError_t launch_set_state(const KParams& kp, Kind k, const Views& v, const float* src,
+                             cudaStream_t st);
+cudaError_t launch_diag(const KParams& kp, Kind k, bool odd, const Views& v, double threshold,
+                        int x0, double H, cudaStream_t st);
+cudaError_t launch_fw_accumulate(const KParams& kp, Kind k, bool odd, const Views& v,
+                                 double* acc, double weight, cudaStream_t st);
 cudaError_t launch_adjoint_step(const KParams& kp, const float* state, const float* lam_next,
                                 float* lam, double* dcs, float wfw, float dAdCs, cudaStream_t st);
 cudaError_t launch_push_step(const KParams& kp, const float* src, float* dst, cudaStream_t st);

@@ -69,10 +69,10 @@ __global__ void na_reset_kernel(unsigned char* scratch, int nx) {
     if (i == 0) ((NaRecord*)(scratch + NA_REC))->flags = 0;
 }
 
-// One thread per column (x, z) of a canonical state ([Q + 7][N] floats,
+// One thread per column (x, z) of a canonical state ([Q + NS][N] floats,
 // f - w then Phi - w), looping over y: the same sums as the workspace-based
 // diagnostics.
-template <int Q>
+template <int Q, int NS>
 __global__ void __launch_bounds__(NA_BX) na_columns_kernel(KParams kp, const float* __restrict__ s,
                                                            unsigned char* scratch) {
     unsigned* keys = (unsigned*)(scratch + NA_KEYS);
@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(NA_BX) na_columns_kernel(KParams kp, const flo
             const size_t n = (size_t)x + (size_t)kp.nx * ((size_t)y + (size_t)kp.ny * z);
             float c = 0.0f, d = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
 #pragma unroll
-            for (int k = 0; k < 7; ++k) c += s[(size_t)(Q + k) * N + n];
+            for (int k = 0; k < NS; ++k) c += s[(size_t)(Q + k) * N + n];
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 const float v = s[(size_t)i * N + n];
@@ -250,8 +250,13 @@ lbm_status lbm_diag_static(const lbm_params* p, const float* state, int64_t step
     unsigned char* s8 = (unsigned char*)scratch;
     na_reset_kernel<<<(p->nx + 255) / 256, 256, 0, st>>>(s8, p->nx);
     dim3 grid(nbx, p->nz);
-    if (p->model == LBM_CUMULANT_Q27) na_columns_kernel<27><<<grid, NA_BX, 0, st>>>(kp, state, s8);
-    else na_columns_kernel<19><<<grid, NA_BX, 0, st>>>(kp, state, s8);
+    if (p->model == LBM_CUMULANT_Q27) {
+        if (p->scalar == LBM_SCALAR_Q27) na_columns_kernel<27, 27><<<grid, NA_BX, 0, st>>>(kp, state, s8);
+        else na_columns_kernel<27, 7><<<grid, NA_BX, 0, st>>>(kp, state, s8);
+    } else {
+        if (p->scalar == LBM_SCALAR_Q6) na_columns_kernel<19, 6><<<grid, NA_BX, 0, st>>>(kp, state, s8);
+        else na_columns_kernel<19, 7><<<grid, NA_BX, 0, st>>>(kp, state, s8);
+    }
     na_finalize_kernel<<<1, NA_FIN, 0, st>>>(p->nx, (double)kp.N, (unsigned)(nbx * p->nz), s8,
                                              p->front_threshold, p->x0, (double)p->H);
     if ((e = cudaGetLastError()) != cudaSuccess) return LBM_ERR_CUDA;

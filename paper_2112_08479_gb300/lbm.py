@@ -20,7 +20,10 @@ LBM_FP32, LBM_FP16S, LBM_BF16S = 0, 1, 2
 LBM_FLAG_NO_COLLIDE, LBM_FLAG_PERIODIC_X, LBM_FLAG_PERIODIC_Z = 1, 2, 4
 LBM_DEVFLAG_NONFINITE, LBM_DEVFLAG_RHO_NONPOS = 1, 2
 
+LBM_SCALAR_Q7, LBM_SCALAR_Q6, LBM_SCALAR_Q27 = 0, 1, 2
+
 MODELS = {"bgk": LBM_BGK_SMAG_Q19, "cumulant": LBM_CUMULANT_Q27}
+SCALARS = {"q7": LBM_SCALAR_Q7, "q6": LBM_SCALAR_Q6, "q27": LBM_SCALAR_Q27}
 STORAGES = {"fp32": LBM_FP32, "fp16s": LBM_FP16S, "bf16s": LBM_BF16S}
 
 
@@ -38,7 +41,7 @@ class lbm_params(C.Structure):
                 ("omega_bulk", C.c_double), ("x0", C.c_int32), ("H", C.c_int32),
                 ("noise_amp", C.c_double), ("seed", C.c_uint64),
                 ("front_threshold", C.c_double), ("scale_f", C.c_double),
-                ("scale_phi", C.c_double)]
+                ("scale_phi", C.c_double), ("scalar", C.c_int32), ("pad_", C.c_int32)]
 
 
 class lbm_diagnostics(C.Structure):
@@ -224,6 +227,7 @@ class Params:
     front_threshold: float = 0.02
     scale_f: float = 2.0 ** 14
     scale_phi: float = 2.0 ** 14
+    scalar: int = LBM_SCALAR_Q7
 
     def c(self) -> lbm_params:
         p = lbm_params()
@@ -240,6 +244,10 @@ class Params:
         return 27 if self.model == LBM_CUMULANT_Q27 else 19
 
     @property
+    def NS(self) -> int:
+        return {LBM_SCALAR_Q7: 7, LBM_SCALAR_Q6: 6, LBM_SCALAR_Q27: 27}[self.scalar]
+
+    @property
     def N(self) -> int:
         return self.nx * self.ny * self.nz
 
@@ -250,12 +258,13 @@ class Params:
 
 def lock_exchange(nx: int, ny: int, nz: int, *, H: int, x0: int, u_b: float, Re: float,
                   Sc: float = 1.0, model: str = "bgk", storage: str = "fp32",
-                  cs_smag: float = 0.17, **kw) -> Params:
+                  cs_smag: float = 0.17, scalar: str = "q7", **kw) -> Params:
     """Lattice-unit parameters of the lock-exchange box (Sec. 2.5): g' = u_b^2 / H
     (u_b = sqrt(g' H)), nu = u_b H / Re_b, D = nu / Sc (Eq. 12-14)."""
     nu = u_b * H / Re
     return Params(nx=nx, ny=ny, nz=nz, model=MODELS[model], storage=STORAGES[storage],
-                  nu=nu, D=nu / Sc, cs_smag=cs_smag, gprime=u_b * u_b / H, x0=x0, H=H, **kw)
+                  nu=nu, D=nu / Sc, cs_smag=cs_smag, gprime=u_b * u_b / H, x0=x0, H=H,
+                  scalar=SCALARS[scalar], **kw)
 
 
 # --- torch-backed context -----------------------------------------------------------
@@ -288,6 +297,10 @@ class Lattice:
     @property
     def Q(self) -> int:
         return self.params.Q
+
+    @property
+    def NS(self) -> int:
+        return self.params.NS
 
     @property
     def N(self) -> int:
@@ -323,12 +336,13 @@ class Lattice:
 
     def get_state(self, out=None):
         if out is None:
-            out = self._empty(self.Q + 7, self.N)
+            out = self._empty(self.Q + self.NS, self.N)
         lbm_get_state(self.ctx, out.data_ptr())
         return out
 
     def set_state(self, src, step: int = 0):
-        assert src.dtype == self.torch.float32 and src.is_contiguous() and src.numel() == (self.Q + 7) * self.N
+        assert (src.dtype == self.torch.float32 and src.is_contiguous()
+                and src.numel() == (self.Q + self.NS) * self.N)
         lbm_set_state(self.ctx, src.data_ptr(), step)
 
     def adjoint_step(self, state, lam_next, lam, dcs, w_fw: float):

@@ -21,8 +21,10 @@ class LBMObjective(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, chi0, cs, params: lbm.Params, nsteps: int, K: int = 100):
-        if params.model != lbm.LBM_BGK_SMAG_Q19 or params.storage != lbm.LBM_FP32:
-            raise ValueError("the adjoint exists for the BGK-Smagorinsky model with FP32 storage")
+        if (params.model != lbm.LBM_BGK_SMAG_Q19 or params.storage != lbm.LBM_FP32
+                or params.scalar != lbm.LBM_SCALAR_Q7):
+            raise ValueError("the adjoint exists for the BGK-Smagorinsky model with the D3Q7 "
+                             "scalar and FP32 storage")
         if nsteps < 1 or K < 1:
             raise ValueError("nsteps and K must be >= 1")
         p = replace(params, cs_smag=float(cs))
@@ -30,7 +32,7 @@ class LBMObjective(torch.autograd.Function):
         lat.set_scalar(chi0.detach().to(torch.float32).contiguous())
         acc = torch.zeros(1, dtype=torch.float64, device=chi0.device)
         nck = (nsteps + K - 1) // K
-        ckpts = torch.empty(nck, lat.Q + 7, lat.N, device=chi0.device)
+        ckpts = torch.empty(nck, lat.Q + lat.NS, lat.N, device=chi0.device)
         lat.objective_forward(nsteps, K, ckpts, acc)
         ctx.lat = lat
         ctx.ckpts = ckpts

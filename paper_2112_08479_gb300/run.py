@@ -81,6 +81,9 @@ def main(argv=None):
     ap.add_argument("--Sc", type=float, default=1.0)
     ap.add_argument("--model", default="bgk", choices=sorted(lbm.MODELS))
     ap.add_argument("--storage", default="fp32", choices=sorted(lbm.STORAGES))
+    ap.add_argument("--scalar", default="q7", choices=sorted(lbm.SCALARS),
+                    help="scalar lattice: q7 (both models), q6 (BGK, Eq. 29-31), "
+                         "q27 (cumulant, factorized central moments, Eq. 37-51)")
     ap.add_argument("--cs", type=float, default=0.17)
     ap.add_argument("--seed", type=int, default=2112)
     ap.add_argument("--steps", type=int, default=None)
@@ -90,7 +93,8 @@ def main(argv=None):
     ap.add_argument("--fr-window", type=float, nargs=2, default=(2.5, 10.0))
     a = ap.parse_args(argv)
     p = lbm.lock_exchange(a.nx, a.ny, a.nz, H=a.H, x0=a.x0, u_b=a.ub, Re=a.Re, Sc=a.Sc,
-                          model=a.model, storage=a.storage, cs_smag=a.cs, seed=a.seed)
+                          model=a.model, storage=a.storage, cs_smag=a.cs, seed=a.seed,
+                          scalar=a.scalar)
     steps = a.steps if a.steps is not None else int(round(a.t_end * a.H / a.ub))
     recs, wall = run(p, a.ub, steps, a.every, a.out)
     fr = froude([r["t"] for r in recs], [r["front"] for r in recs], *a.fr_window)

@@ -16,7 +16,8 @@ def oracle_params(p: lbm.Params, **kw) -> O.OracleParams:
                         omega_high=1.0,
                         periodic_x=bool(p.flags & lbm.LBM_FLAG_PERIODIC_X),
                         periodic_z=bool(p.flags & lbm.LBM_FLAG_PERIODIC_Z),
-                        no_collide=bool(p.flags & lbm.LBM_FLAG_NO_COLLIDE))
+                        no_collide=bool(p.flags & lbm.LBM_FLAG_NO_COLLIDE),
+                        scalar=p.scalar, omega_phi_high=1.0)
     for k, v in kw.items():
         setattr(op, k, v)
     return op
@@ -30,24 +31,29 @@ def w7() -> np.ndarray:
     return O.velocities_q7()[1]
 
 
+def wscalar(p: lbm.Params) -> np.ndarray:
+    """Weights of the scalar lattice of p (D3Q7, D3Q6 or D3Q27)."""
+    return O.velocities_scalar(p.scalar)[1]
+
+
 def canonical_to_oracle(state: np.ndarray, p: lbm.Params, shifted: bool = True):
     """[Q+7, N] float32 (f - w, Phi - w) -> oracle (f, phi) float64 arrays.
     shifted=False takes the rows as they are (streaming tests, adjoints)."""
     Q = p.Q
-    s = np.asarray(state, dtype=np.float64).reshape(Q + 7, *p.shape)
+    s = np.asarray(state, dtype=np.float64).reshape(Q + p.NS, *p.shape)
     f = np.moveaxis(s[:Q], 0, -1).copy()
     phi = np.moveaxis(s[Q:], 0, -1).copy()
     if shifted:
         f += weights(p.model)
-        phi += w7()
+        phi += wscalar(p)
     return f, phi
 
 
 def oracle_to_canonical(f: np.ndarray, phi: np.ndarray, p: lbm.Params, shifted: bool = True):
     """oracle (f, phi) -> [Q+7, N] float64 in the library layout."""
     ff = f - weights(p.model) if shifted else f
-    pp = phi - w7() if shifted else phi
-    return np.concatenate([np.moveaxis(ff, -1, 0), np.moveaxis(pp, -1, 0)]).reshape(p.Q + 7, -1)
+    pp = phi - wscalar(p) if shifted else phi
+    return np.concatenate([np.moveaxis(ff, -1, 0), np.moveaxis(pp, -1, 0)]).reshape(p.Q + p.NS, -1)
 
 
 def lock_state_oracle(p: lbm.Params):
@@ -66,7 +72,7 @@ def rel_inf(a, b) -> float:
 def window_oracle(p: lbm.Params, state0: np.ndarray, node, steps: int):
     """Oracle value of every population at `node` after `steps` steps of a
     full-size run, from a (2 steps + 1)-wide window of the initial canonical
-    state `state0` ([Q+7, nz, ny, nx] float32, numpy or torch).  Window edges inside the
+    state `state0` ([Q+NS, nz, ny, nx] float32, numpy or torch).  Window edges inside the
     domain are given walls (x, z) or a wrap (y); their wrong values travel one
     node per step and do not reach the centre within `steps` steps."""
     Q = p.Q
@@ -85,7 +91,7 @@ def window_oracle(p: lbm.Params, state0: np.ndarray, node, steps: int):
         sub = sub.cpu().numpy()
     sub = sub.astype(np.float64)
     f = np.moveaxis(sub[:Q], 0, -1) + weights(p.model)
-    phi = np.moveaxis(sub[Q:], 0, -1) + w7()
+    phi = np.moveaxis(sub[Q:], 0, -1) + wscalar(p)
     op = oracle_params(p)
     op.nx, op.ny, op.nz = len(xs), len(ys), len(zs)
     op.periodic_x = False
@@ -93,4 +99,4 @@ def window_oracle(p: lbm.Params, state0: np.ndarray, node, steps: int):
     f, phi = O.run(op, steps, f, phi)
     cx = int(np.where(xs == x)[0][0])
     cz = int(np.where(zs == z)[0][0])
-    return f[cz, cy, cx] - weights(p.model), phi[cz, cy, cx] - w7()
+    return f[cz, cy, cx] - weights(p.model), phi[cz, cy, cx] - wscalar(p)

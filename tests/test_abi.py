@@ -37,7 +37,7 @@ def test_header_symbols_exported(lib):
 
 def test_struct_layouts():
     # sizes computed from the C declarations with natural alignment
-    assert C.sizeof(lbm.lbm_params) == 6 * 4 + 5 * 8 + 3 * 8 + 8 + 2 * 4 + 8 + 8 + 3 * 8
+    assert C.sizeof(lbm.lbm_params) == 6 * 4 + 5 * 8 + 3 * 8 + 8 + 2 * 4 + 8 + 8 + 3 * 8 + 2 * 4
     assert C.sizeof(lbm.lbm_diagnostics) == 5 * 8 + 8 + 4 + 4
 
 
@@ -63,6 +63,19 @@ def test_validate_rejects(lib, field, value):
     p = _good(**{field: value})
     assert lbm.lbm_validate(p) == lbm.LBM_ERR_ARG
     assert lbm.lbm_workspace_bytes(p) == 0
+
+
+def test_scalar_lattice_pairs(lib):
+    """BGK runs with D3Q7 or D3Q6, the cumulant model with D3Q7 or D3Q27."""
+    assert lbm.lbm_validate(_good(scalar=lbm.LBM_SCALAR_Q6)) == lbm.LBM_OK
+    assert lbm.lbm_validate(_good(scalar=lbm.LBM_SCALAR_Q27)) == lbm.LBM_ERR_ARG
+    assert lbm.lbm_validate(_good(model=lbm.LBM_CUMULANT_Q27, scalar=lbm.LBM_SCALAR_Q27)) == lbm.LBM_OK
+    assert lbm.lbm_validate(_good(model=lbm.LBM_CUMULANT_Q27, scalar=lbm.LBM_SCALAR_Q6)) == lbm.LBM_ERR_ARG
+    assert lbm.lbm_validate(_good(scalar=5)) == lbm.LBM_ERR_ARG
+    N = 16 * 4 * 8
+    b7 = lbm.lbm_workspace_bytes(_good())
+    b6 = lbm.lbm_workspace_bytes(_good(scalar=lbm.LBM_SCALAR_Q6))
+    assert b7 - b6 == pytest.approx(N * 4, abs=512)
 
 
 def test_cumulant_bulk_rate_range(lib):

@@ -212,10 +212,10 @@ LBM_API lbm_status lbm_adjoint_step(lbm_ctx* ctx, const float* state_n, const fl
 
 /* Forward pass of the time-integrated bottom friction J = sum_n F_w(s_n):
  * advances nsteps >= 0 steps from the current state s_0, adding F_w of each
- * new state to *J_dev (one device double), and, when ckpt is not NULL,
- * copies the state before relative step n to ckpt + (n / K) (Q + NS) N for
- * every n % K == 0 (canonical layout, device; ceil(nsteps / K) states).
- * Asynchronous. */
+ * new state to *J_dev (one device double; NULL skips the sum, for objectives
+ * of the final state only), and, when ckpt is not NULL, copies the state
+ * before relative step n to ckpt + (n / K) (Q + NS) N for every n % K == 0
+ * (canonical layout, device; ceil(nsteps / K) states).  Asynchronous. */
 LBM_API lbm_status lbm_objective_forward(lbm_ctx* ctx, int32_t nsteps, int32_t K, float* ckpt,
                                          double* J_dev);
 
@@ -223,12 +223,30 @@ LBM_API lbm_status lbm_objective_forward(lbm_ctx* ctx, int32_t nsteps, int32_t K
  * from the checkpoint ckpt = s_{n0}, recomputes s_{n0+1} .. s_{n0+k-1} into
  * seg + j (Q + NS) N (j = 1 .. k-1; seg holds k states, slot 0 unused) with
  * an out-of-place step of the same arithmetic, then applies k adjoint steps
- * backwards: on entry lam holds lam_{n0+k}, on return lam_{n0} (w_fw = 1
- * for n >= 1, 0 for n = 0).  tmp: a second adjoint buffer, distinct from
+ * backwards: on entry lam holds lam_{n0+k}, on return lam_{n0}; the
+ * friction of every state s_n with n >= 1 enters with weight w_fw (1 for the
+ * time-integrated friction, 0 for an objective of the final state, e.g. the
+ * front of lbm_front_adjoint).  tmp: a second adjoint buffer, distinct from
  * lam.  *dJdCs_dev accumulates the C_s derivative.  Asynchronous.
  * LBM_ERR_STATE for the cumulant model or 16-bit storage. */
 LBM_API lbm_status lbm_adjoint_segment(lbm_ctx* ctx, const float* ckpt, int64_t n0, int32_t k,
-                                       float* seg, float* lam, float* tmp, double* dJdCs_dev);
+                                       float* seg, float* lam, float* tmp, double* dJdCs_dev,
+                                       double w_fw);
+
+/* Front position of a state and its derivative (Sec. 3.1 with reading R11:
+ * chibar(x, z) = mean over y of chi, m(x) = max over z of chibar, x_f = the
+ * largest x with m(x) >= front_threshold, moved to the linear threshold
+ * crossing between x_f and x_f + 1; value (x_f + 1/2 - x0) / H).  The
+ * interpolated front is a continuous, piecewise smooth function of the
+ * state, the smooth surrogate of the node-wise front used as an objective.
+ * state: canonical layout ((Q + NS) * N floats, device).  front_dev: one
+ * device double receiving the value, or NULL.  lam: NULL, or (Q + NS) * N
+ * floats (device) receiving d value / d state: zero except on the scalar
+ * rows of the 2 ny nodes (x_f, y, z0) and (x_f + 1, y, z1), z0 and z1 the
+ * first z attaining m; zero everywhere when no column reaches the threshold
+ * or x_f = nx - 1.  Any model, scalar lattice and storage.  Asynchronous. */
+LBM_API lbm_status lbm_front_adjoint(lbm_ctx* ctx, const float* state, float* lam,
+                                     double* front_dev);
 
 /* Gradient with respect to the initial scalar field of a quantity whose
  * adjoint at step 0 is lam0: grad_chi0[n] = sum_k w_k lam0_Phi_k[n]

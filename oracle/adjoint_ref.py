@@ -1,12 +1,16 @@
-"""FP64 reference gradient of the time-integrated bottom friction.
+"""FP64 reference gradients of two lock-exchange objectives.
 
 TEST INFRASTRUCTURE ONLY (see the package docstring).
 
-Objective (Sec. 3.2, Eq. 62-64): J = sum_{n=1..N} F_w(s_n), where s_n is the
-state after n steps of the BGK-Smagorinsky + D3Q7 scalar + Boussinesq step and
-F_w = sum_{x,y} nu (9 u_x(z=0) - u_x(z=1)) / 3.  Gradients with respect to the
-initial scalar field chi0 (s_0: f = w, Phi_k = w_k chi0) and the Smagorinsky
-constant C_s.
+Objectives, with s_n the state after n steps of the BGK-Smagorinsky + D3Q7
+scalar + Boussinesq step:
+- "friction" (Sec. 3.2, Eq. 62-64): J = sum_{n=1..N} F_w(s_n),
+  F_w = sum_{x,y} nu (9 u_x(z=0) - u_x(z=1)) / 3;
+- "front" (Sec. 3.1, reading R11): J = (x_f(s_N) + 1/2 - x0) / H, x_f the
+  threshold crossing of m(x) = max_z mean_y chi, linearly interpolated
+  between the last column at or above the threshold and the next one.
+Gradients with respect to the initial scalar field chi0 (s_0: f = w,
+Phi_k = w_k chi0) and the Smagorinsky constant C_s.
 
 The step is restated here with torch float64 tensor operations, vectorised
 over nodes, directly from the equations (Eq. 11, 17, 19-30, 32-35 with the
@@ -100,6 +104,24 @@ class BGKStep:
         ux = u[..., 0]
         return (self.p.nu * (9 * ux[0] - ux[1]) / 3).sum()
 
+    def front(self, f, phi, x0: int, H: float, thr: float = 0.02):
+        """Front position (x_f + 1/2 - x0) / H; differentiable where the
+        crossing column and the maximising z do not change (torch.max passes
+        the gradient to the maximising element)."""
+        chi = phi.sum(-1)                       # (nz, ny, nx)
+        m = chi.mean(1).max(0).values           # (nx,)
+        nx = m.shape[0]
+        above = torch.nonzero(m >= thr)
+        if above.numel() == 0:
+            xn = m.new_tensor(-1.0)
+        else:
+            xf = int(above.max())
+            if xf == nx - 1:
+                xn = m.new_tensor(float(xf))
+            else:
+                xn = xf + (m[xf] - thr) / (m[xf] - m[xf + 1])
+        return (xn + 0.5 - x0) / H
+
 
 def initial_state(step: BGKStep, chi0):
     p = step.p
@@ -122,8 +144,10 @@ def objective(p: O.OracleParams, chi0, cs: float, nsteps: int) -> float:
     return J
 
 
-def gradient(p: O.OracleParams, chi0, cs: float, nsteps: int):
-    """Returns (J, dJ/dchi0 with the shape of chi0, dJ/dC_s) in FP64."""
+def gradient(p: O.OracleParams, chi0, cs: float, nsteps: int, objective: str = "friction",
+             x0: int = 0, H: float = 1.0, thr: float = 0.02):
+    """Returns (J, dJ/dchi0 with the shape of chi0, dJ/dC_s) in FP64 for the
+    objective "friction" or "front" (the latter with x0, H, thr)."""
     st = BGKStep(p)
     f, phi = initial_state(st, chi0)
     cs_t = torch.tensor(cs, dtype=DT)
@@ -133,17 +157,28 @@ def gradient(p: O.OracleParams, chi0, cs: float, nsteps: int):
         for _ in range(nsteps):
             f, phi = st(f, phi, cs_t)
             traj.append((f, phi))
-            J += float(st.friction(f, phi))
-    # lam_N = dF_w(s_N)/ds_N
+            if objective == "friction":
+                J += float(st.friction(f, phi))
+    # lam_N = dJ/ds_N of the final state's term
     fN, pN = (t.clone().requires_grad_(True) for t in traj[-1])
-    lf, lp = torch.autograd.grad(st.friction(fN, pN), (fN, pN))
+    if objective == "friction":
+        final = st.friction(fN, pN)
+    else:
+        final = st.front(fN, pN, x0, H, thr)
+        J = float(final.detach())
+    if final.requires_grad:
+        lf, lp = torch.autograd.grad(final, (fN, pN), allow_unused=True)
+        lf = torch.zeros_like(fN) if lf is None else lf
+        lp = torch.zeros_like(pN) if lp is None else lp
+    else:                                       # a front that does not move
+        lf, lp = torch.zeros_like(fN), torch.zeros_like(pN)
     gcs = 0.0
     for n in range(nsteps - 1, -1, -1):
         fn, pn = (t.clone().requires_grad_(True) for t in traj[n])
         c = cs_t.clone().requires_grad_(True)
         f1, p1 = st(fn, pn, c)
         inner = (f1 * lf).sum() + (p1 * lp).sum()
-        if n >= 1:
+        if n >= 1 and objective == "friction":
             inner = inner + st.friction(fn, pn)
         lf, lp, gc = torch.autograd.grad(inner, (fn, pn, c))
         gcs += float(gc)

@@ -30,7 +30,7 @@ constexpr size_t ALIGN = 256;
 inline size_t up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
 
 struct Layout {
-    size_t f, phi, stage, chibar, colmax, part, fwpart, ddiag, total;
+    size_t f, phi, stage, chibar, colmax, part, fwpart, ddiag, fgrad, total;
     unsigned nblocks;
 };
 
@@ -92,6 +92,7 @@ Layout layout(const lbm_params* p) {
     L.part = o;   o = up(o + (size_t)L.nblocks * 2 * sizeof(double));
     L.fwpart = o; o = up(o + (size_t)L.nblocks * 2 * sizeof(float));
     L.ddiag = o;  o = up(o + sizeof(DevDiag) + 2 * sizeof(int));
+    L.fgrad = o;  o = up(o + sizeof(FrontGrad));
     L.total = o;
     return L;
 }
@@ -198,6 +199,7 @@ lbm_status lbm_init(const lbm_params* p, void* workspace, size_t bytes, void* cu
     c->v.fwpart = (float*)(w + L.fwpart);
     c->v.ddiag = (DevDiag*)(w + L.ddiag);
     c->v.devflags = (int*)(w + L.ddiag + sizeof(DevDiag));
+    c->v.fgrad = (FrontGrad*)(w + L.fgrad);
     c->v.diag_blocks = L.nblocks;
     cudaError_t e = launch_init(c->kp, kind(p), c->v, nullptr, p->x0, p->noise_amp,
                                 p->seed, c->stream);
@@ -335,7 +337,6 @@ lbm_status lbm_objective_forward(lbm_ctx* c, int32_t nsteps, int32_t K, float* c
                                  double* J_dev) {
     if (!c) return arg_fail(nullptr, "ctx is NULL");
     if (nsteps < 0 || K < 1) return arg_fail(c, "nsteps must be >= 0 and K >= 1");
-    if (!J_dev) return arg_fail(c, "J_dev is NULL");
     const size_t S = (size_t)(q_of(&c->p) + ns_of(&c->p)) * c->kp.N;
     for (int32_t n = 0; n < nsteps; ++n) {
         cudaError_t e = cudaSuccess;
@@ -348,15 +349,16 @@ lbm_status lbm_objective_forward(lbm_ctx* c, int32_t nsteps, int32_t K, float* c
         if (e != cudaSuccess) return cuda_fail(c, e, "objective forward launch");
         c->odd ^= 1;
         ++c->step;
-        e = launch_fw_accumulate(c->kp, kind(&c->p), c->odd != 0, c->v, J_dev, 1.0,
-                                 c->stream);
+        if (J_dev)
+            e = launch_fw_accumulate(c->kp, kind(&c->p), c->odd != 0, c->v, J_dev, 1.0,
+                                     c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "objective forward launch");
     }
     return LBM_OK;
 }
 
 lbm_status lbm_adjoint_segment(lbm_ctx* c, const float* ckpt, int64_t n0, int32_t k, float* seg,
-                               float* lam, float* tmp, double* dJdCs_dev) {
+                               float* lam, float* tmp, double* dJdCs_dev, double w_fw) {
     if (!c) return arg_fail(nullptr, "ctx is NULL");
     if (c->p.model != LBM_BGK_SMAG_Q19 || c->p.storage != LBM_FP32 ||
         c->p.scalar != LBM_SCALAR_Q7) {
@@ -367,6 +369,7 @@ lbm_status lbm_adjoint_segment(lbm_ctx* c, const float* ckpt, int64_t n0, int32_
     if (k < 1 || n0 < 0) return arg_fail(c, "k must be >= 1 and n0 >= 0");
     if (!ckpt || !lam || !tmp || (k > 1 && !seg)) return arg_fail(c, "NULL buffer");
     if (lam == tmp) return arg_fail(c, "lam and tmp must differ");
+    if (!isfinite(w_fw)) return arg_fail(c, "w_fw must be finite");
     const size_t S = (size_t)(q_of(&c->p) + ns_of(&c->p)) * c->kp.N;
     const float dAdCs = (float)(36.0 * sqrt(2.0) * c->p.cs_smag);
     cudaError_t e = cudaSuccess;
@@ -382,13 +385,24 @@ lbm_status lbm_adjoint_segment(lbm_ctx* c, const float* ckpt, int64_t n0, int32_
     for (int32_t j = k - 1; j >= 0 && e == cudaSuccess; --j) {
         const int64_t n = n0 + j;
         const float* st = j == 0 ? ckpt : seg + (size_t)j * S;
-        e = launch_adjoint_step(c->kp, st, cur, nxt, dJdCs_dev, n >= 1 ? 1.0f : 0.0f, dAdCs,
-                                c->stream);
+        e = launch_adjoint_step(c->kp, st, cur, nxt, dJdCs_dev, n >= 1 ? (float)w_fw : 0.0f,
+                                dAdCs, c->stream);
         float* t = cur; cur = nxt; nxt = t;
     }
     if (e == cudaSuccess && cur != lam)
         e = cudaMemcpyAsync(lam, cur, S * sizeof(float), cudaMemcpyDeviceToDevice, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "adjoint segment");
+    return LBM_OK;
+}
+
+lbm_status lbm_front_adjoint(lbm_ctx* c, const float* state, float* lam, double* front_dev) {
+    if (!c) return arg_fail(nullptr, "ctx is NULL");
+    if (!state) return arg_fail(c, "state is NULL");
+    if (lam == state) return arg_fail(c, "lam must not alias state");
+    cudaError_t e = launch_front_adjoint(c->kp, q_of(&c->p), ns_of(&c->p), c->v, state, lam,
+                                         front_dev, c->p.front_threshold, c->p.x0,
+                                         (double)c->p.H, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "front_adjoint launch");
     return LBM_OK;
 }
 

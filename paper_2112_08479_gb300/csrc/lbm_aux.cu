@@ -327,6 +327,98 @@ __global__ void adjoint_chi0_kernel(unsigned N, int Q, const float* __restrict__
 
 // ---------------------------------------------------------------------------
 // Launchers.
+// ---------------------------------------------------------------------------
+// Front of a canonical FP32 state (Sec. 3.1, reading R11) and its derivative:
+// the interpolated front x_f = x + (m0 - thr) / (m0 - m1), m0 = m(x) >= thr >
+// m1 = m(x + 1), m(x) = max_z chibar(x, z), depends on the state only through
+// chibar at the two maximising (x, z), each the mean over y of chi = 1 +
+// sum_k (Phi_k - w_k).  Hence d value / d(Phi_k - w_k) is g0 / ny on the
+// column (x, ., z0) and g1 / ny on (x + 1, ., z1), zero elsewhere, with
+//   g0 = (thr - m1) / ((m0 - m1)^2 H),  g1 = (m0 - thr) / ((m0 - m1)^2 H).
+// When no column reaches thr, or the crossing column is the last one, the
+// front does not move with the state and the derivative is zero.
+__global__ void __launch_bounds__(DIAG_BX) front_columns_kernel(KParams kp, int Q, int NS,
+                                                                const float* __restrict__ s,
+                                                                float* __restrict__ chibar,
+                                                                unsigned* __restrict__ colmax) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int z = blockIdx.y;
+    if (x >= kp.nx) return;
+    Kahan kc;
+    for (int y = 0; y < kp.ny; ++y) {
+        const unsigned n = (unsigned)x + (unsigned)kp.nx * ((unsigned)y + (unsigned)kp.ny * (unsigned)z);
+        float c = 0.0f;
+        for (int k = 0; k < NS; ++k) c += s[(size_t)(Q + k) * kp.N + n];
+        kc.add(c);
+    }
+    const float cb = 1.0f + (kc.s + kc.c) / (float)kp.ny;
+    chibar[(size_t)z * kp.nx + x] = cb;
+    atomicMax(colmax + x, fkey(cb));
+}
+
+__global__ void __launch_bounds__(FIN_T) front_finalize_kernel(int nx, int nz,
+                                                               const float* __restrict__ chibar,
+                                                               unsigned* __restrict__ colmax,
+                                                               FrontGrad* __restrict__ out,
+                                                               double* __restrict__ value,
+                                                               double thr, int x0, double H) {
+    __shared__ int sx[FIN_T];
+    const int t = threadIdx.x;
+    int xf = -1;
+    for (int x = t; x < nx; x += FIN_T)
+        if ((double)fkey_inv(colmax[x]) >= thr) xf = x;
+    sx[t] = xf;
+    __syncthreads();
+    for (int w = FIN_T / 2; w > 0; w >>= 1) {
+        if (t < w) sx[t] = max(sx[t], sx[t + w]);
+        __syncthreads();
+    }
+    if (t == 0) {
+        const int x = sx[0];
+        FrontGrad g;
+        g.x = x; g.z0 = 0; g.z1 = 0; g.valid = 0; g.g0 = 0.0; g.g1 = 0.0;
+        double xn;
+        if (x < 0) xn = -1.0;
+        else if (x == nx - 1) xn = (double)x;
+        else {
+            const unsigned k0 = colmax[x], k1 = colmax[x + 1];
+            const double m0 = fkey_inv(k0), m1 = fkey_inv(k1);
+            const double d = m0 - m1;
+            xn = x + (m0 - thr) / d;
+            g.g0 = (thr - m1) / (d * d * H);
+            g.g1 = (m0 - thr) / (d * d * H);
+            // the first z attaining each maximum
+            int z0 = -1, z1 = -1;
+            for (int z = 0; z < nz && (z0 < 0 || z1 < 0); ++z) {
+                if (z0 < 0 && fkey(chibar[(size_t)z * nx + x]) == k0) z0 = z;
+                if (z1 < 0 && fkey(chibar[(size_t)z * nx + x + 1]) == k1) z1 = z;
+            }
+            g.z0 = z0; g.z1 = z1;
+            g.valid = z0 >= 0 && z1 >= 0;
+        }
+        g.value = (xn + 0.5 - x0) / H;
+        *out = g;
+        if (value) *value = g.value;
+    }
+    __syncthreads();
+    for (int x = t; x < nx; x += FIN_T) colmax[x] = 0x007fffffu;  // ready for the next call
+}
+
+// lam (zeroed by the caller's launcher) receives the derivative on the 2 ny
+// nodes it lives on, in every scalar row.
+__global__ void front_scatter_kernel(KParams kp, int Q, int NS, const FrontGrad* __restrict__ g,
+                                     float* __restrict__ lam) {
+    const int y = blockIdx.x * blockDim.x + threadIdx.x;
+    if (y >= kp.ny || !g->valid) return;
+    const float a0 = (float)(g->g0 / kp.ny), a1 = (float)(g->g1 / kp.ny);
+    const unsigned n0 = (unsigned)g->x + (unsigned)kp.nx * ((unsigned)y + (unsigned)kp.ny * (unsigned)g->z0);
+    const unsigned n1 = (unsigned)(g->x + 1) + (unsigned)kp.nx * ((unsigned)y + (unsigned)kp.ny * (unsigned)g->z1);
+    for (int k = 0; k < NS; ++k) {
+        lam[(size_t)(Q + k) * kp.N + n0] = a0;
+        lam[(size_t)(Q + k) * kp.N + n1] = a1;
+    }
+}
+
 static inline dim3 node_grid(const KParams& kp) { return dim3((kp.nx + 127) / 128, kp.ny, kp.nz); }
 
 unsigned diag_block_count(int nx, int nz) { return (unsigned)((nx + DIAG_BX - 1) / DIAG_BX) * nz; }
@@ -429,6 +521,23 @@ cudaError_t launch_fw_accumulate(const KParams& kp, Kind k, bool odd, const View
             fw_kernel<Q, SL, false, S><<<grid, 128, 0, st>>>(kp, (const S*)v.f, (const S*)v.phi, acc, weight);
         return cudaGetLastError();
     });
+}
+
+cudaError_t launch_front_adjoint(const KParams& kp, int Q, int NS, const Views& v,
+                                 const float* state, float* lam, double* value, double threshold,
+                                 int x0, double H, cudaStream_t st) {
+    dim3 grid((kp.nx + DIAG_BX - 1) / DIAG_BX, kp.nz);
+    front_columns_kernel<<<grid, DIAG_BX, 0, st>>>(kp, Q, NS, state, v.chibar, v.colmax);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    front_finalize_kernel<<<1, FIN_T, 0, st>>>(kp.nx, kp.nz, v.chibar, v.colmax, v.fgrad, value,
+                                               threshold, x0, H);
+    e = cudaGetLastError();
+    if (e != cudaSuccess || !lam) return e;
+    e = cudaMemsetAsync(lam, 0, (size_t)(Q + NS) * kp.N * sizeof(float), st);
+    if (e != cudaSuccess) return e;
+    front_scatter_kernel<<<(kp.ny + 127) / 128, 128, 0, st>>>(kp, Q, NS, v.fgrad, lam);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint_chi0(const KParams& kp, const float* lam0, float* grad, cudaStream_t st) {

@@ -14,6 +14,15 @@ struct DevDiag {
     double front, front_node, Fw, mass_delta, scalar_mass;
 };
 
+// Front of a canonical state and its derivative with respect to the
+// column maxima it interpolates between (lbm_front_adjoint).
+struct FrontGrad {
+    double value;     // (x_f + 1/2 - x0) / H
+    double g0, g1;    // d value / d m(x), d value / d m(x + 1)
+    int x, z0, z1;    // crossing column x and the z of the maxima of x and x + 1
+    int valid;        // 1 when x + 1 < nx (the interpolated case)
+};
+
 // Workspace views handed to the launchers.
 struct Views {
     void* f;              // Q * N storage elements
@@ -24,6 +33,7 @@ struct Views {
     double* part;         // 2 doubles per diagnostics block
     float* fwpart;        // 2 floats per diagnostics block
     DevDiag* ddiag;       // one record
+    FrontGrad* fgrad;     // one record
     int* devflags;        // sticky device flags
     unsigned diag_blocks; // number of diagnostics blocks
 };
@@ -58,6 +68,9 @@ cudaError_t launch_fw_accumulate(const KParams& kp, Kind k, bool odd, const View
 cudaError_t launch_adjoint_step(const KParams& kp, const float* state, const float* lam_next,
                                 float* lam, double* dcs, float wfw, float dAdCs, cudaStream_t st);
 cudaError_t launch_push_step(const KParams& kp, const float* src, float* dst, cudaStream_t st);
+cudaError_t launch_front_adjoint(const KParams& kp, int Q, int NS, const Views& v,
+                                 const float* state, float* lam, double* value, double threshold,
+                                 int x0, double H, cudaStream_t st);
 cudaError_t launch_adjoint_chi0(const KParams& kp, const float* lam0, float* grad, cudaStream_t st);
 
 unsigned diag_block_count(int nx, int nz);

@@ -73,7 +73,8 @@ SIGNATURES = [
     ("lbm_adjoint_step", C.c_int, [_CTX, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double]),
     ("lbm_objective_forward", C.c_int, [_CTX, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]),
     ("lbm_adjoint_segment", C.c_int, [_CTX, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p,
-                                      C.c_void_p, C.c_void_p, C.c_void_p]),
+                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_double]),
+    ("lbm_front_adjoint", C.c_int, [_CTX, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("lbm_adjoint_chi0", C.c_int, [_CTX, C.c_void_p, C.c_void_p]),
     ("lbm_diag_static", C.c_int, [_P, C.c_void_p, C.c_int64, C.c_void_p,
                                   C.POINTER(lbm_diagnostics)]),
@@ -182,8 +183,14 @@ def lbm_objective_forward(ctx, nsteps: int, K: int, ckpt_ptr, J_ptr):
     _check(load().lbm_objective_forward(ctx, nsteps, K, ckpt_ptr, J_ptr), ctx)
 
 
-def lbm_adjoint_segment(ctx, ckpt_ptr, n0: int, k: int, seg_ptr, lam_ptr, tmp_ptr, dcs_ptr):
-    _check(load().lbm_adjoint_segment(ctx, ckpt_ptr, n0, k, seg_ptr, lam_ptr, tmp_ptr, dcs_ptr), ctx)
+def lbm_adjoint_segment(ctx, ckpt_ptr, n0: int, k: int, seg_ptr, lam_ptr, tmp_ptr, dcs_ptr,
+                        w_fw: float = 1.0):
+    _check(load().lbm_adjoint_segment(ctx, ckpt_ptr, n0, k, seg_ptr, lam_ptr, tmp_ptr, dcs_ptr,
+                                      w_fw), ctx)
+
+
+def lbm_front_adjoint(ctx, state_ptr, lam_ptr, front_ptr):
+    _check(load().lbm_front_adjoint(ctx, state_ptr, lam_ptr, front_ptr), ctx)
 
 
 def lbm_adjoint_chi0(ctx, lam0_ptr, grad_ptr):
@@ -350,11 +357,16 @@ class Lattice:
                          dcs.data_ptr() if dcs is not None else None, w_fw)
 
     def objective_forward(self, nsteps: int, K: int, ckpt, acc):
-        lbm_objective_forward(self.ctx, nsteps, K, _ptr(ckpt), acc.data_ptr())
+        lbm_objective_forward(self.ctx, nsteps, K, _ptr(ckpt), _ptr(acc))
 
-    def adjoint_segment(self, ckpt, n0: int, k: int, seg, lam, tmp, dcs):
+    def adjoint_segment(self, ckpt, n0: int, k: int, seg, lam, tmp, dcs, w_fw: float = 1.0):
         lbm_adjoint_segment(self.ctx, ckpt.data_ptr(), n0, k, _ptr(seg), lam.data_ptr(),
-                            tmp.data_ptr(), dcs.data_ptr() if dcs is not None else None)
+                            tmp.data_ptr(), dcs.data_ptr() if dcs is not None else None, w_fw)
+
+    def front_adjoint(self, state, lam=None, value=None):
+        """Front of `state` (canonical layout) into `value` (one device double)
+        and its derivative into `lam`; either may be None."""
+        lbm_front_adjoint(self.ctx, state.data_ptr(), _ptr(lam), _ptr(value))
 
     def adjoint_chi0(self, lam0, grad):
         lbm_adjoint_chi0(self.ctx, lam0.data_ptr(), grad.data_ptr())

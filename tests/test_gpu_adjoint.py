@@ -8,7 +8,7 @@ import pytest
 import oracle as O
 from oracle import adjoint_ref as A
 from paper_2112_08479_gb300 import inputs, lbm
-from paper_2112_08479_gb300.objective import friction_objective
+from paper_2112_08479_gb300.objective import friction_objective, front_objective
 
 from helpers import canonical_to_oracle, oracle_params, weights
 
@@ -170,3 +170,84 @@ def test_segment_matches_per_step_adjoint():
     # the recomputed trajectory is the recorded one
     for j in range(1, k):
         assert torch.allclose(seg[j], traj[j], rtol=0, atol=1e-7)
+
+
+# ---------------------------------------------------------------------------
+# Front objective (Sec. 3.1, reading R11): lbm_front_adjoint and the adjoint
+# sweep with the friction weight 0.
+
+def _front_state(p, seed):
+    """Canonical state whose scalar falls from ~1 to ~0 around x = nx / 2
+    (distinct values, so the crossing column and the maximising z are
+    unique), with a random fluid part."""
+    w = weights(p.model)
+    fdev = w[:, None] * inputs.uniform((p.Q, p.N), seed, 0.05)
+    x = np.tile(np.arange(p.nx), p.ny * p.nz)
+    chi = 1.0 / (1.0 + np.exp(2.0 * (x - p.nx / 2 - 0.37)))
+    chi = chi * (1 + 0.05 * inputs.uniform(p.N, seed + 1, 1.0)) + 1e-3 * inputs.uniform(p.N, seed + 2, 1.0)
+    w7 = O.velocities_q7()[1]
+    phi = w7[:, None] * (chi[None, :] * (1 + inputs.uniform((7, p.N), seed + 3, 0.05)) - 1.0)
+    return np.concatenate([fdev, phi]).astype(np.float32)
+
+
+@pytest.mark.parametrize("model", [0, 1])
+@pytest.mark.parametrize("thr", [0.02, 0.5])
+def test_front_adjoint_of_a_state(model, thr):
+    p = _sub_case(nx=40, ny=5, nz=6, model=model, front_threshold=thr)
+    lat = lbm.Lattice(p, device="cuda")
+    s0 = _front_state(p, 4)
+    st = torch.from_numpy(s0).cuda()
+    lam = torch.full((p.Q + 7, p.N), 7.0, device="cuda")
+    val = torch.zeros(1, dtype=torch.float64, device="cuda")
+    lat.front_adjoint(st, lam, val)
+    got = lam.cpu().numpy().astype(np.float64)
+    # oracle: chi from the stored values in FP64, front and its gradient
+    chi = (1.0 + s0[p.Q:].astype(np.float64).sum(0)).reshape(p.nz, p.ny, p.nx)
+    want_val = (O.front_node(chi, thr) + 0.5 - p.x0) / p.H
+    assert val.item() == pytest.approx(want_val, abs=1e-5 / p.H)
+    step = A.BGKStep(oracle_params(lbm.Params(nx=p.nx, ny=p.ny, nz=p.nz, x0=p.x0, H=p.H)))
+    c = torch.tensor(chi, dtype=torch.float64, requires_grad=True)
+    J = step.front(step.w.expand(*chi.shape, 19), c[..., None] * step.w7, p.x0, p.H, thr)
+    (g,) = torch.autograd.grad(J, c)
+    g = g.numpy().reshape(-1)
+    assert np.all(got[: p.Q] == 0.0)
+    for k in range(7):
+        row = got[p.Q + k]
+        assert np.array_equal(row != 0.0, g != 0.0)
+        assert np.abs(row - g).max() < 1e-5 * np.abs(g).max()
+
+
+def test_front_adjoint_degenerate_fronts():
+    """No column at or above the threshold, and a front at the last column:
+    the front does not move with the state, the derivative is zero."""
+    p = _sub_case(nx=12, ny=3, nz=4)
+    lat = lbm.Lattice(p, device="cuda")
+    for chi_val, node in ((0.0, -1.0), (1.0, p.nx - 1.0)):
+        s = np.zeros((26, p.N), dtype=np.float32)
+        w7 = O.velocities_q7()[1]
+        s[19:] = (w7 * (chi_val - 1.0))[:, None]
+        lam = torch.full((26, p.N), 7.0, device="cuda")
+        val = torch.zeros(1, dtype=torch.float64, device="cuda")
+        lat.front_adjoint(torch.from_numpy(s).cuda(), lam, val)
+        assert val.item() == pytest.approx((node + 0.5 - p.x0) / p.H)
+        assert torch.count_nonzero(lam).item() == 0
+
+
+def test_front_gradient_vs_fp64_reference_sub_case():
+    """Front after 800 steps of the 32 x 4 x 8 sub-case (mid-domain, the
+    crossing column and maximising z separated by >= 9e-4 in chibar), with
+    checkpoints every 100 steps, vs the FP64 reference gradient."""
+    p = _sub_case()
+    nsteps = 800
+    chi0 = O.lock_chi0(p.nx, p.ny, p.nz, p.x0, p.noise_amp, p.seed)
+    J_ref, g_ref, gcs_ref = A.gradient(oracle_params(p), chi0, p.cs_smag, nsteps,
+                                       objective="front", x0=p.x0, H=p.H)
+    x = torch.tensor(chi0.ravel(), dtype=torch.float32, device="cuda", requires_grad=True)
+    cs = torch.tensor(p.cs_smag, dtype=torch.float64, device="cuda", requires_grad=True)
+    J = front_objective(x, cs, p, nsteps, K=100)
+    J.backward()
+    assert J.item() == pytest.approx(J_ref, abs=1e-4)
+    g = x.grad.cpu().numpy().astype(np.float64)
+    rel = np.linalg.norm(g - g_ref.ravel()) / np.linalg.norm(g_ref)
+    assert rel < 1e-3, rel
+    assert cs.grad.item() == pytest.approx(gcs_ref, rel=1e-3)

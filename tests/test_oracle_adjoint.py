@@ -62,3 +62,87 @@ def test_gradient_matches_central_differences(flags):
     pm.cs_smag -= h
     fd = (_J_c_oracle(pp, chi0, n) - _J_c_oracle(pm, chi0, n)) / (2 * h)
     assert gcs == pytest.approx(fd, rel=1e-5)
+
+
+# ---------------------------------------------------------------------------
+# Front objective (Sec. 3.1, reading R11)
+
+def _front_field(seed, nx=12, ny=3, nz=4, xc=6.4):
+    """A distinct-valued scalar field that falls from ~1 to ~0 around x = xc,
+    so that the threshold crossing lies between two interior columns."""
+    x = np.arange(nx)[None, None, :]
+    base = 1.0 / (1.0 + np.exp(3.0 * (x - xc)))
+    noise = 0.05 * inputs.uniform((nz, ny, nx), seed, 1.0)
+    return np.clip(base + noise * base, 0.0, None) + 1e-3 * inputs.uniform((nz, ny, nx), seed + 1, 1.0)
+
+
+def _torch_front(chi, x0, H, thr=0.02):
+    st = A.BGKStep(_params(nx=chi.shape[2], ny=chi.shape[1], nz=chi.shape[0]))
+    c = torch.tensor(chi, dtype=torch.float64, requires_grad=True)
+    phi = c[..., None] * st.w7
+    f = st.w.expand(*chi.shape, 19)
+    return st.front(f, phi, x0, H, thr), c
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_torch_front_matches_c_front(seed):
+    chi = _front_field(seed)
+    for thr in (0.02, 0.3, 0.9):
+        J, _ = _torch_front(chi, 5, 4.0, thr)
+        want = (O.front_node(chi, thr) + 0.5 - 5) / 4.0
+        assert float(J.detach()) == pytest.approx(want, abs=1e-14)
+    # no column reaches the threshold; the last column does
+    J, _ = _torch_front(np.zeros((4, 3, 12)), 5, 4.0)
+    assert float(J) == pytest.approx((-1 + 0.5 - 5) / 4.0)
+    J, _ = _torch_front(np.ones((4, 3, 12)), 5, 4.0)
+    assert float(J) == pytest.approx((11 + 0.5 - 5) / 4.0)
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_front_gradient_matches_central_differences_of_c_front(seed):
+    """The interpolated front is smooth away from a change of crossing column
+    or maximising z; node by node, the torch gradient equals central
+    differences of the C oracle's front."""
+    chi = _front_field(seed)
+    x0, H, thr = 5, 4.0, 0.3
+    J, c = _torch_front(chi, x0, H, thr)
+    (g,) = torch.autograd.grad(J, c)
+    g = g.numpy()
+    eps = 1e-6
+    fd = np.zeros_like(chi)
+    for idx in np.ndindex(chi.shape):
+        a, b = chi.copy(), chi.copy()
+        a[idx] += eps
+        b[idx] -= eps
+        fd[idx] = ((O.front_node(a, thr) - O.front_node(b, thr)) / (2 * eps)) / H
+    assert np.count_nonzero(fd) == 2 * chi.shape[1]      # (x_f, ., z0) and (x_f + 1, ., z1)
+    assert np.abs(g - fd).max() < 1e-7 * np.abs(fd).max()
+
+
+def _front_c_oracle(p, chi0, nsteps, x0, H):
+    f, phi = O.init(p, chi0)
+    f, phi = O.run(p, nsteps, f, phi)
+    return O.diag(p, f, phi, x0, H)["front"]
+
+
+def test_front_objective_gradient_matches_central_differences():
+    """Adjoint of the front after n steps of the lock exchange against central
+    differences of the C oracle, in random directions and in C_s."""
+    p = _params()
+    x0, H, n = 5, 6.0, 60
+    chi0 = O.lock_chi0(p.nx, p.ny, p.nz, x0, 1e-2, 3)
+    J, g, gcs = A.gradient(p, chi0, p.cs_smag, n, objective="front", x0=x0, H=H)
+    assert J == pytest.approx(_front_c_oracle(p, chi0, n, x0, H), abs=1e-12)
+    assert np.abs(g).max() > 0
+    eps = 1e-3
+    for seed in (1, 2, 3):
+        d = inputs.unit_direction(chi0.shape, seed)
+        fd = (_front_c_oracle(p, chi0 + eps * d, n, x0, H)
+              - _front_c_oracle(p, chi0 - eps * d, n, x0, H)) / (2 * eps)
+        assert np.sum(g * d) == pytest.approx(fd, rel=1e-4, abs=1e-9)
+    h = 1e-3
+    pp, pm = _params(), _params()
+    pp.cs_smag += h
+    pm.cs_smag -= h
+    fd = (_front_c_oracle(pp, chi0, n, x0, H) - _front_c_oracle(pm, chi0, n, x0, H)) / (2 * h)
+    assert gcs == pytest.approx(fd, rel=1e-4, abs=1e-9)

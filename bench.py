@@ -39,10 +39,13 @@ WORKLOADS = {
 WORKLOAD = dict(WORKLOADS["config3"])
 def bytes_per_node(model="bgk", storage="fp32", scalar="q7") -> int:
     """Algorithmic bytes of one node update: every population read once and
-    written once (AA in place), (Q + NS) populations of 4 or 2 bytes."""
+    written once (AA in place), (Q + NS) populations of 4 or 2 bytes; with
+    16-bit storage the scalar's rest population (D3Q7, D3Q27) is FP32."""
     q = 19 if model == "bgk" else 27
     ns = {"q7": 7, "q6": 6, "q27": 27}[scalar]
-    return (q + ns) * 2 * (4 if storage == "fp32" else 2)
+    if storage == "fp32":
+        return (q + ns) * 2 * 4
+    return (q + ns) * 2 * 2 + (4 if scalar != "q6" else 0)
 PROFILE = os.path.join(ROOT, "profiles", "aa_step_bgk_fp32_traffic.md")
 # the sources that define the headline step kernel (bgk_step2_kernel)
 KERNEL_SOURCES = ["paper_2112_08479_gb300/csrc/lbm_bgk.cu",

@@ -29,6 +29,7 @@ template <> struct PairIO<float> {
     static __device__ __forceinline__ void st(float* p, float a, float b) {
         st_pop(reinterpret_cast<float2*>(p), make_float2(a, b));
     }
+    static __device__ __forceinline__ void rnd(float& a, float& b) {}
 };
 template <> struct PairIO<__half> {
     static __device__ __forceinline__ void ld(const __half* p, float& a, float& b) {
@@ -38,6 +39,10 @@ template <> struct PairIO<__half> {
     }
     static __device__ __forceinline__ void st(__half* p, float a, float b) {
         st_pop(reinterpret_cast<__half2*>(p), __floats2half2_rn(a, b));
+    }
+    static __device__ __forceinline__ void rnd(float& a, float& b) {
+        const float2 f = __half22float2(__floats2half2_rn(a, b));
+        a = f.x; b = f.y;
     }
 };
 template <> struct PairIO<__nv_bfloat16> {
@@ -49,7 +54,28 @@ template <> struct PairIO<__nv_bfloat16> {
     static __device__ __forceinline__ void st(__nv_bfloat16* p, float a, float b) {
         st_pop(reinterpret_cast<__nv_bfloat162*>(p), __floats2bfloat162_rn(a, b));
     }
+    static __device__ __forceinline__ void rnd(float& a, float& b) {
+        const float2 f = __bfloat1622float2(__floats2bfloat162_rn(a, b));
+        a = f.x; b = f.y;
+    }
 };
+
+// feed_rest (lbm_common.cuh) for a node pair, with paired conversions.
+template <typename S, int NS>
+__device__ __forceinline__ void feed_rest2(float (&p0)[NS], float (&p1)[NS]) {
+    float e0 = 0.0f, e1 = 0.0f;
+#pragma unroll
+    for (int k = 1; k < NS; ++k) {
+        float r0 = p0[k], r1 = p1[k];
+        PairIO<S>::rnd(r0, r1);
+        e0 += p0[k] - r0;
+        e1 += p1[k] - r1;
+        p0[k] = r0;
+        p1[k] = r1;
+    }
+    p0[0] += e0;
+    p1[0] += e1;
+}
 
 // Neighbourhood of a node pair (x, x + 1), x even.
 struct Stencil2 {
@@ -90,7 +116,8 @@ __device__ __forceinline__ Stencil2 make_stencil2(const KParams& kp, int x, int 
 // loads, predicated, (3) the shuffles that hand the shifted element across.
 // A z wall (uniform over the block) turns a direction into a bounce-back from
 // the node's own slot, selected without branching.
-template <int Q, bool ODD, typename S, int D0 = 0>
+// R32: population 0 (direction 0) lives in the FP32 rest row (rest_row).
+template <int Q, bool ODD, typename S, int D0 = 0, bool R32 = false>
 __device__ __forceinline__ void gather2(const KParams& kp, const S* __restrict__ a,
                                         const Stencil2& st, float (&v0)[Q], float (&v1)[Q]) {
     const unsigned N = kp.N;
@@ -98,6 +125,11 @@ __device__ __forceinline__ void gather2(const KParams& kp, const S* __restrict__
 #pragma unroll
     for (int k = 0; k < Q; ++k) {
         const int i = k + D0;       // direction; population k lives in row k
+        if (R32 && i == 0) {
+            P0[k] = 0.0f; P1[k] = 0.0f;
+            if (st.active) PairIO<float>::ld(rest_row(a, Q, N) + st.n, P0[k], P1[k]);
+            continue;
+        }
         unsigned off = (unsigned)k * N + st.n;
         if (ODD && i != 0) {
             const int dy = -cy27(i), dz = -cz27(i);
@@ -148,7 +180,7 @@ __device__ __forceinline__ void gather2(const KParams& kp, const S* __restrict__
 // The scatter first exchanges the shifted elements, then issues every store
 // under a predicate (pair stores for the interior lanes, single-element
 // stores for the edge lanes, pair stores into the own slots at a z wall).
-template <int Q, bool ODD, typename S, int D0 = 0>
+template <int Q, bool ODD, typename S, int D0 = 0, bool R32 = false>
 __device__ __forceinline__ void scatter2(const KParams& kp, S* __restrict__ a, const Stencil2& st,
                                          const float (&v0)[Q], const float (&v1)[Q]) {
     const unsigned N = kp.N;
@@ -165,6 +197,10 @@ __device__ __forceinline__ void scatter2(const KParams& kp, S* __restrict__ a, c
     for (int k = 0; k < Q; ++k) {
         const int i = k + D0;
         const int dx = cx27(i), dy = cy27(i), dz = cz27(i);
+        if (R32 && i == 0) {
+            if (st.active) PairIO<float>::st(rest_row(a, Q, N) + st.n, v0[k], v1[k]);
+            continue;
+        }
         const unsigned own = (unsigned)(opp(i) - D0) * N + st.n;
         if (!ODD || i == 0) {
             if (st.active) PairIO<S>::st(a + own, v0[k], v1[k]);

@@ -86,6 +86,9 @@ Layout layout(const lbm_params* p) {
     size_t o = 0;
     L.f = o;      o = up(o + (size_t)q_of(p) * N * es);
     L.phi = o;    o = up(o + (size_t)ns_of(p) * N * es);
+    // 16-bit storage: the scalar's rest population in an FP32 row after the
+    // 16-bit rows (rest_row in lbm_common.cuh; none on D3Q6)
+    if (es == 2 && p->scalar != LBM_SCALAR_Q6) o = up(o + N * sizeof(float));
     L.stage = o;  o = up(o + N * sizeof(float));
     L.chibar = o; o = up(o + (size_t)p->nx * p->nz * sizeof(float));
     L.colmax = o; o = up(o + (size_t)p->nx * sizeof(unsigned));

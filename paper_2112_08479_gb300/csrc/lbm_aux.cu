@@ -31,7 +31,7 @@ __device__ __forceinline__ void node_macros(const KParams& kp, const S* __restri
     const Stencil st = make_stencil(kp, x, y, z);
     float fv[Q], pv[NS];
     gather<Q, ODD>(kp, f, st, fv);
-    gather<NS, ODD, S, ScalarLat<SL>::D0>(kp, phi, st, pv);
+    gather<NS, ODD, S, ScalarLat<SL>::D0, rest32<S, SL>()>(kp, phi, st, pv);
     float c = 0.0f;   // chi - 1 (Phi is held as Phi - w)
 #pragma unroll
     for (int k = 0; k < NS; ++k) c += pv[k];
@@ -88,8 +88,11 @@ __global__ void init_kernel(KParams kp, S* __restrict__ f, S* __restrict__ phi,
 #pragma unroll
     for (int i = 0; i < Q; ++i) Store<S>::st(f + (size_t)i * N + n, 0.0f);
 #pragma unroll
-    for (int k = 0; k < ScalarLat<SL>::NS; ++k)
-        Store<S>::st(phi + (size_t)k * N + n, kp.sp * (ScalarLat<SL>::w(k) * c));
+    for (int k = 0; k < ScalarLat<SL>::NS; ++k) {
+        const float v = kp.sp * (ScalarLat<SL>::w(k) * c);
+        if (rest32<S, SL>() && k == 0) rest_row(phi, ScalarLat<SL>::NS, kp.N)[n] = v;
+        else Store<S>::st(phi + (size_t)k * N + n, v);
+    }
 }
 
 __global__ void fill_keys_kernel(unsigned* __restrict__ keys, int n, int* __restrict__ flags,
@@ -127,7 +130,7 @@ __global__ void get_state_kernel(KParams kp, const S* __restrict__ f, const S* _
     const unsigned n = st.n;
     float fv[Q], pv[NS];
     gather<Q, ODD>(kp, f, st, fv);
-    gather<NS, ODD, S, ScalarLat<SL>::D0>(kp, phi, st, pv);
+    gather<NS, ODD, S, ScalarLat<SL>::D0, rest32<S, SL>()>(kp, phi, st, pv);
     const size_t N = kp.N;
 #pragma unroll
     for (int i = 0; i < Q; ++i) dst[(size_t)i * N + n] = is16<S>() ? fv[i] * kp.isf : fv[i];
@@ -151,7 +154,8 @@ __global__ void set_state_kernel(KParams kp, S* __restrict__ f, S* __restrict__ 
 #pragma unroll
     for (int k = 0; k < ScalarLat<SL>::NS; ++k) {
         const float v = src[(size_t)(Q + k) * N + n];
-        Store<S>::st(phi + (size_t)k * N + n, is16<S>() ? v * kp.sp : v);
+        if (rest32<S, SL>() && k == 0) rest_row(phi, ScalarLat<SL>::NS, kp.N)[n] = v * kp.sp;
+        else Store<S>::st(phi + (size_t)k * N + n, is16<S>() ? v * kp.sp : v);
     }
 }
 

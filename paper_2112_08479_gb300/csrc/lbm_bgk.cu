@@ -37,9 +37,10 @@ __global__ void __launch_bounds__(128, LBM_STEP_MINB) bgk_step_kernel(KParams kp
     const unsigned n = st.n;
 
     constexpr int NS = ScalarLat<SL>::NS, D0 = ScalarLat<SL>::D0;
+    constexpr bool R32 = rest32<S, SL>();
     float fv[19], pv[NS];
     gather<19, ODD>(kp, f, st, fv);
-    gather<NS, ODD, S, D0>(kp, phi, st, pv);
+    gather<NS, ODD, S, D0, R32>(kp, phi, st, pv);
     constexpr bool s16 = !std::is_same<S, float>::value;   // populations in storage units
     if (SAVE) {
         const size_t N = kp.N;
@@ -49,8 +50,9 @@ __global__ void __launch_bounds__(128, LBM_STEP_MINB) bgk_step_kernel(KParams kp
         for (int k = 0; k < NS; ++k) save[(size_t)(19 + k) * N + n] = s16 ? pv[k] * kp.isp : pv[k];
     }
     if (!(kp.flags & LBM_FLAG_NO_COLLIDE)) collide_bgk<s16, SL>(kp, fv, pv);
+    if constexpr (R32) feed_rest<S>(pv);
     scatter<19, ODD>(kp, f, st, fv);
-    scatter<NS, ODD, S, D0>(kp, phi, st, pv);
+    scatter<NS, ODD, S, D0, R32>(kp, phi, st, pv);
 }
 
 
@@ -63,9 +65,10 @@ __global__ void __launch_bounds__(128, LBM_STEP2_MINB) bgk_step2_kernel(KParams 
     const int x = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     const Stencil2 st = make_stencil2(kp, x, blockIdx.y, blockIdx.z);
     constexpr int NS = ScalarLat<SL>::NS, D0 = ScalarLat<SL>::D0;
+    constexpr bool R32 = rest32<S, SL>();
     float f0[19], f1[19], p0[NS], p1[NS];
     gather2<19, ODD>(kp, f, st, f0, f1);
-    gather2<NS, ODD, S, D0>(kp, phi, st, p0, p1);
+    gather2<NS, ODD, S, D0, R32>(kp, phi, st, p0, p1);
     constexpr bool s16 = !std::is_same<S, float>::value;   // populations in storage units
     if (SAVE && st.active) {
         const unsigned N = kp.N;
@@ -82,8 +85,9 @@ __global__ void __launch_bounds__(128, LBM_STEP2_MINB) bgk_step2_kernel(KParams 
         collide_bgk<s16, SL>(kp, f0, p0);
         collide_bgk<s16, SL>(kp, f1, p1);
     }
+    if constexpr (R32) feed_rest2<S>(p0, p1);
     scatter2<19, ODD>(kp, f, st, f0, f1);
-    scatter2<NS, ODD, S, D0>(kp, phi, st, p0, p1);
+    scatter2<NS, ODD, S, D0, R32>(kp, phi, st, p0, p1);
 }
 
 template <typename S, int SL>

@@ -14,6 +14,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "../../include/lbm.h"
 
 namespace lbmgpu {
@@ -136,10 +138,12 @@ template <typename S> struct Store;
 template <> struct Store<float> {
     static __device__ __forceinline__ float ld(const float* p) { return ld_pop(p); }
     static __device__ __forceinline__ void st(float* p, float v) { st_pop(p, v); }
+    static __device__ __forceinline__ float rnd(float v) { return v; }
 };
 template <> struct Store<__half> {
     static __device__ __forceinline__ float ld(const __half* p) { return __half2float(ld_pop(p)); }
     static __device__ __forceinline__ void st(__half* p, float v) { st_pop(p, __float2half_rn(v)); }
+    static __device__ __forceinline__ float rnd(float v) { return __half2float(__float2half_rn(v)); }
 };
 template <> struct Store<__nv_bfloat16> {
     static __device__ __forceinline__ float ld(const __nv_bfloat16* p) {
@@ -148,7 +152,49 @@ template <> struct Store<__nv_bfloat16> {
     static __device__ __forceinline__ void st(__nv_bfloat16* p, float v) {
         st_pop(p, __float2bfloat16_rn(v));
     }
+    static __device__ __forceinline__ float rnd(float v) {
+        return __bfloat162float(__float2bfloat16_rn(v));
+    }
 };
+
+// ---------------------------------------------------------------------------
+// With 16-bit storage the scalar's rest population is kept in FP32: a row of
+// N floats after the NS 16-bit rows of the scalar array, at the next 256-byte
+// boundary (the 16-bit row of the rest population is unused).  Each step the
+// storage roundings of the moving populations are added to it (feed_rest),
+// so the 16-bit forms conserve sum chi up to FP32 rounding: rounding the
+// scalar to 16 bits otherwise loses or gains mass systematically wherever a
+// node's increments fall below half an ulp (the tails of the interface).
+__host__ __device__ constexpr size_t rest_row_bytes(int rows, size_t N, size_t es) {
+    return (rows * N * es + 255) / 256 * 256;
+}
+template <typename S>
+__device__ __forceinline__ float* rest_row(S* a, int rows, unsigned N) {
+    return reinterpret_cast<float*>(reinterpret_cast<char*>(a) + rest_row_bytes(rows, N, sizeof(S)));
+}
+template <typename S>
+__device__ __forceinline__ const float* rest_row(const S* a, int rows, unsigned N) {
+    return reinterpret_cast<const float*>(reinterpret_cast<const char*>(a) +
+                                          rest_row_bytes(rows, N, sizeof(S)));
+}
+template <typename S, int SL>
+__host__ __device__ constexpr bool rest32() {
+    return !std::is_same<S, float>::value && SL != 6;
+}
+
+// Rounds populations 1 .. NS-1 (storage units) to the storage type and adds
+// their rounding errors to population 0, which is stored in FP32.
+template <typename S, int NS>
+__device__ __forceinline__ void feed_rest(float (&p)[NS]) {
+    float e = 0.0f;
+#pragma unroll
+    for (int k = 1; k < NS; ++k) {
+        const float r = Store<S>::rnd(p[k]);
+        e += p[k] - r;
+        p[k] = r;
+    }
+    p[0] += e;
+}
 
 // ---------------------------------------------------------------------------
 // Neighbourhood of one node, computed once per thread: the node indices of
@@ -202,13 +248,18 @@ __device__ __forceinline__ unsigned nbr(const Stencil& s, int dx, int dy, int dz
 
 // Population k is direction dk = k + D0 and lives in row k; its opposite
 // direction's row is opp(dk) - D0.
-template <int Q, bool ODD, typename S, int D0 = 0>
+// R32: population 0 (direction 0) lives in the FP32 rest row (rest_row).
+template <int Q, bool ODD, typename S, int D0 = 0, bool R32 = false>
 __device__ __forceinline__ void gather(const KParams& kp, const S* __restrict__ a,
                                        const Stencil& st, float (&v)[Q]) {
     const unsigned N = kp.N;
 #pragma unroll
     for (int k = 0; k < Q; ++k) {
         const int d = k + D0;
+        if (R32 && d == 0) {
+            v[k] = ld_pop(rest_row(a, Q, N) + st.n);
+            continue;
+        }
         unsigned off = (unsigned)k * N + st.n;
         if (ODD && d != 0) {
             bool in;
@@ -219,13 +270,17 @@ __device__ __forceinline__ void gather(const KParams& kp, const S* __restrict__ 
     }
 }
 
-template <int Q, bool ODD, typename S, int D0 = 0>
+template <int Q, bool ODD, typename S, int D0 = 0, bool R32 = false>
 __device__ __forceinline__ void scatter(const KParams& kp, S* __restrict__ a, const Stencil& st,
                                         const float (&v)[Q]) {
     const unsigned N = kp.N;
 #pragma unroll
     for (int k = 0; k < Q; ++k) {
         const int d = k + D0;
+        if (R32 && d == 0) {
+            st_pop(rest_row(a, Q, N) + st.n, v[k]);
+            continue;
+        }
         unsigned off = (unsigned)(opp(d) - D0) * N + st.n;
         if (ODD && d != 0) {
             bool in;

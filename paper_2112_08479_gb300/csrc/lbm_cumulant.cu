@@ -120,6 +120,7 @@ __device__ __forceinline__ void collide_cumulant(const KParams& kp, float (&f)[2
     // for c = -1, 0, +1 (index c + 1)
     constexpr float R[3] = {1.0f, 0.0f, 1.0f / 3.0f};
     constexpr float W1[3] = {1.0f / 6.0f, 2.0f / 3.0f, 1.0f / 6.0f};
+    float dsum = 0.0f;
     float A[3][3][3];  // [a][b][cz + 1]
 #pragma unroll
     for (int a = 0; a < 3; ++a)
@@ -143,17 +144,28 @@ __device__ __forceinline__ void collide_cumulant(const KParams& kp, float (&f)[2
             // f*_i - w_i = drho w_i + rho (P_i - w_i)
             const int im = dir27(-1, b - 1, c - 1), i0 = dir27(0, b - 1, c - 1),
                       ip = dir27(1, b - 1, c - 1);
-            f[im] = drho * w27(im) + rho * pm;
-            f[i0] = drho * w27(i0) + rho * p0;
-            f[ip] = drho * w27(ip) + rho * pp;
+            const float vm = drho * w27(im) + rho * pm;
+            const float vp = drho * w27(ip) + rho * pp;
+            dsum += (vm - f[im]) + (vp - f[ip]);
+            f[im] = vm;
+            f[ip] = vp;
+            if (i0 != 0) {
+                const float v0 = drho * w27(i0) + rho * p0;
+                dsum += v0 - f[i0];
+                f[i0] = v0;
+            }
         }
+    // the rest population takes minus the sum of the stored changes of the
+    // others (in exact arithmetic the same value as its reconstruction), so
+    // the mass changes only by the rounding of f_0
+    f[0] -= dsum;
 
     const float hx = (jx + 0.5f * Fx) * irho, hy = (jy + 0.5f * Fy) * irho,
                 hz = (jz + 0.5f * Fz) * irho;
     if constexpr (SL == 7) {
         // scalar (Eq. 28-30) with the half-force velocity and the molecular D;
-        // non-equilibrium form whose parts sum to zero, so sum Phi is conserved
-        // up to the rounding of the stored results (see collide_bgk)
+        // non-equilibrium form closed by the rest population, so sum Phi is
+        // conserved up to the rounding of Phi_0 (see collide_bgk)
         const float omp = 1.0f / kp.taup0;
         const float pe = w7(1) * chit, pa = w7(1) * 4.0f * chi;
         float nq[7];
@@ -163,9 +175,14 @@ __device__ __forceinline__ void collide_cumulant(const KParams& kp, float (&f)[2
         nq[4] = p[4] - (pe - pa * hy);
         nq[5] = p[5] - (pe + pa * hz);
         nq[6] = p[6] - (pe - pa * hz);
-        nq[0] = -(((nq[1] + nq[2]) + (nq[3] + nq[4])) + (nq[5] + nq[6]));
+        float psum = 0.0f;
 #pragma unroll
-        for (int k = 0; k < 7; ++k) p[k] -= omp * nq[k];
+        for (int k = 1; k < 7; ++k) {
+            const float v = p[k] - omp * nq[k];
+            psum += v - p[k];
+            p[k] = v;
+        }
+        p[0] -= psum;
     } else {
         // D3Q27 factorized central moments (Eq. 37-51) with every rate of order
         // >= 2 equal to 1: the moments in the frame of u relax to their lattice
@@ -202,8 +219,9 @@ __device__ __forceinline__ void collide_cumulant(const KParams& kp, float (&f)[2
             G[a][0] = u[a] - 0.5f;
             G[a][2] = u[a] + 0.5f;
         }
+        float psum = 0.0f;
 #pragma unroll
-        for (int i = 0; i < 27; ++i) {
+        for (int i = 1; i < 27; ++i) {
             const int cx = cx27(i) + 1, cy = cy27(i) + 1, cz = cz27(i) + 1;
             const float Ex = W[0][cx] + dE[0][cx], Ey = W[1][cy] + dE[1][cy], Ez = W[2][cz] + dE[2][cz];
             // Ex Ey Ez - Wx Wy Wz without cancellation
@@ -211,8 +229,14 @@ __device__ __forceinline__ void collide_cumulant(const KParams& kp, float (&f)[2
                                 W[0][cx] * W[1][cy] * dE[2][cz];
             const float vt = v[0] * G[0][cx] * Ey * Ez + v[1] * Ex * G[1][cy] * Ez +
                              v[2] * Ex * Ey * G[2][cz];
-            p[i] = chit * w27(i) + chi * dprod + vt;
+            const float nv = chit * w27(i) + chi * dprod + vt;
+            psum += nv - p[i];
+            p[i] = nv;
         }
+        // the rest population closes the sum (its reconstruction
+        // chit w_0 + chi dprod_0 + vt_0 in exact arithmetic): sum Phi changes
+        // only by the rounding of Phi_0, not by that of the 27-term chi
+        p[0] -= psum;
     }
 }
 
@@ -226,9 +250,10 @@ __global__ void __launch_bounds__(128, LBM_STEP_MINB) cumulant_step_kernel(KPara
     const unsigned n = st.n;
 
     constexpr int NS = ScalarLat<SL>::NS;
+    constexpr bool R32 = rest32<S, SL>();
     float fv[27], pv[NS];
     gather<27, ODD>(kp, f, st, fv);
-    gather<NS, ODD>(kp, phi, st, pv);
+    gather<NS, ODD, S, 0, R32>(kp, phi, st, pv);
     if (!std::is_same<S, float>::value) {
 #pragma unroll
         for (int i = 0; i < 27; ++i) fv[i] *= kp.isf;
@@ -249,8 +274,9 @@ __global__ void __launch_bounds__(128, LBM_STEP_MINB) cumulant_step_kernel(KPara
 #pragma unroll
         for (int k = 0; k < NS; ++k) pv[k] *= kp.sp;
     }
+    if constexpr (R32) feed_rest<S>(pv);
     scatter<27, ODD>(kp, f, st, fv);
-    scatter<NS, ODD>(kp, phi, st, pv);
+    scatter<NS, ODD, S, 0, R32>(kp, phi, st, pv);
 }
 
 

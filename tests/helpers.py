@@ -100,3 +100,13 @@ def window_oracle(p: lbm.Params, state0: np.ndarray, node, steps: int):
     cx = int(np.where(xs == x)[0][0])
     cz = int(np.where(zs == z)[0][0])
     return f[cz, cy, cx] - weights(p.model), phi[cz, cy, cx] - wscalar(p)
+
+
+def rest_row_tol(phi_rows, rel):
+    """Bound on the error of the scalar's rest population under 16-bit storage,
+    where it is held in FP32 and receives the storage roundings of the moving
+    populations: at most one half-ulp (rel = 2^-11 FP16, 2^-8 BF16) of each
+    moving population.  phi_rows: the scalar populations (NS, ...) of the
+    reference, population 0 first."""
+    import numpy as np
+    return rel * np.abs(np.asarray(phi_rows)[1:]).sum(0) * 1.01

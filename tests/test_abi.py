@@ -91,7 +91,13 @@ def test_workspace_scales_with_storage(lib):
     b32 = lbm.lbm_workspace_bytes(_good(nx=256, ny=32, nz=64))
     b16 = lbm.lbm_workspace_bytes(_good(nx=256, ny=32, nz=64, storage=lbm.LBM_FP16S))
     N = 256 * 32 * 64
-    assert b32 - b16 == pytest.approx(26 * N * 2, abs=4096)
+    # 26 rows at half the width, plus the FP32 row of the scalar's rest
+    # population that 16-bit storage adds
+    assert b32 - b16 == pytest.approx(26 * N * 2 - N * 4, abs=4096)
+    b16q6 = lbm.lbm_workspace_bytes(_good(nx=256, ny=32, nz=64, storage=lbm.LBM_FP16S,
+                                          scalar=lbm.LBM_SCALAR_Q6))
+    b32q6 = lbm.lbm_workspace_bytes(_good(nx=256, ny=32, nz=64, scalar=lbm.LBM_SCALAR_Q6))
+    assert b32q6 - b16q6 == pytest.approx(25 * N * 2, abs=4096)   # D3Q6 has no rest population
 
 
 def test_init_checks_before_touching_the_device(lib):

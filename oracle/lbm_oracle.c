@@ -569,10 +569,18 @@ double orc_wall_friction(int nx, int ny, int nz, double nu, const double* u) {
 }
 
 /* Front (Sec. 3.1): chibar(x,z) = mean_y chi, m(x) = max_z chibar, x_f = the
- * largest x with m(x) >= thr, moved to the linear threshold crossing between
- * x_f and x_f + 1.  Returns the node coordinate (-1 when no column reaches
- * thr). */
-double orc_front_node(int nx, int ny, int nz, const double* chi, double thr) {
+ * largest x < xlim with m(x) >= thr, moved to the linear threshold crossing
+ * between x_f and x_f + 1 unless x_f = xlim - 1.  xlim = nx with walls at the
+ * x ends; with periodic ends (Fig. 4b) the columns ahead of the lock,
+ * xlim = (nx + x0) / 2 (orc_front_xlim).  Returns the node coordinate (-1
+ * when no column reaches thr). */
+int orc_front_xlim(int nx, int x0, int periodic_x) {
+    if (!periodic_x) return nx;
+    int h = (nx + x0) / 2;
+    return h < 1 ? 1 : h;
+}
+
+double orc_front_node_lim(int nx, int ny, int nz, const double* chi, double thr, int xlim) {
     double* m = (double*)malloc(sizeof(double) * nx);
     for (int x = 0; x < nx; ++x) m[x] = -INFINITY;
     for (int z = 0; z < nz; ++z)
@@ -583,13 +591,17 @@ double orc_front_node(int nx, int ny, int nz, const double* chi, double thr) {
         if (s > m[x]) m[x] = s;
     }
     int xf = -1;
-    for (int x = nx - 1; x >= 0; --x) if (m[x] >= thr) { xf = x; break; }
+    for (int x = xlim - 1; x >= 0; --x) if (m[x] >= thr) { xf = x; break; }
     double r;
     if (xf < 0) r = -1.0;
-    else if (xf == nx - 1) r = (double)xf;
+    else if (xf == xlim - 1) r = (double)xf;
     else r = xf + (m[xf] - thr) / (m[xf] - m[xf + 1]);
     free(m);
     return r;
+}
+
+double orc_front_node(int nx, int ny, int nz, const double* chi, double thr) {
+    return orc_front_node_lim(nx, ny, nz, chi, thr, nx);
 }
 
 /* out[0] = front position (x_f + 1/2 - x0) / H, out[1] = F_w,
@@ -601,7 +613,8 @@ void orc_diag(const orc_params* p, const double* f, const double* phi,
     double* u = (double*)malloc(sizeof(double) * N * 3);
     double* chi = (double*)malloc(sizeof(double) * N);
     orc_macros(p, f, phi, rho, u, chi);
-    double xf = orc_front_node(p->nx, p->ny, p->nz, chi, thr);
+    double xf = orc_front_node_lim(p->nx, p->ny, p->nz, chi, thr,
+                                   orc_front_xlim(p->nx, x0, p->periodic_x));
     out[0] = (xf + 0.5 - x0) / H;
     out[1] = orc_wall_friction(p->nx, p->ny, p->nz, p->nu, u);
     double sm = 0.0, sc = 0.0;

@@ -24,7 +24,7 @@ __all__ = [
     "feq_q19", "phieq_q7", "tau_eff", "collide_node", "cumulants27",
     "f_from_cumulants27", "bgk_nu_t", "lock_chi0", "init", "step", "run", "stream",
     "macros", "wall_friction", "front_node", "diag", "splitmix64", "velocities_scalar",
-    "phieq_q6",
+    "phieq_q6", "front_xlim",
 ]
 
 
@@ -123,6 +123,8 @@ def lib():
             "orc_macros": (None, [P, d, d, d, d, d]),
             "orc_wall_friction": (C.c_double, [C.c_int, C.c_int, C.c_int, C.c_double, d]),
             "orc_front_node": (C.c_double, [C.c_int, C.c_int, C.c_int, d, C.c_double]),
+            "orc_front_node_lim": (C.c_double, [C.c_int, C.c_int, C.c_int, d, C.c_double, C.c_int]),
+            "orc_front_xlim": (C.c_int, [C.c_int, C.c_int, C.c_int]),
             "orc_diag": (None, [P, d, d, C.c_int, C.c_double, C.c_double, d]),
             "orc_step": (None, [P, d, d]),
             "orc_run": (None, [P, C.c_int, d, d, d]),
@@ -304,11 +306,17 @@ def wall_friction(nu: float, u) -> float:
     return lib().orc_wall_friction(nx, ny, nz, nu, _d(u))
 
 
-def front_node(chi, thr: float = 0.02) -> float:
-    """Front node coordinate from the span-averaged field (Sec. 3.1, R11)."""
+def front_node(chi, thr: float = 0.02, xlim: int | None = None) -> float:
+    """Front node coordinate from the span-averaged field (Sec. 3.1, R11),
+    searching the columns x < xlim (default all)."""
     chi = _f64(chi)
     nz, ny, nx = chi.shape
-    return lib().orc_front_node(nx, ny, nz, _d(chi), thr)
+    return lib().orc_front_node_lim(nx, ny, nz, _d(chi), thr, nx if xlim is None else xlim)
+
+
+def front_xlim(nx: int, x0: int, periodic_x: bool) -> int:
+    """Columns searched for the front: nx, or (nx + x0) // 2 with periodic ends."""
+    return lib().orc_front_xlim(nx, x0, int(bool(periodic_x)))
 
 
 def diag(p: OracleParams, f, phi, x0: int, H: float, thr: float = 0.02) -> dict:

@@ -3,6 +3,7 @@
 // trajectory for it.  The objective is the time-integrated bottom friction
 // J = sum_n F_w(s_n) (Eq. 62-64); the step differentiated is Eq. 11, 17,
 // 19-30 and 32-35 as computed by collide_bgk.
+#include "lbm_aa2.cuh"
 #include "lbm_bgk_collide.cuh"
 #include "lbm_internal.h"
 
@@ -41,7 +42,33 @@ __global__ void __launch_bounds__(128, LBM_STEP_MINB) bgk_push_kernel(KParams kp
     }
 }
 
+// The same push for two x-adjacent nodes per thread (nx even): reading the
+// own slots is the AA even-step gather and pushing to slot i of node x + c_i
+// (own slot opp(i) across a wall) is the AA odd-step scatter, both with
+// paired accesses (lbm_aa2.cuh), here between two arrays.
+__global__ void __launch_bounds__(128, LBM_STEP2_MINB) bgk_push2_kernel(KParams kp,
+                                                                      const float* __restrict__ src,
+                                                                      float* __restrict__ dst) {
+    const int x = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const Stencil2 st = make_stencil2(kp, x, blockIdx.y, blockIdx.z);
+    const unsigned N = kp.N;
+    float f0[19], f1[19], p0[7], p1[7];
+    gather2<19, false>(kp, src, st, f0, f1);
+    gather2<7, false>(kp, src + (size_t)19 * N, st, p0, p1);
+    if (!(kp.flags & LBM_FLAG_NO_COLLIDE)) {
+        collide_bgk(kp, f0, p0);
+        collide_bgk(kp, f1, p1);
+    }
+    scatter2<19, true>(kp, dst, st, f0, f1);
+    scatter2<7, true>(kp, dst + (size_t)19 * N, st, p0, p1);
+}
+
 cudaError_t launch_push_step(const KParams& kp, const float* src, float* dst, cudaStream_t st) {
+    if (kp.nx % 2 == 0) {
+        dim3 block(128), grid((kp.nx / 2 + 127) / 128, kp.ny, kp.nz);
+        bgk_push2_kernel<<<grid, block, 0, st>>>(kp, src, dst);
+        return cudaGetLastError();
+    }
     dim3 block(128), grid((kp.nx + 127) / 128, kp.ny, kp.nz);
     bgk_push_kernel<<<grid, block, 0, st>>>(kp, src, dst);
     return cudaGetLastError();
@@ -101,15 +128,18 @@ __global__ void __launch_bounds__(128) bgk_adjoint_kernel(KParams kp, const floa
         for (int k = 0; k < 7; ++k) chit += p[k];
         const float chi = 1.0f + chit;
         const float Fx = kp.gx * chi, Fy = kp.gy * chi, Fz = kp.gz * chi;
-        float drho = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
+        float drho = f[0], jx = 0.0f, jy = 0.0f, jz = 0.0f;
         float mxx = 0.0f, myy = 0.0f, mzz = 0.0f, mxy = 0.0f, mxz = 0.0f, myz = 0.0f;
 #pragma unroll
-        for (int i = 0; i < 19; ++i) {
-            const float v = f[i];
-            drho += v;
-            jx += cx27(i) * v; jy += cy27(i) * v; jz += cz27(i) * v;
-            mxx += cx27(i) * cx27(i) * v; myy += cy27(i) * cy27(i) * v; mzz += cz27(i) * cz27(i) * v;
-            mxy += cx27(i) * cy27(i) * v; mxz += cx27(i) * cz27(i) * v; myz += cy27(i) * cz27(i) * v;
+        for (int i = 1; i < 19; i += 2) {
+            const float sm = f[i] + f[i + 1], dm = f[i] - f[i + 1];
+            drho += sm;
+            if (cx27(i)) { jx += cx27(i) * dm; mxx += sm; }
+            if (cy27(i)) { jy += cy27(i) * dm; myy += sm; }
+            if (cz27(i)) { jz += cz27(i) * dm; mzz += sm; }
+            if (cx27(i) * cy27(i)) mxy += cx27(i) * cy27(i) * sm;
+            if (cx27(i) * cz27(i)) mxz += cx27(i) * cz27(i) * sm;
+            if (cy27(i) * cz27(i)) myz += cy27(i) * cz27(i) * sm;
         }
         const float rho = 1.0f + drho, irho = 1.0f / rho;
         const float ux = (jx + 0.5f * Fx) * irho, uy = (jy + 0.5f * Fy) * irho,
@@ -148,33 +178,58 @@ __global__ void __launch_bounds__(128) bgk_adjoint_kernel(KParams kp, const floa
         }
         // tau_Phi = taup0 + kT dtau
         float gtau = -gomp * omp * omp * kp.kT;
-        // fluid: f* = (1 - om) f + om feq + (1 - om/2) B
+        // fluid: f* = (1 - om) f + om feq + (1 - om/2) B, with
+        //   feq_i = w (drho + rho (3 cu + 4.5 cu^2 - 1.5 u.u)),
+        //   B_i = w (3 cF - 3 u.F + 9 cu cF),  cu = c_i.u, cF = c_i.F.
+        // Opposite directions (i, i + 1) share w and flip c, so with the sums
+        // ms = mu_i + mu_{i+1} and differences md = mu_i - mu_{i+1} each pair
+        // contributes (even parts E = 4.5 cu^2 - 1.5 u.u, Be = 9 cu cF - 3 u.F;
+        // odd parts O = 3 cu, Bo = 3 cF):
+        //   d/d om:  w (ms (drho + rho E) + md rho O) - (ms fs + md fd)/2
+        //            - w (ms Be + md Bo)/2
+        //   d/d rho: om w (ms (1 + E) + md O)
+        //   d/d u:   om w rho V + guo w ms (9 cF c - 3 F),  V = 3 md c + ms (9 cu c - 3 u)
+        //   d/d F:   guo w V
         float gom = 0.0f;
+        {
+            // rest population (c = 0)
+            const float w = w19(0), m0 = mu[0];
+            const float E = -1.5f * usq;
+            gf[0] = (1.0f - om) * m0;
+            gom += m0 * (w * (drho + rho * E) - f[0]) + 0.5f * m0 * w * 3.0f * uF;
+            grho += om * w * m0 * (1.0f + E);
+            const float a = -3.0f * w * m0 * (om * rho);
+            gux += a * ux; guy += a * uy; guz += a * uz;
+            const float b = -3.0f * w * m0 * guo;
+            gFx += b * ux; gFy += b * uy; gFz += b * uz;
+            gux += b * Fx; guy += b * Fy; guz += b * Fz;
+        }
 #pragma unroll
-        for (int i = 0; i < 19; ++i) {
+        for (int i = 1; i < 19; i += 2) {
             const float cxi = cx27(i), cyi = cy27(i), czi = cz27(i);
             const float cu = cxi * ux + cyi * uy + czi * uz;
             const float cF = cxi * Fx + cyi * Fy + czi * Fz;
             const float w = w19(i);
-            const float pol = 3.0f * cu + 4.5f * cu * cu - 1.5f * usq;
-            const float feq = w * (drho + rho * pol);
-            const float B = w * (3.0f * cF - 3.0f * uF + 9.0f * cu * cF);
+            const float ms = mu[i] + mu[i + 1], md = mu[i] - mu[i + 1];
+            const float fs = f[i] + f[i + 1], fd = f[i] - f[i + 1];
+            const float E = 4.5f * cu * cu - 1.5f * usq, O = 3.0f * cu;
+            const float Be = 9.0f * cu * cF - 3.0f * uF, Bo = 3.0f * cF;
             gf[i] = (1.0f - om) * mu[i];
-            gom += mu[i] * (feq - f[i]) - 0.5f * mu[i] * B;
-            const float gfeq = om * mu[i];
-            const float gB = guo * mu[i];
-            grho += gfeq * w * (1.0f + pol);
-            const float a = gfeq * w * rho;   // d feq / du = w rho (3 c + 9 cu c - 3 u)
-            gux += a * (3.0f * cxi + 9.0f * cu * cxi - 3.0f * ux);
-            guy += a * (3.0f * cyi + 9.0f * cu * cyi - 3.0f * uy);
-            guz += a * (3.0f * czi + 9.0f * cu * czi - 3.0f * uz);
-            const float b = gB * w;           // dB/dF = w (3 c - 3 u + 9 cu c), dB/du = w (-3 F + 9 cF c)
-            gFx += b * (3.0f * cxi - 3.0f * ux + 9.0f * cu * cxi);
-            gFy += b * (3.0f * cyi - 3.0f * uy + 9.0f * cu * cyi);
-            gFz += b * (3.0f * czi - 3.0f * uz + 9.0f * cu * czi);
-            gux += b * (-3.0f * Fx + 9.0f * cF * cxi);
-            guy += b * (-3.0f * Fy + 9.0f * cF * cyi);
-            guz += b * (-3.0f * Fz + 9.0f * cF * czi);
+            gf[i + 1] = (1.0f - om) * mu[i + 1];
+            gom += w * (ms * (drho + rho * E) + md * rho * O) - 0.5f * (ms * fs + md * fd) -
+                   0.5f * w * (ms * Be + md * Bo);
+            grho += om * w * (ms * (1.0f + E) + md * O);
+            const float m3 = 3.0f * md, m9 = 9.0f * ms * cu;
+            const float Vx = m3 * cxi + m9 * cxi - 3.0f * ms * ux;
+            const float Vy = m3 * cyi + m9 * cyi - 3.0f * ms * uy;
+            const float Vz = m3 * czi + m9 * czi - 3.0f * ms * uz;
+            const float a = om * w * rho, b = guo * w;
+            gux += a * Vx; guy += a * Vy; guz += a * Vz;
+            gFx += b * Vx; gFy += b * Vy; gFz += b * Vz;
+            const float bm = b * ms, c9 = 9.0f * cF;
+            gux += bm * (c9 * cxi - 3.0f * Fx);
+            guy += bm * (c9 * cyi - 3.0f * Fy);
+            guz += bm * (c9 * czi - 3.0f * Fz);
         }
         gtau += -gom * om * om;
         // dtau = (s - tau0)/2, s = sqrt(tau0^2 + X): d dtau / dX = 1 / (4 s)
@@ -207,12 +262,16 @@ __global__ void __launch_bounds__(128) bgk_adjoint_kernel(KParams kp, const floa
         gFx += 0.5f * gux * irho; gFy += 0.5f * guy * irho; gFz += 0.5f * guz * irho;
         grho += -(gux * ux + guy * uy + guz * uz) * irho;
         // j = sum c f, rho = 1 + sum f, M = sum c c f
+        // (even part grho + c c : gP, odd part c . gj for each opposite pair)
+        gf[0] += grho;
 #pragma unroll
-        for (int i = 0; i < 19; ++i) {
+        for (int i = 1; i < 19; i += 2) {
             const float cxi = cx27(i), cyi = cy27(i), czi = cz27(i);
-            gf[i] += grho + cxi * gjx + cyi * gjy + czi * gjz + gpxx * cxi * cxi +
-                     gpyy * cyi * cyi + gpzz * czi * czi + gpxy * cxi * cyi + gpxz * cxi * czi +
-                     gpyz * cyi * czi;
+            const float te = grho + gpxx * cxi * cxi + gpyy * cyi * cyi + gpzz * czi * czi +
+                             gpxy * cxi * cyi + gpxz * cxi * czi + gpyz * cyi * czi;
+            const float to = cxi * gjx + cyi * gjy + czi * gjz;
+            gf[i] += te + to;
+            gf[i + 1] += te - to;
         }
         // F = g' chi e^g, chi = 1 + sum (Phi - w)
         gchi += gFx * kp.gx + gFy * kp.gy + gFz * kp.gz;

@@ -247,7 +247,7 @@ constexpr int FIN_T = 512;
 __global__ void __launch_bounds__(FIN_T) diag_finalize_kernel(
     int nx, double nodes, unsigned nblocks, const double* __restrict__ part,
     const float* __restrict__ fwpart, unsigned* __restrict__ colmax, DevDiag* __restrict__ out,
-    double thr, int x0, double H) {
+    double thr, int x0, double H, int xlim) {
     __shared__ double sa[FIN_T], sb[FIN_T];
     __shared__ float ss[FIN_T], sc[FIN_T];
     __shared__ int sx[FIN_T];
@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(FIN_T) diag_finalize_kernel(
         pair_add(s, c, fwpart[2 * i], fwpart[2 * i + 1]);
     }
     int xf = -1;
-    for (int x = t; x < nx; x += FIN_T)
+    for (int x = t; x < xlim; x += FIN_T)
         if ((double)fkey_inv(colmax[x]) >= thr) xf = x;
     sa[t] = a; sb[t] = b; ss[t] = s; sc[t] = c; sx[t] = xf;
     __syncthreads();
@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(FIN_T) diag_finalize_kernel(
         const int x = sx[0];
         double xn;
         if (x < 0) xn = -1.0;
-        else if (x == nx - 1) xn = (double)x;
+        else if (x == xlim - 1) xn = (double)x;
         else {
             const double m0 = fkey_inv(colmax[x]), m1 = fkey_inv(colmax[x + 1]);
             xn = x + (m0 - thr) / (m0 - m1);
@@ -339,8 +339,9 @@ __global__ void adjoint_chi0_kernel(unsigned N, int Q, const float* __restrict__
 // sum_k (Phi_k - w_k).  Hence d value / d(Phi_k - w_k) is g0 / ny on the
 // column (x, ., z0) and g1 / ny on (x + 1, ., z1), zero elsewhere, with
 //   g0 = (thr - m1) / ((m0 - m1)^2 H),  g1 = (m0 - thr) / ((m0 - m1)^2 H).
-// When no column reaches thr, or the crossing column is the last one, the
-// front does not move with the state and the derivative is zero.
+// When no column reaches thr, or the crossing column is the last one searched
+// (front_xlim), the front does not move with the state and the derivative is
+// zero.
 __global__ void __launch_bounds__(DIAG_BX) front_columns_kernel(KParams kp, int Q, int NS,
                                                                 const float* __restrict__ s,
                                                                 float* __restrict__ chibar,
@@ -365,11 +366,12 @@ __global__ void __launch_bounds__(FIN_T) front_finalize_kernel(int nx, int nz,
                                                                unsigned* __restrict__ colmax,
                                                                FrontGrad* __restrict__ out,
                                                                double* __restrict__ value,
-                                                               double thr, int x0, double H) {
+                                                               double thr, int x0, double H,
+                                                               int xlim) {
     __shared__ int sx[FIN_T];
     const int t = threadIdx.x;
     int xf = -1;
-    for (int x = t; x < nx; x += FIN_T)
+    for (int x = t; x < xlim; x += FIN_T)
         if ((double)fkey_inv(colmax[x]) >= thr) xf = x;
     sx[t] = xf;
     __syncthreads();
@@ -383,7 +385,7 @@ __global__ void __launch_bounds__(FIN_T) front_finalize_kernel(int nx, int nz,
         g.x = x; g.z0 = 0; g.z1 = 0; g.valid = 0; g.g0 = 0.0; g.g1 = 0.0;
         double xn;
         if (x < 0) xn = -1.0;
-        else if (x == nx - 1) xn = (double)x;
+        else if (x == xlim - 1) xn = (double)x;
         else {
             const unsigned k0 = colmax[x], k1 = colmax[x + 1];
             const double m0 = fkey_inv(k0), m1 = fkey_inv(k1);
@@ -509,7 +511,8 @@ cudaError_t launch_diag(const KParams& kp, Kind k, bool odd, const Views& v, dou
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         diag_finalize_kernel<<<1, FIN_T, 0, st>>>(kp.nx, (double)kp.N, v.diag_blocks, v.part,
-                                                  v.fwpart, v.colmax, v.ddiag, threshold, x0, H);
+                                                  v.fwpart, v.colmax, v.ddiag, threshold, x0, H,
+                                                  front_xlim(kp.nx, x0, kp.flags));
         return cudaGetLastError();
     });
 }
@@ -535,7 +538,7 @@ cudaError_t launch_front_adjoint(const KParams& kp, int Q, int NS, const Views& 
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     front_finalize_kernel<<<1, FIN_T, 0, st>>>(kp.nx, kp.nz, v.chibar, v.colmax, v.fgrad, value,
-                                               threshold, x0, H);
+                                               threshold, x0, H, front_xlim(kp.nx, x0, kp.flags));
     e = cudaGetLastError();
     if (e != cudaSuccess || !lam) return e;
     e = cudaMemsetAsync(lam, 0, (size_t)(Q + NS) * kp.N * sizeof(float), st);

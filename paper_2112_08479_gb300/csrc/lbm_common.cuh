@@ -291,6 +291,17 @@ __device__ __forceinline__ void scatter(const KParams& kp, S* __restrict__ a, co
     }
 }
 
+// Columns searched for the front (Sec. 3.1 with reading R11): all of them
+// with walls at the x ends; with periodic ends (Fig. 4b: a periodic array of
+// currents) the half of the ring ahead of the lock, x < (nx + x0) / 2, so that
+// the current leaving the lock to the left and re-entering at x = nx - 1 is
+// not taken for the front.
+__host__ __device__ inline int front_xlim(int nx, int x0, int flags) {
+    if (!(flags & LBM_FLAG_PERIODIC_X)) return nx;
+    const int h = (nx + x0) / 2;
+    return h < 1 ? 1 : h;
+}
+
 // Legacy form used by the auxiliary kernels: neighbour of (x, y, z) displaced
 // by (dx, dy, dz), false beyond a wall.
 __device__ __forceinline__ bool neighbour(const KParams& kp, int x, int y, int z, int dx, int dy,

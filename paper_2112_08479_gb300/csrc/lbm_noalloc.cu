@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(NA_BX) na_columns_kernel(KParams kp, const flo
 
 __global__ void __launch_bounds__(NA_FIN) na_finalize_kernel(int nx, double nodes, unsigned nblocks,
                                                              unsigned char* scratch, double thr,
-                                                             int x0, double H) {
+                                                             int x0, double H, int xlim) {
     const unsigned* keys = (const unsigned*)(scratch + NA_KEYS);
     const double* part = (const double*)(scratch + NA_PART);
     const float* fwpart = (const float*)(scratch + NA_FWPART);
@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(NA_FIN) na_finalize_kernel(int nx, double node
         na_pair_add(s, c, fwpart[2 * i], fwpart[2 * i + 1]);
     }
     int xf = -1;
-    for (int x = t; x < nx; x += NA_FIN)
+    for (int x = t; x < xlim; x += NA_FIN)
         if ((double)na_key_inv(keys[x]) >= thr) xf = x;
     sa[t] = a; sb[t] = b; ss[t] = s; sc[t] = c; sx[t] = xf;
     __syncthreads();
@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(NA_FIN) na_finalize_kernel(int nx, double node
         const int x = sx[0];
         double xn;
         if (x < 0) xn = -1.0;
-        else if (x == nx - 1) xn = (double)x;
+        else if (x == xlim - 1) xn = (double)x;
         else {
             const double m0 = na_key_inv(keys[x]), m1 = na_key_inv(keys[x + 1]);
             xn = x + (m0 - thr) / (m0 - m1);
@@ -258,7 +258,8 @@ lbm_status lbm_diag_static(const lbm_params* p, const float* state, int64_t step
         else na_columns_kernel<19, 7><<<grid, NA_BX, 0, st>>>(kp, state, s8);
     }
     na_finalize_kernel<<<1, NA_FIN, 0, st>>>(p->nx, (double)kp.N, (unsigned)(nbx * p->nz), s8,
-                                             p->front_threshold, p->x0, (double)p->H);
+                                             p->front_threshold, p->x0, (double)p->H,
+                                             front_xlim(p->nx, p->x0, p->flags));
     if ((e = cudaGetLastError()) != cudaSuccess) return LBM_ERR_CUDA;
     NaRecord rec;
     e = cudaMemcpyAsync(&rec, s8 + NA_REC, sizeof rec, cudaMemcpyDeviceToHost, st);

@@ -263,15 +263,28 @@ class Params:
         return (self.nz, self.ny, self.nx)
 
 
+GEOMETRIES = ("walls", "periodic")
+
+
 def lock_exchange(nx: int, ny: int, nz: int, *, H: int, x0: int, u_b: float, Re: float,
                   Sc: float = 1.0, model: str = "bgk", storage: str = "fp32",
-                  cs_smag: float = 0.17, scalar: str = "q7", **kw) -> Params:
+                  cs_smag: float = 0.17, scalar: str = "q7", geometry: str = "walls",
+                  sc_t: float | str = 1.0, **kw) -> Params:
     """Lattice-unit parameters of the lock-exchange box (Sec. 2.5): g' = u_b^2 / H
-    (u_b = sqrt(g' H)), nu = u_b H / Re_b, D = nu / Sc (Eq. 12-14)."""
+    (u_b = sqrt(g' H)), nu = u_b H / Re_b, D = nu / Sc (Eq. 12-14).
+
+    geometry: "walls" (Fig. 4a, Cases 2, 4, 6, 8: walls at the x ends) or
+    "periodic" (Fig. 4b, Cases 1, 3, 5, 7: periodic ends; the span is periodic
+    in both).  sc_t: turbulent Schmidt number of the BGK model's eddy
+    diffusivity (Eq. 35), or "paper" for the literal Sc_T = C_s^2."""
+    if geometry not in GEOMETRIES:
+        raise ValueError(f"geometry must be one of {GEOMETRIES}")
     nu = u_b * H / Re
+    flags = kw.pop("flags", 0) | (LBM_FLAG_PERIODIC_X if geometry == "periodic" else 0)
+    sct = cs_smag * cs_smag if sc_t == "paper" else float(sc_t)
     return Params(nx=nx, ny=ny, nz=nz, model=MODELS[model], storage=STORAGES[storage],
                   nu=nu, D=nu / Sc, cs_smag=cs_smag, gprime=u_b * u_b / H, x0=x0, H=H,
-                  scalar=SCALARS[scalar], **kw)
+                  scalar=SCALARS[scalar], flags=flags, sc_t=sct, **kw)
 
 
 # --- torch-backed context -----------------------------------------------------------

@@ -84,6 +84,11 @@ def main(argv=None):
     ap.add_argument("--scalar", default="q7", choices=sorted(lbm.SCALARS),
                     help="scalar lattice: q7 (both models), q6 (BGK, Eq. 29-31), "
                          "q27 (cumulant, factorized central moments, Eq. 37-51)")
+    ap.add_argument("--geometry", default="walls", choices=lbm.GEOMETRIES,
+                    help="walls: Fig. 4a (Cases 2, 4, 6, 8); periodic: Fig. 4b, periodic "
+                         "ends (Cases 1, 3, 5, 7)")
+    ap.add_argument("--sc-t", default="1.0",
+                    help="turbulent Schmidt number (Eq. 35) or 'paper' for Sc_T = C_s^2")
     ap.add_argument("--cs", type=float, default=0.17)
     ap.add_argument("--seed", type=int, default=2112)
     ap.add_argument("--steps", type=int, default=None)
@@ -94,7 +99,8 @@ def main(argv=None):
     a = ap.parse_args(argv)
     p = lbm.lock_exchange(a.nx, a.ny, a.nz, H=a.H, x0=a.x0, u_b=a.ub, Re=a.Re, Sc=a.Sc,
                           model=a.model, storage=a.storage, cs_smag=a.cs, seed=a.seed,
-                          scalar=a.scalar)
+                          scalar=a.scalar, geometry=a.geometry,
+                          sc_t=a.sc_t if a.sc_t == "paper" else float(a.sc_t))
     steps = a.steps if a.steps is not None else int(round(a.t_end * a.H / a.ub))
     recs, wall = run(p, a.ub, steps, a.every, a.out)
     fr = froude([r["t"] for r in recs], [r["front"] for r in recs], *a.fr_window)

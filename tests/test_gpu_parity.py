@@ -253,3 +253,30 @@ def test_scalar_mass_conserved_over_long_run(model):
     assert abs(d1["scalar_mass"] - d0["scalar_mass"]) < 2 * u * 1.5 * p.N * steps
     assert abs(d1["mass_delta"] - d0["mass_delta"]) < 2 * u * 0.2 * p.N * steps
     assert d1["flags"] == 0
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+def test_front_window_matches_oracle(periodic):
+    """Front search window (all columns with x walls, x < (nx + x0)/2 with
+    periodic ends) in lbm_diag and lbm_front_adjoint, on a state holding the
+    right-going current and a wrapped left-going one."""
+    nx, ny, nz, x0 = 40, 3, 4, 8
+    p = lbm.Params(nx, ny, nz, x0=x0, H=8, flags=lbm.LBM_FLAG_PERIODIC_X if periodic else 0)
+    chi = np.zeros((nz, ny, nx))
+    chi[:, :, :14] = 1.0
+    chi[:, :, 14] = 0.3 + 0.01 * np.arange(nz)[:, None]
+    chi[0, :, 33:] = 0.6
+    w7 = O.velocities_q7()[1]
+    s = np.zeros((26, p.N), dtype=np.float32)
+    s[19:] = (w7[:, None] * (chi.reshape(1, -1) - 1.0)).astype(np.float32)
+    lat = _lat(p)
+    lat.set_state(_to_dev(s))
+    chi_o = (1.0 + s[19:].astype(np.float64).sum(0)).reshape(nz, ny, nx)
+    want = O.front_node(chi_o, 0.02, O.front_xlim(nx, x0, periodic))
+    assert lat.diag()["front_node"] == pytest.approx(want, abs=1e-5)
+    val = torch.zeros(1, dtype=torch.float64, device="cuda")
+    lam = torch.empty(26, p.N, device="cuda")
+    lat.front_adjoint(_to_dev(s), lam, val)
+    assert val.item() == pytest.approx((want + 0.5 - x0) / 8, abs=1e-6)
+    nnz = torch.count_nonzero(lam).item()
+    assert nnz == (0 if want == nx - 1 else 2 * ny * 7)

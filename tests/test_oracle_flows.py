@@ -301,3 +301,30 @@ def test_front_on_synthetic_fields():
     assert O.front_node(np.zeros((nz, ny, nx)), 0.02) == -1.0
     full = np.ones((nz, ny, nx))
     assert O.front_node(full, 0.02) == nx - 1
+
+
+def test_front_window_with_periodic_ends():
+    """Periodic ends (Fig. 4b): the current leaving the lock [0, x0) to the
+    left re-enters at x = nx - 1; the front is searched in x < (nx + x0) / 2,
+    the half of the ring ahead of the lock (reading of Sec. 3.1 for Cases 1,
+    3, 5, 7)."""
+    nx, ny, nz, x0 = 40, 3, 4, 8
+    chi = np.zeros((nz, ny, nx))
+    chi[:, :, :14] = 1.0                    # lock and the right-going current
+    chi[0, :, 33:] = 0.6                    # the left-going current, wrapped
+    xlim = O.front_xlim(nx, x0, True)
+    assert xlim == (nx + x0) // 2 == 24 and O.front_xlim(nx, x0, False) == nx
+    assert O.front_node(chi, 0.02) == nx - 1          # walls: the whole box
+    assert O.front_node(chi, 0.02, xlim) == pytest.approx(13 + 0.98, abs=1e-14)
+    # through the diagnostics: the window follows the periodic_x flag
+    for periodic, want in ((False, nx - 1), (True, 13 + 0.98)):
+        p = O.OracleParams(nx, ny, nz, model=0, periodic_x=periodic)
+        f = np.broadcast_to(np.asarray(O.velocities(0)[1]), (nz, ny, nx, 19)).copy()
+        phi = chi[..., None] * np.asarray(O.velocities_q7()[1])
+        d = O.diag(p, f, phi, x0, 8.0)
+        assert d["front_node"] == pytest.approx(want, abs=1e-12)
+    # a front on the last searched column is not interpolated
+    edge = np.zeros((nz, ny, nx))
+    edge[:, :, :xlim] = 1.0
+    edge[:, :, xlim:] = 0.5
+    assert O.front_node(edge, 0.02, xlim) == xlim - 1

@@ -197,16 +197,18 @@ LBM_API lbm_status lbm_get_state(lbm_ctx* ctx, float* dst);
  * Asynchronous. */
 LBM_API lbm_status lbm_set_state(lbm_ctx* ctx, const float* src, int64_t step);
 
-/* One reverse step of the discrete adjoint of the BGK-Smagorinsky + scalar +
- * Boussinesq step (BGK model, FP32 arithmetic):
+/* One reverse step of the discrete adjoint of the time step with the D3Q7
+ * scalar and the Boussinesq force, for either fluid (BGK-Smagorinsky,
+ * Eq. 17-35; cumulant, Eq. 54-58 and 28-30), in FP32 arithmetic:
  *   lam_n = (dT/ds_n)^T lam_next + w_fw * dF_w(s_n)/ds_n,
- *   *dJdCs_dev += lam_next . dT/dC_s (s_n),
+ *   *dJdCs_dev += lam_next . dT/dC_s (s_n)   (BGK; the cumulant model has
+ *                                            no C_s and adds nothing),
  * where T is the time step of lbm_step, s_n = state_n (canonical layout,
  * device, (Q + NS) * N floats) is the state it was applied to, and lam_next,
  * lam_n are adjoint states in the canonical layout (device, (Q + NS) * N
  * floats; lam_next == NULL means zero).  lam_n must not alias lam_next or
  * state_n.  dJdCs_dev: one device double, accumulated.  Asynchronous.
- * LBM_ERR_STATE for the cumulant model. */
+ * LBM_ERR_STATE for the D3Q6 and D3Q27 scalars. */
 LBM_API lbm_status lbm_adjoint_step(lbm_ctx* ctx, const float* state_n, const float* lam_next,
                             float* lam_n, double* dJdCs_dev, double w_fw);
 
@@ -219,7 +221,8 @@ LBM_API lbm_status lbm_adjoint_step(lbm_ctx* ctx, const float* state_n, const fl
 LBM_API lbm_status lbm_objective_forward(lbm_ctx* ctx, int32_t nsteps, int32_t K, float* ckpt,
                                          double* J_dev);
 
-/* One reverse segment of the adjoint of J (BGK model, FP32 storage):
+/* One reverse segment of the adjoint of J (either fluid with the D3Q7
+ * scalar, FP32 storage):
  * from the checkpoint ckpt = s_{n0}, recomputes s_{n0+1} .. s_{n0+k-1} into
  * seg + j (Q + NS) N (j = 1 .. k-1; seg holds k states, slot 0 unused) with
  * an out-of-place step of the same arithmetic, then applies k adjoint steps
@@ -228,7 +231,7 @@ LBM_API lbm_status lbm_objective_forward(lbm_ctx* ctx, int32_t nsteps, int32_t K
  * time-integrated friction, 0 for an objective of the final state, e.g. the
  * front of lbm_front_adjoint).  tmp: a second adjoint buffer, distinct from
  * lam.  *dJdCs_dev accumulates the C_s derivative.  Asynchronous.
- * LBM_ERR_STATE for the cumulant model or 16-bit storage. */
+ * LBM_ERR_STATE for 16-bit storage or the D3Q6 and D3Q27 scalars. */
 LBM_API lbm_status lbm_adjoint_segment(lbm_ctx* ctx, const float* ckpt, int64_t n0, int32_t k,
                                        float* seg, float* lam, float* tmp, double* dJdCs_dev,
                                        double w_fw);

@@ -33,12 +33,15 @@ DT = torch.float64
 
 
 class BGKStep:
-    """One time step on a (nz, ny, nx) box with x and z walls, periodic y."""
+    """One time step of the BGK-Smagorinsky D3Q19 fluid with the D3Q7 scalar
+    on a (nz, ny, nx) box with x and z walls (or periodic), periodic y."""
+
+    MODEL = 0
 
     def __init__(self, p: O.OracleParams):
-        assert p.model == 0
+        assert p.model == self.MODEL and p.scalar == 0
         self.p = p
-        c, w = O.velocities(0)
+        c, w = O.velocities(p.model)
         c7, w7 = O.velocities_q7()
         self.c = torch.tensor(c, dtype=DT)
         self.w = torch.tensor(w, dtype=DT)
@@ -125,17 +128,119 @@ class BGKStep:
         return (xn + 0.5 - x0) / H
 
 
+class CumulantStep(BGKStep):
+    """One time step of the D3Q27 cumulant fluid (Eq. 54-58, reading R7) with
+    the D3Q7 scalar (molecular D only, no eddy diffusivity).
+
+    The cumulants are the coefficients of ln G, G(Xi) = sum_i f_i exp(Xi.c_i)
+    (Eq. 54), computed in the ring of Taylor coefficients truncated at degree
+    2 per axis (exact for those coefficients; the series of ln(1 + H) and
+    exp(K) stop at degree 6).  Relaxation as Eq. 55-58: rho kept, first order
+    to (j + F)/rho, off-diagonal second order and the deviators with omega1 =
+    1/(3 nu + 1/2), the trace with omega_bulk to 1, orders >= 3 with
+    omega_high to 0.  Populations from the moments by the per-axis inverse of
+    the Vandermonde map {f(-1), f(0), f(1)} -> {m0, m1, m2}."""
+
+    MODEL = 1
+
+    def __init__(self, p: O.OracleParams):
+        super().__init__(p)
+        idx = [(a, b, c) for a in range(3) for b in range(3) for c in range(3)]
+        i1, i2, o = [], [], []
+        for n1, (a1, b1, c1) in enumerate(idx):
+            for n2, (a2, b2, c2) in enumerate(idx):
+                if a1 + a2 < 3 and b1 + b2 < 3 and c1 + c2 < 3:
+                    i1.append(n1)
+                    i2.append(n2)
+                    o.append(idx.index((a1 + a2, b1 + b2, c1 + c2)))
+        self.i1, self.i2, self.o = (torch.tensor(v, dtype=torch.long) for v in (i1, i2, o))
+        fact = [1.0, 1.0, 2.0]
+        self.fact = torch.tensor([fact[a] * fact[b] * fact[c] for a, b, c in idx], dtype=DT)
+        c = self.c.numpy()
+        self.mom = torch.tensor([[c[i][0] ** a * c[i][1] ** b * c[i][2] ** cc for i in range(27)]
+                                 for a, b, cc in idx], dtype=DT)          # m = mom @ f
+
+        def coef(cv, n):
+            if cv == 0:
+                return {0: 1.0, 1: 0.0, 2: -1.0}[n]
+            return {0: 0.0, 1: 0.5 * cv, 2: 0.5}[n]
+        self.inv = torch.tensor([[coef(c[i][0], a) * coef(c[i][1], b) * coef(c[i][2], cc)
+                                  for a, b, cc in idx] for i in range(27)], dtype=DT)
+        self.n_of = [a + b + cc for a, b, cc in idx]
+        self.pos = {t: n for n, t in enumerate(idx)}
+
+    def _mul(self, A, B):
+        out = torch.zeros_like(A)
+        return out.index_add(-1, self.o, A[..., self.i1] * B[..., self.i2])
+
+    def _log1p(self, H):
+        P, S = H, H
+        for k in range(2, 7):
+            P = self._mul(P, H)
+            S = S + ((1.0 if k % 2 else -1.0) / k) * P
+        return S
+
+    def _exp(self, K):
+        S = torch.zeros_like(K)
+        S = S.index_fill(-1, torch.tensor([0]), 1.0)
+        P, fk = K, 1.0
+        for k in range(1, 7):
+            if k > 1:
+                P = self._mul(P, K)
+            fk *= k
+            S = S + P / fk
+        return S
+
+    def collide(self, f, phi, cs):
+        p = self.p
+        rho, u, chi, F = self.macros(f, phi)
+        m = f @ self.mom.T
+        g = m / self.fact
+        H = g / rho[..., None]
+        H = H * (torch.arange(27) != 0).to(DT)              # G / rho = 1 + H
+        C = self._log1p(H) * self.fact                       # C_abc, C_000 replaced below
+        om1 = 1.0 / (3.0 * p.nu + 0.5)
+        om2, omh = p.omega_bulk, p.omega_high
+        P = self.pos
+        cxx, cyy, czz = C[..., P[2, 0, 0]], C[..., P[0, 2, 0]], C[..., P[0, 0, 2]]
+        d1 = (1 - om1) * (cxx - cyy)
+        d2 = (1 - om1) * (cxx - czz)
+        tr = (1 - om2) * (cxx + cyy + czz) + om2
+        nxx = (tr + d1 + d2) / 3
+        new = {(2, 0, 0): nxx, (0, 2, 0): nxx - d1, (0, 0, 2): nxx - d2,
+               (1, 1, 0): (1 - om1) * C[..., P[1, 1, 0]], (1, 0, 1): (1 - om1) * C[..., P[1, 0, 1]],
+               (0, 1, 1): (1 - om1) * C[..., P[0, 1, 1]],
+               (1, 0, 0): C[..., P[1, 0, 0]] + F[..., 0] / rho,
+               (0, 1, 0): C[..., P[0, 1, 0]] + F[..., 1] / rho,
+               (0, 0, 1): C[..., P[0, 0, 1]] + F[..., 2] / rho,
+               (0, 0, 0): torch.zeros_like(rho)}
+        cols = []
+        for n, t in enumerate(P):
+            cols.append(new[t] if t in new else (1 - omh) * C[..., n])
+        K = torch.stack(cols, -1) / self.fact
+        ms = rho[..., None] * self._exp(K) * self.fact       # exp(C_000) = rho
+        fo = ms @ self.inv.T
+        taup = 0.5 + 4 * p.D
+        phieq = self.w7 * chi[..., None] * (1 + 4 * (u @ self.c7.T))
+        po = phi - (phi - phieq) / taup
+        return fo, po
+
+
+def make_step(p: O.OracleParams):
+    return CumulantStep(p) if p.model == 1 else BGKStep(p)
+
+
 def initial_state(step: BGKStep, chi0):
     p = step.p
     chi0 = torch.as_tensor(np.asarray(chi0).reshape(p.nz, p.ny, p.nx), dtype=DT)
-    f = step.w.expand(p.nz, p.ny, p.nx, 19).clone()
+    f = step.w.expand(p.nz, p.ny, p.nx, len(step.w)).clone()
     phi = step.w7 * chi0[..., None]
     return f, phi
 
 
 def objective(p: O.OracleParams, chi0, cs: float, nsteps: int) -> float:
     """J = sum_{n=1..N} F_w(s_n) with the torch restatement (FP64)."""
-    st = BGKStep(p)
+    st = make_step(p)
     f, phi = initial_state(st, chi0)
     J = 0.0
     cs_t = torch.tensor(cs, dtype=DT)
@@ -149,8 +254,10 @@ def objective(p: O.OracleParams, chi0, cs: float, nsteps: int) -> float:
 def gradient(p: O.OracleParams, chi0, cs: float, nsteps: int, objective: str = "friction",
              x0: int = 0, H: float = 1.0, thr: float = 0.02):
     """Returns (J, dJ/dchi0 with the shape of chi0, dJ/dC_s) in FP64 for the
-    objective "friction" or "front" (the latter with x0, H, thr)."""
-    st = BGKStep(p)
+    objective "friction" or "front" (the latter with x0, H, thr).  BGK or
+    cumulant fluid (p.model) with the D3Q7 scalar; for the cumulant model
+    dJ/dC_s is 0 (no Smagorinsky closure)."""
+    st = make_step(p)
     f, phi = initial_state(st, chi0)
     cs_t = torch.tensor(cs, dtype=DT)
     traj = [(f, phi)]
@@ -182,7 +289,7 @@ def gradient(p: O.OracleParams, chi0, cs: float, nsteps: int, objective: str = "
         inner = (f1 * lf).sum() + (p1 * lp).sum()
         if n >= 1 and objective == "friction":
             inner = inner + st.friction(fn, pn)
-        lf, lp, gc = torch.autograd.grad(inner, (fn, pn, c))
-        gcs += float(gc)
+        lf, lp, gc = torch.autograd.grad(inner, (fn, pn, c), allow_unused=True)
+        gcs += 0.0 if gc is None else float(gc)     # the cumulant step does not use C_s
     gchi = (lp * st.w7).sum(-1)        # Phi_k = w_k chi0 at t = 0
     return J, gchi.numpy(), gcs

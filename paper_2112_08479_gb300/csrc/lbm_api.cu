@@ -319,19 +319,38 @@ lbm_status lbm_set_state(lbm_ctx* c, const float* src, int64_t step) {
     return LBM_OK;
 }
 
+namespace {
+// One reverse step of the model's adjoint (BGK: with the C_s term).
+cudaError_t adjoint_step_any(lbm_ctx* c, const float* state, const float* lam_next, float* lam,
+                             double* dcs, float wfw) {
+    if (c->p.model == LBM_CUMULANT_Q27)
+        return launch_cumulant_adjoint_step(c->kp, state, lam_next, lam, wfw, c->stream);
+    const float dAdCs = (float)(36.0 * sqrt(2.0) * c->p.cs_smag);
+    return launch_adjoint_step(c->kp, state, lam_next, lam, dcs, wfw, dAdCs, c->stream);
+}
+
+cudaError_t push_step_any(lbm_ctx* c, const float* src, float* dst) {
+    if (c->p.model == LBM_CUMULANT_Q27) return launch_cumulant_push_step(c->kp, src, dst, c->stream);
+    return launch_push_step(c->kp, src, dst, c->stream);
+}
+
+lbm_status adjoint_model_check(lbm_ctx* c) {
+    if (c->p.scalar != LBM_SCALAR_Q7) {
+        snprintf(c->err, sizeof c->err, "the adjoint exists for the D3Q7 scalar");
+        return LBM_ERR_STATE;
+    }
+    return LBM_OK;
+}
+}  // namespace
+
 lbm_status lbm_adjoint_step(lbm_ctx* c, const float* state_n, const float* lam_next, float* lam_n,
                             double* dJdCs_dev, double w_fw) {
     if (!c) return arg_fail(nullptr, "ctx is NULL");
-    if (c->p.model != LBM_BGK_SMAG_Q19 || c->p.scalar != LBM_SCALAR_Q7) {
-        snprintf(c->err, sizeof c->err, "the adjoint exists for the BGK model with the D3Q7 scalar");
-        return LBM_ERR_STATE;
-    }
+    if (lbm_status s = adjoint_model_check(c); s != LBM_OK) return s;
     if (!state_n || !lam_n) return arg_fail(c, "state_n and lam_n must not be NULL");
     if (lam_n == lam_next || lam_n == state_n) return arg_fail(c, "lam_n must not alias its inputs");
     if (!isfinite(w_fw)) return arg_fail(c, "w_fw must be finite");
-    const float dAdCs = (float)(36.0 * sqrt(2.0) * c->p.cs_smag);
-    cudaError_t e = launch_adjoint_step(c->kp, state_n, lam_next, lam_n, dJdCs_dev, (float)w_fw,
-                                        dAdCs, c->stream);
+    cudaError_t e = adjoint_step_any(c, state_n, lam_next, lam_n, dJdCs_dev, (float)w_fw);
     if (e != cudaSuccess) return cuda_fail(c, e, "adjoint launch");
     return LBM_OK;
 }
@@ -363,10 +382,9 @@ lbm_status lbm_objective_forward(lbm_ctx* c, int32_t nsteps, int32_t K, float* c
 lbm_status lbm_adjoint_segment(lbm_ctx* c, const float* ckpt, int64_t n0, int32_t k, float* seg,
                                float* lam, float* tmp, double* dJdCs_dev, double w_fw) {
     if (!c) return arg_fail(nullptr, "ctx is NULL");
-    if (c->p.model != LBM_BGK_SMAG_Q19 || c->p.storage != LBM_FP32 ||
-        c->p.scalar != LBM_SCALAR_Q7) {
+    if (c->p.storage != LBM_FP32 || c->p.scalar != LBM_SCALAR_Q7) {
         snprintf(c->err, sizeof c->err,
-                 "the adjoint exists for the BGK model with the D3Q7 scalar and FP32 storage");
+                 "the adjoint sweep exists for the D3Q7 scalar and FP32 storage");
         return LBM_ERR_STATE;
     }
     if (k < 1 || n0 < 0) return arg_fail(c, "k must be >= 1 and n0 >= 0");
@@ -374,12 +392,11 @@ lbm_status lbm_adjoint_segment(lbm_ctx* c, const float* ckpt, int64_t n0, int32_
     if (lam == tmp) return arg_fail(c, "lam and tmp must differ");
     if (!isfinite(w_fw)) return arg_fail(c, "w_fw must be finite");
     const size_t S = (size_t)(q_of(&c->p) + ns_of(&c->p)) * c->kp.N;
-    const float dAdCs = (float)(36.0 * sqrt(2.0) * c->p.cs_smag);
     cudaError_t e = cudaSuccess;
     // recompute s_{n0+1} .. s_{n0+k-1} into seg[1 .. k-1]
     const float* prev = ckpt;
     for (int32_t j = 1; j < k && e == cudaSuccess; ++j) {
-        e = launch_push_step(c->kp, prev, seg + (size_t)j * S, c->stream);
+        e = push_step_any(c, prev, seg + (size_t)j * S);
         prev = seg + (size_t)j * S;
     }
     // lam_{n0+k} -> lam_{n0}
@@ -388,8 +405,7 @@ lbm_status lbm_adjoint_segment(lbm_ctx* c, const float* ckpt, int64_t n0, int32_
     for (int32_t j = k - 1; j >= 0 && e == cudaSuccess; --j) {
         const int64_t n = n0 + j;
         const float* st = j == 0 ? ckpt : seg + (size_t)j * S;
-        e = launch_adjoint_step(c->kp, st, cur, nxt, dJdCs_dev, n >= 1 ? (float)w_fw : 0.0f,
-                                dAdCs, c->stream);
+        e = adjoint_step_any(c, st, cur, nxt, dJdCs_dev, n >= 1 ? (float)w_fw : 0.0f);
         float* t = cur; cur = nxt; nxt = t;
     }
     if (e == cudaSuccess && cur != lam)
@@ -412,11 +428,8 @@ lbm_status lbm_front_adjoint(lbm_ctx* c, const float* state, float* lam, double*
 lbm_status lbm_adjoint_chi0(lbm_ctx* c, const float* lam0, float* grad_chi0) {
     if (!c) return arg_fail(nullptr, "ctx is NULL");
     if (!lam0 || !grad_chi0) return arg_fail(c, "lam0 and grad_chi0 must not be NULL");
-    if (c->p.model != LBM_BGK_SMAG_Q19 || c->p.scalar != LBM_SCALAR_Q7) {
-        snprintf(c->err, sizeof c->err, "the adjoint exists for the BGK model with the D3Q7 scalar");
-        return LBM_ERR_STATE;
-    }
-    cudaError_t e = launch_adjoint_chi0(c->kp, lam0, grad_chi0, c->stream);
+    if (lbm_status s = adjoint_model_check(c); s != LBM_OK) return s;
+    cudaError_t e = launch_adjoint_chi0(c->kp, q_of(&c->p), lam0, grad_chi0, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "adjoint_chi0 launch");
     return LBM_OK;
 }

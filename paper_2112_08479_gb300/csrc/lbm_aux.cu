@@ -547,8 +547,9 @@ cudaError_t launch_front_adjoint(const KParams& kp, int Q, int NS, const Views& 
     return cudaGetLastError();
 }
 
-cudaError_t launch_adjoint_chi0(const KParams& kp, const float* lam0, float* grad, cudaStream_t st) {
-    adjoint_chi0_kernel<<<(kp.N + 255) / 256, 256, 0, st>>>(kp.N, 19, lam0, grad);
+cudaError_t launch_adjoint_chi0(const KParams& kp, int Q, const float* lam0, float* grad,
+                                cudaStream_t st) {
+    adjoint_chi0_kernel<<<(kp.N + 255) / 256, 256, 0, st>>>(kp.N, Q, lam0, grad);
     return cudaGetLastError();
 }
 

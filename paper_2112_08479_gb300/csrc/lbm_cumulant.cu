@@ -2,243 +2,15 @@
 // fluid (Sec. 2.3.1 "VirtualFluids", Eq. 52-58) with the D3Q7 scalar and the
 // Boussinesq force.
 //
-// Cumulants C_abc are the derivatives of ln G, G(Xi) = sum_i f_i exp(Xi.c_i)
-// (Eq. 54).  The collision keeps rho (Eq. 56), moves the first-order
-// cumulants to u* = (j + F) / rho (Eq. 57 plus the body-force impulse),
-// relaxes the second-order ones with omega1 = 1/(3 nu + 1/2) (Eq. 58) on
-// the shear parts and omega_bulk on the trace (Eq. 55, C_eq = c_s^2 = 1/3
-// per axis), and relaxes every cumulant of order >= 3 with rate 1 to its
-// equilibrium 0.  Because all higher cumulants leave the collision as 0,
-// only the pre-collision moments of order <= 2 are needed, and the
-// post-collision distribution has the truncated moment generating function
-//   G* = rho exp(u*.Xi) exp(Xi^T Sigma* Xi / 2)   mod (Xi^3, Y^3, Z^3),
-// whose central moments are rho times the Gaussian moments of Sigma*
-// (Isserlis): kappa_220 = s_xx s_yy + 2 s_xy^2, kappa_211 = s_xx s_yz +
-// 2 s_xy s_xz, kappa_222 = s_xx s_yy s_zz + 2 (s_xx s_yz^2 + s_yy s_xz^2 +
-// s_zz s_xy^2) + 8 s_xy s_xz s_yz, odd orders 0.  The populations follow from
-// the per-axis inverse of the central-moment map in the frame u*, applied on
-// z, then y, then x.  Every quantity is carried as a deviation from the rest
-// state (rho = 1, u = 0, Sigma = I/3) so FP32 keeps its digits.
+// The collision (Eq. 54-58 with all rates of order >= 3 equal to 1, built
+// from the Gaussian central moments of the relaxed covariance) is
+// collide_cumulant in lbm_cumulant_collide.cuh.
 #include <type_traits>
 
+#include "lbm_cumulant_collide.cuh"
 #include "lbm_internal.h"
 
 namespace lbmgpu {
-
-// Per-axis inverse of the central-moment map, in deviation form.  A line
-// (k0, k1, k2) of central moments in the frame moving with v holds the rest
-// values s * (1, 0, 1/3) plus the deviations (d0, d1, d2); the populations at
-// c = -1, 0, +1 are the rest values s * (1/6, 2/3, 1/6) plus the returned
-// deviations:
-//   p(0)  = d0 - (s + d0) v^2 - 2 v d1 - d2
-//   p(+-) = ((v^2 +- v)(s + d0) + (2 v +- 1) d1 + d2) / 2
-__device__ __forceinline__ void axis_inverse(float s, float v, float d0, float d1, float d2,
-                                             float& pm, float& p0, float& pp) {
-    const float k0 = s + d0;
-    const float v2 = v * v;
-    p0 = d0 - k0 * v2 - 2.0f * v * d1 - d2;
-    const float a = v2 * k0 + 2.0f * v * d1 + d2;
-    const float b = v * k0 + d1;
-    pp = 0.5f * (a + b);
-    pm = 0.5f * (a - b);
-}
-
-// Index of the D3Q27 direction (cx, cy, cz) in the library order, looked up
-// by (cx + 1) * 9 + (cy + 1) * 3 + (cz + 1).
-__host__ __device__ constexpr int dir27(int x, int y, int z) {
-    constexpr int t[27] = {20, 8, 22, 12, 2, 14, 24, 10, 25, 16, 4, 18, 6, 0,
-                           5, 17, 3, 15, 26, 9, 23, 13, 1, 11, 21, 7, 19};
-    return t[(x + 1) * 9 + (y + 1) * 3 + (z + 1)];
-}
-
-// SL: scalar lattice, D3Q7 BGK or D3Q27 factorized central moments.
-template <int SL = 7>
-__device__ __forceinline__ void collide_cumulant(const KParams& kp, float (&f)[27],
-                                                 float (&p)[ScalarLat<SL>::NS]) {
-    static_assert(SL == 7 || SL == 27, "the cumulant model runs with the D3Q7 or D3Q27 scalar");
-    constexpr int NS = ScalarLat<SL>::NS;
-    float chit = 0.0f;  // chi - 1 (Phi is held as Phi - w)
-#pragma unroll
-    for (int k = 0; k < NS; ++k) chit += p[k];
-    const float chi = 1.0f + chit;
-    const float Fx = kp.gx * chi, Fy = kp.gy * chi, Fz = kp.gz * chi;
-
-    float drho = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
-    float mxx = 0.0f, myy = 0.0f, mzz = 0.0f, mxy = 0.0f, mxz = 0.0f, myz = 0.0f;
-#pragma unroll
-    for (int i = 0; i < 27; ++i) {
-        const float v = f[i];
-        drho += v;
-        if (cx27(i)) { jx += cx27(i) * v; mxx += v; }
-        if (cy27(i)) { jy += cy27(i) * v; myy += v; }
-        if (cz27(i)) { jz += cz27(i) * v; mzz += v; }
-        if (cx27(i) * cy27(i)) mxy += cx27(i) * cy27(i) * v;
-        if (cx27(i) * cz27(i)) mxz += cx27(i) * cz27(i) * v;
-        if (cy27(i) * cz27(i)) myz += cy27(i) * cz27(i) * v;
-    }
-    const float rho = 1.0f + drho;
-    const float irho = 1.0f / rho;
-    // pre-collision mean velocity and second-order cumulants (deviation of
-    // the diagonal from 1/3): C_aa - 1/3 = (M_aa - drho/3)/rho - v_a^2
-    const float vx = jx * irho, vy = jy * irho, vz = jz * irho;
-    const float d3 = drho * (1.0f / 3.0f);
-    const float cxx = (mxx - d3) * irho - vx * vx;
-    const float cyy = (myy - d3) * irho - vy * vy;
-    const float czz = (mzz - d3) * irho - vz * vz;
-    const float cxy = mxy * irho - vx * vy;
-    const float cxz = mxz * irho - vx * vz;
-    const float cyz = myz * irho - vy * vz;
-    // relaxation (Eq. 55): shear with omega1, trace with omega_bulk
-    const float r1 = 1.0f - kp.om1, r2 = 1.0f - kp.om2;
-    const float D1 = r1 * (cxx - cyy), D2 = r1 * (cxx - czz), T = r2 * (cxx + cyy + czz);
-    const float sxx = (T + D1 + D2) * (1.0f / 3.0f);
-    const float syy = sxx - D1, szz = sxx - D2;
-    const float sxy = r1 * cxy, sxz = r1 * cxz, syz = r1 * cyz;
-    // post-collision velocity (first-order cumulants + body-force impulse)
-    const float ux = (jx + Fx) * irho, uy = (jy + Fy) * irho, uz = (jz + Fz) * irho;
-
-    // central-moment deviations K[a][b][c] (rho-normalised) of the Gaussian
-    // with covariance I/3 + s; entries of odd total order vanish
-    const float t3 = 1.0f / 3.0f;
-    const float sgx = t3 + sxx, sgy = t3 + syy, sgz = t3 + szz;
-    float K[3][3][3];
-#pragma unroll
-    for (int a = 0; a < 27; ++a) (&K[0][0][0])[a] = 0.0f;
-    K[2][0][0] = sxx; K[0][2][0] = syy; K[0][0][2] = szz;
-    K[1][1][0] = sxy; K[1][0][1] = sxz; K[0][1][1] = syz;
-    K[2][2][0] = (sxx + syy) * t3 + sxx * syy + 2.0f * sxy * sxy;
-    K[2][0][2] = (sxx + szz) * t3 + sxx * szz + 2.0f * sxz * sxz;
-    K[0][2][2] = (syy + szz) * t3 + syy * szz + 2.0f * syz * syz;
-    K[2][1][1] = sgx * syz + 2.0f * sxy * sxz;
-    K[1][2][1] = sgy * sxz + 2.0f * sxy * syz;
-    K[1][1][2] = sgz * sxy + 2.0f * sxz * syz;
-    K[2][2][2] = (sxx + syy + szz) * (1.0f / 9.0f) + (sxx * syy + sxx * szz + syy * szz) * t3 +
-                 sxx * syy * szz + 2.0f * (sgx * syz * syz + sgy * sxz * sxz + sgz * sxy * sxy) +
-                 8.0f * sxy * sxz * syz;
-
-    // rest value per moment order r = (1, 0, 1/3), per velocity w1 = (1/6, 2/3, 1/6)
-    // for c = -1, 0, +1 (index c + 1)
-    constexpr float R[3] = {1.0f, 0.0f, 1.0f / 3.0f};
-    constexpr float W1[3] = {1.0f / 6.0f, 2.0f / 3.0f, 1.0f / 6.0f};
-    float dsum = 0.0f;
-    float A[3][3][3];  // [a][b][cz + 1]
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int b = 0; b < 3; ++b)
-            axis_inverse(R[a] * R[b], uz, K[a][b][0], K[a][b][1], K[a][b][2], A[a][b][0],
-                         A[a][b][1], A[a][b][2]);
-    float B[3][3][3];  // [a][cy + 1][cz + 1]
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-            axis_inverse(R[a] * W1[c], uy, A[a][0][c], A[a][1][c], A[a][2][c], B[a][0][c],
-                         B[a][1][c], B[a][2][c]);
-#pragma unroll
-    for (int b = 0; b < 3; ++b)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            float pm, p0, pp;
-            axis_inverse(W1[b] * W1[c], ux, B[0][b][c], B[1][b][c], B[2][b][c], pm, p0, pp);
-            // f*_i - w_i = drho w_i + rho (P_i - w_i)
-            const int im = dir27(-1, b - 1, c - 1), i0 = dir27(0, b - 1, c - 1),
-                      ip = dir27(1, b - 1, c - 1);
-            const float vm = drho * w27(im) + rho * pm;
-            const float vp = drho * w27(ip) + rho * pp;
-            dsum += (vm - f[im]) + (vp - f[ip]);
-            f[im] = vm;
-            f[ip] = vp;
-            if (i0 != 0) {
-                const float v0 = drho * w27(i0) + rho * p0;
-                dsum += v0 - f[i0];
-                f[i0] = v0;
-            }
-        }
-    // the rest population takes minus the sum of the stored changes of the
-    // others (in exact arithmetic the same value as its reconstruction), so
-    // the mass changes only by the rounding of f_0
-    f[0] -= dsum;
-
-    const float hx = (jx + 0.5f * Fx) * irho, hy = (jy + 0.5f * Fy) * irho,
-                hz = (jz + 0.5f * Fz) * irho;
-    if constexpr (SL == 7) {
-        // scalar (Eq. 28-30) with the half-force velocity and the molecular D;
-        // non-equilibrium form closed by the rest population, so sum Phi is
-        // conserved up to the rounding of Phi_0 (see collide_bgk)
-        const float omp = 1.0f / kp.taup0;
-        const float pe = w7(1) * chit, pa = w7(1) * 4.0f * chi;
-        float nq[7];
-        nq[1] = p[1] - (pe + pa * hx);
-        nq[2] = p[2] - (pe - pa * hx);
-        nq[3] = p[3] - (pe + pa * hy);
-        nq[4] = p[4] - (pe - pa * hy);
-        nq[5] = p[5] - (pe + pa * hz);
-        nq[6] = p[6] - (pe - pa * hz);
-        float psum = 0.0f;
-#pragma unroll
-        for (int k = 1; k < 7; ++k) {
-            const float v = p[k] - omp * nq[k];
-            psum += v - p[k];
-            p[k] = v;
-        }
-        p[0] -= psum;
-    } else {
-        // D3Q27 factorized central moments (Eq. 37-51) with every rate of order
-        // >= 2 equal to 1: the moments in the frame of u relax to their lattice
-        // equilibria chi (1, 0, 1/3)^(x) per axis, except the first-order ones,
-        // v = (1 - omega_D) (sum c Phi - chi u) with omega_D from Eq. 51.  The
-        // post-collision populations are therefore
-        //   chi Ex Ey Ez + vx Gx Ey Ez + vy Ex Gy Ez + vz Ex Ey Gz,
-        // E(0) = 2/3 - u^2, E(+-1) = (1/3 + u^2 +- u)/2 (moments (1, 0, 1/3)),
-        // G(0) = -2u, G(+-1) = (2u +- 1)/2 (moments (0, 1, 0)), both inverted in
-        // the frame of u.  Held as deviations: Phi* - w = (chi - 1) w +
-        // chi (Ex Ey Ez - w) + v-terms, with Ex Ey Ez - w expanded in the small
-        // parts dE = E - w1.
-        float jpx = 0.0f, jpy = 0.0f, jpz = 0.0f;   // sum c (Phi - w) = sum c Phi
-#pragma unroll
-        for (int i = 1; i < 27; i += 2) {
-            const float dm = p[i] - p[i + 1];
-            if (cx27(i)) jpx += cx27(i) * dm;
-            if (cy27(i)) jpy += cy27(i) * dm;
-            if (cz27(i)) jpz += cz27(i) * dm;
-        }
-        const float r1 = 1.0f - kp.omD;
-        const float vx = r1 * (jpx - chi * hx), vy = r1 * (jpy - chi * hy), vz = r1 * (jpz - chi * hz);
-        const float u[3] = {hx, hy, hz};
-        const float v[3] = {vx, vy, vz};
-        float W[3][3], dE[3][3], G[3][3];   // [axis][c + 1]
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const float uu = u[a] * u[a];
-            W[a][0] = 1.0f / 6.0f; W[a][1] = 2.0f / 3.0f; W[a][2] = 1.0f / 6.0f;
-            dE[a][1] = -uu;
-            dE[a][0] = 0.5f * (uu - u[a]);
-            dE[a][2] = 0.5f * (uu + u[a]);
-            G[a][1] = -2.0f * u[a];
-            G[a][0] = u[a] - 0.5f;
-            G[a][2] = u[a] + 0.5f;
-        }
-        float psum = 0.0f;
-#pragma unroll
-        for (int i = 1; i < 27; ++i) {
-            const int cx = cx27(i) + 1, cy = cy27(i) + 1, cz = cz27(i) + 1;
-            const float Ex = W[0][cx] + dE[0][cx], Ey = W[1][cy] + dE[1][cy], Ez = W[2][cz] + dE[2][cz];
-            // Ex Ey Ez - Wx Wy Wz without cancellation
-            const float dprod = dE[0][cx] * Ey * Ez + W[0][cx] * dE[1][cy] * Ez +
-                                W[0][cx] * W[1][cy] * dE[2][cz];
-            const float vt = v[0] * G[0][cx] * Ey * Ez + v[1] * Ex * G[1][cy] * Ez +
-                             v[2] * Ex * Ey * G[2][cz];
-            const float nv = chit * w27(i) + chi * dprod + vt;
-            psum += nv - p[i];
-            p[i] = nv;
-        }
-        // the rest population closes the sum (its reconstruction
-        // chit w_0 + chi dprod_0 + vt_0 in exact arithmetic): sum Phi changes
-        // only by the rounding of Phi_0, not by that of the 27-term chi
-        p[0] -= psum;
-    }
-}
 
 template <bool ODD, bool SAVE, typename S, int SL>
 __global__ void __launch_bounds__(128, LBM_STEP_MINB) cumulant_step_kernel(KParams kp, S* __restrict__ f,

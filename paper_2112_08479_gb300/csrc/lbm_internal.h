@@ -68,10 +68,16 @@ cudaError_t launch_fw_accumulate(const KParams& kp, Kind k, bool odd, const View
 cudaError_t launch_adjoint_step(const KParams& kp, const float* state, const float* lam_next,
                                 float* lam, double* dcs, float wfw, float dAdCs, cudaStream_t st);
 cudaError_t launch_push_step(const KParams& kp, const float* src, float* dst, cudaStream_t st);
+cudaError_t launch_cumulant_adjoint_step(const KParams& kp, const float* state,
+                                         const float* lam_next, float* lam, float wfw,
+                                         cudaStream_t st);
+cudaError_t launch_cumulant_push_step(const KParams& kp, const float* src, float* dst,
+                                      cudaStream_t st);
 cudaError_t launch_front_adjoint(const KParams& kp, int Q, int NS, const Views& v,
                                  const float* state, float* lam, double* value, double threshold,
                                  int x0, double H, cudaStream_t st);
-cudaError_t launch_adjoint_chi0(const KParams& kp, const float* lam0, float* grad, cudaStream_t st);
+cudaError_t launch_adjoint_chi0(const KParams& kp, int Q, const float* lam0, float* grad,
+                                cudaStream_t st);
 
 unsigned diag_block_count(int nx, int nz);
 

@@ -1,7 +1,8 @@
 """Differentiable lock-exchange objectives of the initial scalar field and C_s.
 
 ``LBMObjective.apply(chi0, cs, params, nsteps, K, kind)`` runs the
-BGK-Smagorinsky lock-exchange forward on the GPU and returns J (FP64):
+lock-exchange forward (BGK-Smagorinsky or cumulant fluid, D3Q7 scalar, FP32)
+on the GPU and returns J (FP64):
 
 - kind "friction": the time-integrated bottom friction J = sum_{n=1..N}
   F_w(s_n) (Eq. 62-64), accumulated on the device;
@@ -9,8 +10,8 @@ BGK-Smagorinsky lock-exchange forward on the GPU and returns J (FP64):
   (Sec. 3.1), whose threshold crossing is interpolated between columns so
   that J is a continuous, piecewise smooth function of chi0 (lbm_front_adjoint).
 
-Its backward returns dJ/dchi0 and dJ/dC_s from the library's discrete
-adjoint: the forward keeps a checkpoint of the state every K steps, and the
+Its backward returns dJ/dchi0 and dJ/dC_s (0 for the cumulant model, which
+has no Smagorinsky closure) from the library's discrete adjoint: the forward keeps a checkpoint of the state every K steps, and the
 reverse sweep recomputes each K-step segment from its checkpoint before
 stepping the adjoint back through it (lbm_adjoint_segment).  Device memory:
 N/K + 1 checkpoints plus one K-state segment buffer.
@@ -29,10 +30,9 @@ class LBMObjective(torch.autograd.Function):
     @staticmethod
     def forward(ctx, chi0, cs, params: lbm.Params, nsteps: int, K: int = 100,
                 kind: str = "friction"):
-        if (params.model != lbm.LBM_BGK_SMAG_Q19 or params.storage != lbm.LBM_FP32
-                or params.scalar != lbm.LBM_SCALAR_Q7):
-            raise ValueError("the adjoint exists for the BGK-Smagorinsky model with the D3Q7 "
-                             "scalar and FP32 storage")
+        if params.storage != lbm.LBM_FP32 or params.scalar != lbm.LBM_SCALAR_Q7:
+            raise ValueError("the adjoint exists for the D3Q7 scalar and FP32 storage "
+                             "(BGK-Smagorinsky or cumulant fluid)")
         if nsteps < 1 or K < 1:
             raise ValueError("nsteps and K must be >= 1")
         if kind not in ("friction", "front"):
@@ -59,16 +59,16 @@ class LBMObjective(torch.autograd.Function):
     def backward(ctx, gJ):
         lat, K, nsteps = ctx.lat, ctx.K, ctx.nsteps
         dev = ctx.final.device
-        N = lat.N
-        lam = torch.empty(26, N, device=dev)
-        tmp = torch.empty(26, N, device=dev)
+        N, S = lat.N, lat.Q + lat.NS
+        lam = torch.empty(S, N, device=dev)
+        tmp = torch.empty(S, N, device=dev)
         dcs = torch.zeros(1, dtype=torch.float64, device=dev)
         w_fw = 1.0 if ctx.kind == "friction" else 0.0
         if ctx.kind == "friction":
             lat.adjoint_step(ctx.final, None, lam, None, 1.0)   # lam_N = dF_w(s_N)/ds_N
         else:
             lat.front_adjoint(ctx.final, lam, None)             # lam_N = d front(s_N)/ds_N
-        seg_buf = torch.empty(min(K, nsteps), 26, N, device=dev)
+        seg_buf = torch.empty(min(K, nsteps), S, N, device=dev)
         for seg in range(ctx.ckpts.shape[0] - 1, -1, -1):
             n0 = seg * K
             lat.adjoint_segment(ctx.ckpts[seg], n0, min(K, nsteps - n0), seg_buf, lam, tmp, dcs,

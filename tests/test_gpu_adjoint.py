@@ -251,3 +251,60 @@ def test_front_gradient_vs_fp64_reference_sub_case():
     rel = np.linalg.norm(g - g_ref.ravel()) / np.linalg.norm(g_ref)
     assert rel < 1e-3, rel
     assert cs.grad.item() == pytest.approx(gcs_ref, rel=1e-3)
+
+
+# ---------------------------------------------------------------------------
+# Adjoint of the cumulant step (Eq. 54-58 with the D3Q7 scalar)
+
+@pytest.mark.parametrize("flags", [0, lbm.LBM_FLAG_PERIODIC_X | lbm.LBM_FLAG_PERIODIC_Z])
+@pytest.mark.parametrize("w_fw", [0.0, 1.0])
+def test_cumulant_adjoint_step_matches_autograd_vjp(flags, w_fw):
+    """One reverse step of the cumulant model against torch.autograd on the
+    FP64 restatement (truncated ln / exp of the moment generating function)."""
+    p = _sub_case(nx=20, ny=5, nz=6, model=lbm.LBM_CUMULANT_Q27, flags=flags, gprime=3e-3,
+                  eg=(0.3, -0.4, -0.866), nu=0.01, D=0.02, omega_bulk=0.8)
+    lat = lbm.Lattice(p, device="cuda")
+    s0 = _random_state(p, 3)
+    lam_next = inputs.normal((p.Q + 7, p.N), 8).astype(np.float32)
+    st = torch.from_numpy(s0).cuda()
+    out = torch.empty(p.Q + 7, p.N, device="cuda")
+    dcs = torch.zeros(1, dtype=torch.float64, device="cuda")
+    lat.adjoint_step(st, torch.from_numpy(lam_next).cuda(), out, dcs, w_fw)
+    got = out.cpu().numpy().astype(np.float64)
+    assert dcs.item() == 0.0
+
+    op = oracle_params(p)
+    step = A.make_step(op)
+    f, phi = canonical_to_oracle(s0, p)
+    ft = torch.tensor(f, requires_grad=True)
+    pt = torch.tensor(phi, requires_grad=True)
+    f1, p1 = step(ft, pt, torch.tensor(0.0, dtype=torch.float64))
+    lf, lp = canonical_to_oracle(lam_next, p, shifted=False)
+    inner = (f1 * torch.tensor(lf)).sum() + (p1 * torch.tensor(lp)).sum() + w_fw * step.friction(ft, pt)
+    gf, gp = torch.autograd.grad(inner, (ft, pt))
+    want = np.concatenate([np.moveaxis(gf.numpy(), -1, 0),
+                           np.moveaxis(gp.numpy(), -1, 0)]).reshape(p.Q + 7, -1)
+    err = np.abs(got - want).max() / np.abs(want).max()
+    assert err < 1e-4, err
+
+
+@pytest.mark.parametrize("kind", ["friction", "front"])
+def test_cumulant_gradient_vs_fp64_reference_sub_case(kind):
+    """Both objectives through 800 cumulant steps of the 32 x 4 x 8 sub-case,
+    checkpoints every 100 steps, against the FP64 reference gradient."""
+    p = _sub_case(model=lbm.LBM_CUMULANT_Q27)
+    nsteps = 800
+    chi0 = O.lock_chi0(p.nx, p.ny, p.nz, p.x0, p.noise_amp, p.seed)
+    J_ref, g_ref, _ = A.gradient(oracle_params(p), chi0, p.cs_smag, nsteps, objective=kind,
+                                 x0=p.x0, H=p.H)
+    x = torch.tensor(chi0.ravel(), dtype=torch.float32, device="cuda", requires_grad=True)
+    fn = friction_objective if kind == "friction" else front_objective
+    J = fn(x, p.cs_smag, p, nsteps, K=100)
+    J.backward()
+    if kind == "friction":
+        assert J.item() == pytest.approx(J_ref, rel=1e-4)
+    else:
+        assert J.item() == pytest.approx(J_ref, abs=1e-4)
+    g = x.grad.cpu().numpy().astype(np.float64)
+    rel = np.linalg.norm(g - g_ref.ravel()) / np.linalg.norm(g_ref)
+    assert rel < 1e-3, rel

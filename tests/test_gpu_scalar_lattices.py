@@ -124,6 +124,7 @@ def test_16bit_one_step_within_rounding(storage, model, scalar):
 
 
 def test_adjoint_rejects_other_scalar_lattices():
+    """The adjoint exists for the D3Q7 scalar only (either fluid)."""
     p = lbm.Params(8, 2, 4, scalar=lbm.LBM_SCALAR_Q6, x0=1, H=4)
     lat = lbm.Lattice(p, device="cuda")
     st = lat.get_state()

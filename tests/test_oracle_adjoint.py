@@ -146,3 +146,40 @@ def test_front_objective_gradient_matches_central_differences():
     pm.cs_smag -= h
     fd = (_front_c_oracle(pp, chi0, n, x0, H) - _front_c_oracle(pm, chi0, n, x0, H)) / (2 * h)
     assert gcs == pytest.approx(fd, rel=1e-4, abs=1e-9)
+
+
+# ---------------------------------------------------------------------------
+# Cumulant fluid (Eq. 54-58): torch restatement and its gradients
+
+def test_torch_cumulant_step_matches_c_oracle():
+    p = _params(model=1, omega_bulk=0.8, eg=(0.48, 0.6, -0.64))
+    chi0 = O.lock_chi0(p.nx, p.ny, p.nz, 5, 1e-2, 3)
+    f, phi = O.init(p, chi0)
+    st = A.make_step(p)
+    assert isinstance(st, A.CumulantStep)
+    ft, pt = A.initial_state(st, chi0)
+    cs = torch.tensor(p.cs_smag, dtype=torch.float64)
+    with torch.no_grad():
+        for _ in range(25):
+            ft, pt = st(ft, pt, cs)
+    f, phi = O.run(p, 25, f, phi)
+    assert np.abs(ft.numpy() - f).max() < 1e-14
+    assert np.abs(pt.numpy() - phi).max() < 1e-14
+    assert A.objective(p, chi0, p.cs_smag, 25) == pytest.approx(_J_c_oracle(p, chi0, 25), rel=1e-12)
+
+
+@pytest.mark.parametrize("objective", ["friction", "front"])
+def test_cumulant_gradient_matches_central_differences(objective):
+    p = _params(model=1)
+    x0, H, n = 5, 6.0, 60
+    chi0 = O.lock_chi0(p.nx, p.ny, p.nz, x0, 1e-2, 3)
+    J, g, gcs = A.gradient(p, chi0, p.cs_smag, n, objective=objective, x0=x0, H=H)
+    Jc = (_J_c_oracle if objective == "friction" else
+          (lambda pp, c, nn: _front_c_oracle(pp, c, nn, x0, H)))
+    assert J == pytest.approx(Jc(p, chi0, n), rel=1e-12)
+    assert gcs == 0.0                     # no Smagorinsky closure in the cumulant model
+    eps = 1e-3
+    for seed in (1, 2, 3):
+        d = inputs.unit_direction(chi0.shape, seed)
+        fd = (Jc(p, chi0 + eps * d, n) - Jc(p, chi0 - eps * d, n)) / (2 * eps)
+        assert np.sum(g * d) == pytest.approx(fd, rel=1e-4, abs=1e-9)

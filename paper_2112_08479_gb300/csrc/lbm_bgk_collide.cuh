@@ -93,13 +93,7 @@ __device__ __forceinline__ void collide_bgk(const KParams& kp, float (&f)[19],
     // S_i = guo w_i (3 cF - 3 u.F + 9 cu cF)
     const float base = drho - 1.5f * rho * usq;       // even part of (feq - w)/w at cu = 0
     const float gbase = -3.0f * guo * uF;             // even part of S/w at cF = 0
-    // The moving populations take their update; the rest population takes
-    // minus the sum of the changes actually stored in them, so the node's
-    // population sum changes only by the rounding of f_0 (in exact arithmetic
-    // f*_0 = keep f_0 + w_0 (om base + gbase) is the same value).  Otherwise
-    // om times the rounding error of the 19-term density sum, and the
-    // rounding of every stored population, would enter the mass.
-    float dsum = 0.0f;
+    f[0] = keep * f[0] + sf * w19(0) * (om * base + gbase);
 #pragma unroll
     for (int i = 1; i < 19; i += 2) {
         const float cu = cx27(i) * ux + cy27(i) * uy + cz27(i) * uz;
@@ -107,22 +101,17 @@ __device__ __forceinline__ void collide_bgk(const KParams& kp, float (&f)[19],
         const float w = sf * w19(i);
         const float even = w * (om * (base + 4.5f * rho * cu * cu) + gbase + 9.0f * guo * cu * cF);
         const float odd = w * (om * 3.0f * rho * cu + 3.0f * guo * cF);
-        const float a = keep * f[i] + even + odd;
-        const float b = keep * f[i + 1] + even - odd;
-        dsum += (a - f[i]) + (b - f[i + 1]);
-        f[i] = a;
-        f[i + 1] = b;
+        f[i] = keep * f[i] + even + odd;
+        f[i + 1] = keep * f[i + 1] + even - odd;
     }
-    f[0] -= dsum;
 
     const float omp = 1.0f / (kp.taup0 + kp.kT * dtau);
     if constexpr (SL == 7) {
         // scalar: Phi_eq - w = w (chi - 1 + 4 chi c.u).  Only the non-equilibrium
-        // parts of the moving populations are relaxed, and the rest population
-        // takes minus the sum of their stored changes, so the update conserves
-        // sum Phi up to the rounding of Phi_0 (relaxing towards the rounded chi
-        // would inject omega times the rounding error of the 7-term sum at
-        // every node)
+        // parts are relaxed, and the rest population's part closes their sum to
+        // zero, so the update conserves sum Phi exactly up to the rounding of the
+        // stored results (relaxing towards the rounded chi would inject
+        // omega times the rounding error of the 7-term sum at every node)
         const float pe = w7(1) * chs, pa = sp * w7(1) * 4.0f * chi;
         float nq[7];
         nq[1] = p[1] - (pe + pa * ux);
@@ -131,15 +120,9 @@ __device__ __forceinline__ void collide_bgk(const KParams& kp, float (&f)[19],
         nq[4] = p[4] - (pe - pa * uy);
         nq[5] = p[5] - (pe + pa * uz);
         nq[6] = p[6] - (pe - pa * uz);
-        // the rest population closes the sum of the changes actually stored
-        float dsum = 0.0f;
+        nq[0] = -(((nq[1] + nq[2]) + (nq[3] + nq[4])) + (nq[5] + nq[6]));
 #pragma unroll
-        for (int k = 1; k < 7; ++k) {
-            const float v = p[k] - omp * nq[k];
-            dsum += v - p[k];
-            p[k] = v;
-        }
-        p[0] -= dsum;
+        for (int k = 0; k < 7; ++k) p[k] -= omp * nq[k];
     } else {
         // D3Q6: Phi_eq - w = (chi - 1 + 3 chi c.u) / 6; with no rest population
         // the non-equilibrium parts are centred on their mean instead

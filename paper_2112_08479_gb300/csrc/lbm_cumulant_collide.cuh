@@ -120,7 +120,6 @@ __device__ __forceinline__ void collide_cumulant(const KParams& kp, float (&f)[2
     // for c = -1, 0, +1 (index c + 1)
     constexpr float R[3] = {1.0f, 0.0f, 1.0f / 3.0f};
     constexpr float W1[3] = {1.0f / 6.0f, 2.0f / 3.0f, 1.0f / 6.0f};
-    float dsum = 0.0f;
     float A[3][3][3];  // [a][b][cz + 1]
 #pragma unroll
     for (int a = 0; a < 3; ++a)
@@ -144,28 +143,17 @@ __device__ __forceinline__ void collide_cumulant(const KParams& kp, float (&f)[2
             // f*_i - w_i = drho w_i + rho (P_i - w_i)
             const int im = dir27(-1, b - 1, c - 1), i0 = dir27(0, b - 1, c - 1),
                       ip = dir27(1, b - 1, c - 1);
-            const float vm = drho * w27(im) + rho * pm;
-            const float vp = drho * w27(ip) + rho * pp;
-            dsum += (vm - f[im]) + (vp - f[ip]);
-            f[im] = vm;
-            f[ip] = vp;
-            if (i0 != 0) {
-                const float v0 = drho * w27(i0) + rho * p0;
-                dsum += v0 - f[i0];
-                f[i0] = v0;
-            }
+            f[im] = drho * w27(im) + rho * pm;
+            f[i0] = drho * w27(i0) + rho * p0;
+            f[ip] = drho * w27(ip) + rho * pp;
         }
-    // the rest population takes minus the sum of the stored changes of the
-    // others (in exact arithmetic the same value as its reconstruction), so
-    // the mass changes only by the rounding of f_0
-    f[0] -= dsum;
 
     const float hx = (jx + 0.5f * Fx) * irho, hy = (jy + 0.5f * Fy) * irho,
                 hz = (jz + 0.5f * Fz) * irho;
     if constexpr (SL == 7) {
         // scalar (Eq. 28-30) with the half-force velocity and the molecular D;
-        // non-equilibrium form closed by the rest population, so sum Phi is
-        // conserved up to the rounding of Phi_0 (see collide_bgk)
+        // non-equilibrium form whose parts sum to zero, so sum Phi is conserved
+        // up to the rounding of the stored results (see collide_bgk)
         const float omp = 1.0f / kp.taup0;
         const float pe = w7(1) * chit, pa = w7(1) * 4.0f * chi;
         float nq[7];
@@ -175,14 +163,9 @@ __device__ __forceinline__ void collide_cumulant(const KParams& kp, float (&f)[2
         nq[4] = p[4] - (pe - pa * hy);
         nq[5] = p[5] - (pe + pa * hz);
         nq[6] = p[6] - (pe - pa * hz);
-        float psum = 0.0f;
+        nq[0] = -(((nq[1] + nq[2]) + (nq[3] + nq[4])) + (nq[5] + nq[6]));
 #pragma unroll
-        for (int k = 1; k < 7; ++k) {
-            const float v = p[k] - omp * nq[k];
-            psum += v - p[k];
-            p[k] = v;
-        }
-        p[0] -= psum;
+        for (int k = 0; k < 7; ++k) p[k] -= omp * nq[k];
     } else {
         // D3Q27 factorized central moments (Eq. 37-51) with every rate of order
         // >= 2 equal to 1: the moments in the frame of u relax to their lattice

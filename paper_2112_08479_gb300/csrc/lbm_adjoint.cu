@@ -83,7 +83,13 @@ cudaError_t launch_push_step(const KParams& kp, const float* src, float* dst, cu
 // lam_{n+1,opp(i)}(x) when x + c_i is beyond a wall, and C^T is the
 // reverse-mode derivative of collide_bgk at s_n written out by hand.  The
 // kink of q = |Pi| at Pi = 0 takes the subgradient 0.
-__global__ void __launch_bounds__(128) bgk_adjoint_kernel(KParams kp, const float* __restrict__ st,
+// Minimum resident blocks per SM requested from the register allocator: 5
+// caps the kernel at 96 registers (no spills) for 20 resident warps per SM.
+#ifndef LBM_ADJ_MINB
+#define LBM_ADJ_MINB 5
+#endif
+
+__global__ void __launch_bounds__(128, LBM_ADJ_MINB) bgk_adjoint_kernel(KParams kp, const float* __restrict__ st,
                                                           const float* __restrict__ lamn,
                                                           float* __restrict__ lam,
                                                           double* __restrict__ dcs, float wfw,

@@ -281,20 +281,22 @@ def side_variant(torch, model, storage, scalar="q7", steps=3):
     return {"mnups": mnups, "ms_per_time_step": kern * 1e3, "achieved_gbs": gbs}
 
 
-def adjoint_ratio(torch):
+def adjoint_ratio(torch, dims=(256, 32, 64), K=100, model="bgk", reps=5):
     """Forward step vs one reverse step (out-of-place recompute from the
-    checkpoint + adjoint step) on the 256 x 32 x 64 differentiation box, over
-    a K = 100 segment (lbm_adjoint_segment)."""
+    checkpoint + adjoint step) on a lock-exchange box (default the 256 x 32 x
+    64 differentiation box, H = nz, Re = 2000), over a K-step segment
+    (lbm_adjoint_segment)."""
     from paper_2112_08479_gb300 import lbm
-    p = lbm.lock_exchange(256, 32, 64, H=64, x0=64, u_b=0.03, Re=2000.0)
+    nx, ny, nz = dims
+    p = lbm.lock_exchange(nx, ny, nz, H=nz, x0=nz, u_b=0.03, Re=2000.0, model=model)
     lat = lbm.Lattice(p, device="cuda")
-    K = 100
+    S = p.Q + p.NS
     s = lat.stream
     lat.step(200)
     ck = lat.get_state()
-    seg = torch.empty(K, 26, p.N, device="cuda")
-    lam = torch.zeros(26, p.N, device="cuda")
-    tmp = torch.empty(26, p.N, device="cuda")
+    seg = torch.empty(K, S, p.N, device="cuda")
+    lam = torch.zeros(S, p.N, device="cuda")
+    tmp = torch.empty(S, p.N, device="cuda")
     dcs = torch.zeros(1, dtype=torch.float64, device="cuda")
 
     def fwd():
@@ -310,13 +312,17 @@ def adjoint_ratio(torch):
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(s)
-        for _ in range(5):
+        for _ in range(reps):
             fn()
         b.record(s)
         torch.cuda.synchronize()
-        out[name] = a.elapsed_time(b) / 5 / K
-    return {"workload": "256x32x64 BGK-Smagorinsky FP32, K=100 segment", "fwd_ms_per_step": out["forward"],
-            "adj_ms_per_step": out["reverse"], "ratio": out["reverse"] / out["forward"]}
+        out[name] = a.elapsed_time(b) / reps / K
+    del lat, seg, lam, tmp
+    torch.cuda.empty_cache()
+    model_name = "BGK-Smagorinsky" if model == "bgk" else "cumulant"
+    return {"workload": f"{nx}x{ny}x{nz} {model_name} FP32, K={K} segment",
+            "fwd_ms_per_step": out["forward"], "adj_ms_per_step": out["reverse"],
+            "ratio": out["reverse"] / out["forward"]}
 
 
 def run_ours(args, ws, rank, local):
@@ -388,6 +394,8 @@ def run_ours(args, ws, rank, local):
             variants[f"{model}_{storage}" + ("" if scalar == "q7" else f"_{scalar}")] = r
         extra["variants"] = variants
         extra["adjoint"] = adjoint_ratio(torch)
+        extra["adjoint_cumulant"] = adjoint_ratio(torch, model="cumulant")
+        extra["adjoint_1024x64x128"] = adjoint_ratio(torch, (1024, 64, 128), K=20, reps=3)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         cpu = oracle_sample()
@@ -417,7 +425,19 @@ def main():
     ap.add_argument("--workload", default="config3", choices=sorted(WORKLOADS))
     ap.add_argument("--model", default="bgk", choices=["bgk", "cumulant"])
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16s", "bf16s"])
+    ap.add_argument("--adjoint-only", default=None, metavar="NX,NY,NZ",
+                    help="only time the adjoint sweep against the forward step on this "
+                         "lock-exchange box (--model, --adjoint-k) and print it")
+    ap.add_argument("--adjoint-k", type=int, default=100)
     args = ap.parse_args()
+    if args.adjoint_only:
+        import torch
+        from paper_2112_08479_gb300 import lbm
+        lbm.load()
+        dims = tuple(int(v) for v in args.adjoint_only.split(","))
+        print(json.dumps({"adjoint": adjoint_ratio(torch, dims, args.adjoint_k, args.model)}),
+              flush=True)
+        return
     WORKLOAD.clear()
     WORKLOAD.update(WORKLOADS[args.workload])
     ws, rank, local = dist_setup()

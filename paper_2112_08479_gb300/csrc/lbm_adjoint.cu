@@ -185,58 +185,57 @@ __global__ void __launch_bounds__(128, LBM_ADJ_MINB) bgk_adjoint_kernel(KParams 
         // tau_Phi = taup0 + kT dtau
         float gtau = -gomp * omp * omp * kp.kT;
         // fluid: f* = (1 - om) f + om feq + (1 - om/2) B, with
-        //   feq_i = w (drho + rho (3 cu + 4.5 cu^2 - 1.5 u.u)),
-        //   B_i = w (3 cF - 3 u.F + 9 cu cF),  cu = c_i.u, cF = c_i.F.
-        // Opposite directions (i, i + 1) share w and flip c, so with the sums
-        // ms = mu_i + mu_{i+1} and differences md = mu_i - mu_{i+1} each pair
-        // contributes (even parts E = 4.5 cu^2 - 1.5 u.u, Be = 9 cu cF - 3 u.F;
-        // odd parts O = 3 cu, Bo = 3 cF):
-        //   d/d om:  w (ms (drho + rho E) + md rho O) - (ms fs + md fd)/2
-        //            - w (ms Be + md Bo)/2
-        //   d/d rho: om w (ms (1 + E) + md O)
-        //   d/d u:   om w rho V + guo w ms (9 cF c - 3 F),  V = 3 md c + ms (9 cu c - 3 u)
-        //   d/d F:   guo w V
-        float gom = 0.0f;
-        {
-            // rest population (c = 0)
-            const float w = w19(0), m0 = mu[0];
-            const float E = -1.5f * usq;
-            gf[0] = (1.0f - om) * m0;
-            gom += m0 * (w * (drho + rho * E) - f[0]) + 0.5f * m0 * w * 3.0f * uF;
-            grho += om * w * m0 * (1.0f + E);
-            const float a = -3.0f * w * m0 * (om * rho);
-            gux += a * ux; guy += a * uy; guz += a * uz;
-            const float b = -3.0f * w * m0 * guo;
-            gFx += b * ux; gFy += b * uy; gFz += b * uz;
-            gux += b * Fx; guy += b * Fy; guz += b * Fz;
-        }
+        //   feq_i = w_i (drho + rho (3 cu + 4.5 cu^2 - 1.5 u.u)),
+        //   B_i = w_i (3 cF - 3 u.F + 9 cu cF),  cu = c_i.u, cF = c_i.F.
+        // Both are polynomials of degree 2 in c_i, so every sum over i of mu_i
+        // times them or their derivatives is a combination of the weighted
+        // moments of the adjoint A0 = sum w mu, A1 = sum w mu c, A2 = sum w mu c c
+        // (taken with opposite-pair sums and differences):
+        //   sum mu feq = drho A0 + rho (3 u.A1 + 4.5 u.A2.u - 1.5 u.u A0)
+        //   sum mu B   = 3 F.A1 - 3 u.F A0 + 9 u.A2.F
+        //   d/d drho   : om (A0 + 3 u.A1 + 4.5 u.A2.u - 1.5 u.u A0)
+        //   d/d u      : om rho V + guo (9 A2.F - 3 F A0),  V = 3 A1 + 9 A2.u - 3 u A0
+        //   d/d F      : guo V
+        float A0 = w19(0) * mu[0], A1x = 0.0f, A1y = 0.0f, A1z = 0.0f;
+        float Axx = 0.0f, Ayy = 0.0f, Azz = 0.0f, Axy = 0.0f, Axz = 0.0f, Ayz = 0.0f;
+        float muf = mu[0] * f[0];
+        gf[0] = (1.0f - om) * mu[0];
 #pragma unroll
         for (int i = 1; i < 19; i += 2) {
-            const float cxi = cx27(i), cyi = cy27(i), czi = cz27(i);
-            const float cu = cxi * ux + cyi * uy + czi * uz;
-            const float cF = cxi * Fx + cyi * Fy + czi * Fz;
             const float w = w19(i);
-            const float ms = mu[i] + mu[i + 1], md = mu[i] - mu[i + 1];
-            const float fs = f[i] + f[i + 1], fd = f[i] - f[i + 1];
-            const float E = 4.5f * cu * cu - 1.5f * usq, O = 3.0f * cu;
-            const float Be = 9.0f * cu * cF - 3.0f * uF, Bo = 3.0f * cF;
+            const float ms = w * (mu[i] + mu[i + 1]), md = w * (mu[i] - mu[i + 1]);
+            muf += mu[i] * f[i] + mu[i + 1] * f[i + 1];
+            A0 += ms;
+            if (cx27(i)) { A1x += cx27(i) * md; Axx += ms; }
+            if (cy27(i)) { A1y += cy27(i) * md; Ayy += ms; }
+            if (cz27(i)) { A1z += cz27(i) * md; Azz += ms; }
+            if (cx27(i) * cy27(i)) Axy += cx27(i) * cy27(i) * ms;
+            if (cx27(i) * cz27(i)) Axz += cx27(i) * cz27(i) * ms;
+            if (cy27(i) * cz27(i)) Ayz += cy27(i) * cz27(i) * ms;
             gf[i] = (1.0f - om) * mu[i];
             gf[i + 1] = (1.0f - om) * mu[i + 1];
-            gom += w * (ms * (drho + rho * E) + md * rho * O) - 0.5f * (ms * fs + md * fd) -
-                   0.5f * w * (ms * Be + md * Bo);
-            grho += om * w * (ms * (1.0f + E) + md * O);
-            const float m3 = 3.0f * md, m9 = 9.0f * ms * cu;
-            const float Vx = m3 * cxi + m9 * cxi - 3.0f * ms * ux;
-            const float Vy = m3 * cyi + m9 * cyi - 3.0f * ms * uy;
-            const float Vz = m3 * czi + m9 * czi - 3.0f * ms * uz;
-            const float a = om * w * rho, b = guo * w;
-            gux += a * Vx; guy += a * Vy; guz += a * Vz;
-            gFx += b * Vx; gFy += b * Vy; gFz += b * Vz;
-            const float bm = b * ms, c9 = 9.0f * cF;
-            gux += bm * (c9 * cxi - 3.0f * Fx);
-            guy += bm * (c9 * cyi - 3.0f * Fy);
-            guz += bm * (c9 * czi - 3.0f * Fz);
         }
+        const float Aux = Axx * ux + Axy * uy + Axz * uz;
+        const float Auy = Axy * ux + Ayy * uy + Ayz * uz;
+        const float Auz = Axz * ux + Ayz * uy + Azz * uz;
+        const float AFx = Axx * Fx + Axy * Fy + Axz * Fz;
+        const float AFy = Axy * Fx + Ayy * Fy + Ayz * Fz;
+        const float AFz = Axz * Fx + Ayz * Fy + Azz * Fz;
+        const float uA1 = ux * A1x + uy * A1y + uz * A1z;
+        const float uAu = ux * Aux + uy * Auy + uz * Auz;
+        const float FA1 = Fx * A1x + Fy * A1y + Fz * A1z;
+        const float uAF = ux * AFx + uy * AFy + uz * AFz;
+        const float pe = 3.0f * uA1 + 4.5f * uAu - 1.5f * usq * A0;
+        const float gom = drho * A0 + rho * pe - muf - 0.5f * (3.0f * FA1 - 3.0f * uF * A0 + 9.0f * uAF);
+        grho += om * (A0 + pe);
+        const float Vx = 3.0f * A1x + 9.0f * Aux - 3.0f * ux * A0;
+        const float Vy = 3.0f * A1y + 9.0f * Auy - 3.0f * uy * A0;
+        const float Vz = 3.0f * A1z + 9.0f * Auz - 3.0f * uz * A0;
+        const float orho = om * rho;
+        gux += orho * Vx + guo * (9.0f * AFx - 3.0f * Fx * A0);
+        guy += orho * Vy + guo * (9.0f * AFy - 3.0f * Fy * A0);
+        guz += orho * Vz + guo * (9.0f * AFz - 3.0f * Fz * A0);
+        gFx += guo * Vx; gFy += guo * Vy; gFz += guo * Vz;
         gtau += -gom * om * om;
         // dtau = (s - tau0)/2, s = sqrt(tau0^2 + X): d dtau / dX = 1 / (4 s)
         const float gX = gtau / (4.0f * s);

@@ -126,6 +126,10 @@ def test_status_strings(lib):
 def test_null_context_is_rejected(lib):
     assert lib.lbm_step(None, 1) == lbm.LBM_ERR_ARG
     assert lib.lbm_sync(None) == lbm.LBM_ERR_ARG
+    assert lib.lbm_front_adjoint(None, None, None, None) == lbm.LBM_ERR_ARG
+    assert lib.lbm_adjoint_segment(None, None, 0, 1, None, None, None, None, 1.0) == lbm.LBM_ERR_ARG
+    assert lib.lbm_adjoint_step(None, None, None, None, None, 1.0) == lbm.LBM_ERR_ARG
+    assert lib.lbm_objective_forward(None, 1, 1, None, None) == lbm.LBM_ERR_ARG
     assert lib.lbm_get_step(None) == -1
     lib.lbm_destroy(None)
 

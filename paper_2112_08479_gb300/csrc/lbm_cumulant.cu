@@ -12,8 +12,15 @@
 
 namespace lbmgpu {
 
+// Minimum resident blocks per SM for the register allocator: the D3Q27 FCM
+// scalar doubles the live populations, so its instantiation gets its own
+// setting.
+#ifndef LBM_Q27_MINB
+#define LBM_Q27_MINB LBM_STEP_MINB
+#endif
+
 template <bool ODD, bool SAVE, typename S, int SL>
-__global__ void __launch_bounds__(128, LBM_STEP_MINB) cumulant_step_kernel(KParams kp, S* __restrict__ f,
+__global__ void __launch_bounds__(128, SL == 27 ? LBM_Q27_MINB : LBM_STEP_MINB) cumulant_step_kernel(KParams kp, S* __restrict__ f,
                                                             S* __restrict__ phi,
                                                             float* __restrict__ save) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;

@@ -124,7 +124,10 @@ typedef struct lbm_params {
 typedef struct lbm_diagnostics {
     double front;        /* (x_f + 1/2 - x0) / H, Sec. 3.1 */
     double front_node;   /* x_f in node coordinates, -1 when no column reaches
-                            the threshold */
+                            the threshold; searched over all x with walls at
+                            the x ends, over x < (nx + x0) / 2 with
+                            LBM_FLAG_PERIODIC_X (the half of the ring ahead of
+                            the lock) */
     double Fw;           /* bottom-wall friction sum_{x,y} tau_w, Eq. 62-64,
                             lattice units, streamwise component */
     double mass_delta;   /* sum over nodes of rho - 1 (FP64 reduction) */
@@ -238,8 +241,9 @@ LBM_API lbm_status lbm_adjoint_segment(lbm_ctx* ctx, const float* ckpt, int64_t 
 
 /* Front position of a state and its derivative (Sec. 3.1 with reading R11:
  * chibar(x, z) = mean over y of chi, m(x) = max over z of chibar, x_f = the
- * largest x with m(x) >= front_threshold, moved to the linear threshold
- * crossing between x_f and x_f + 1; value (x_f + 1/2 - x0) / H).  The
+ * largest searched x (see lbm_diagnostics.front_node) with m(x) >=
+ * front_threshold, moved to the linear threshold crossing between x_f and
+ * x_f + 1; value (x_f + 1/2 - x0) / H).  The
  * interpolated front is a continuous, piecewise smooth function of the
  * state, the smooth surrogate of the node-wise front used as an objective.
  * state: canonical layout ((Q + NS) * N floats, device).  front_dev: one
@@ -247,7 +251,8 @@ LBM_API lbm_status lbm_adjoint_segment(lbm_ctx* ctx, const float* ckpt, int64_t 
  * floats (device) receiving d value / d state: zero except on the scalar
  * rows of the 2 ny nodes (x_f, y, z0) and (x_f + 1, y, z1), z0 and z1 the
  * first z attaining m; zero everywhere when no column reaches the threshold
- * or x_f = nx - 1.  Any model, scalar lattice and storage.  Asynchronous. */
+ * or x_f is the last searched column.  Any model, scalar lattice and storage.
+ * Asynchronous. */
 LBM_API lbm_status lbm_front_adjoint(lbm_ctx* ctx, const float* state, float* lam,
                                      double* front_dev);
 

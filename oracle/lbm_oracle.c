@@ -43,6 +43,7 @@
  *   R10 interface noise on column x0 - 1 from splitmix64(seed ^ n).
  *   R11 front = largest x whose span-averaged column maximum is >= threshold,
  *       linearly interpolated to the threshold crossing.
+ *   R18 with periodic x ends the front is searched in x < (nx + x0) / 2.
  *   R12 F_w = sum over the bottom plane of nu (9 u_x(z=0) - u_x(z=1)) / 3.
  *
  * Parity pins: every function here is pinned by tests against closed forms,

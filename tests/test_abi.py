@@ -141,3 +141,10 @@ def test_lock_exchange_parameters():
     assert p.nu == pytest.approx(2.56e-4)
     assert p.D == p.nu
     assert 3 * p.nu + 0.5 == pytest.approx(0.500768)
+    assert p.flags == 0 and p.sc_t == 1.0
+    q = lbm.lock_exchange(2500, 150, 100, H=100, x0=100, u_b=0.03, Re=895.0, geometry="periodic",
+                          sc_t="paper")
+    assert q.flags == lbm.LBM_FLAG_PERIODIC_X            # Fig. 4b: periodic ends
+    assert q.sc_t == pytest.approx(0.17**2)               # literal Sc_T = C_s^2
+    with pytest.raises(ValueError):
+        lbm.lock_exchange(8, 2, 4, H=4, x0=2, u_b=0.03, Re=100.0, geometry="open")

@@ -83,10 +83,11 @@ cudaError_t launch_push_step(const KParams& kp, const float* src, float* dst, cu
 // lam_{n+1,opp(i)}(x) when x + c_i is beyond a wall, and C^T is the
 // reverse-mode derivative of collide_bgk at s_n written out by hand.  The
 // kink of q = |Pi| at Pi = 0 takes the subgradient 0.
-// Minimum resident blocks per SM requested from the register allocator: 5
-// caps the kernel at 96 registers (no spills) for 20 resident warps per SM.
+// Minimum resident blocks per SM requested from the register allocator: 6
+// caps the kernel at 80 registers (44 bytes of spills, served by L1) for 24
+// resident warps per SM; measured faster than 4 (128 registers) and 5 (96).
 #ifndef LBM_ADJ_MINB
-#define LBM_ADJ_MINB 5
+#define LBM_ADJ_MINB 6
 #endif
 
 __global__ void __launch_bounds__(128, LBM_ADJ_MINB) bgk_adjoint_kernel(KParams kp, const float* __restrict__ st,

@@ -102,11 +102,21 @@ def window_oracle(p: lbm.Params, state0: np.ndarray, node, steps: int):
     return f[cz, cy, cx] - weights(p.model), phi[cz, cy, cx] - wscalar(p)
 
 
-def rest_row_tol(phi_rows, rel):
-    """Bound on the error of the scalar's rest population under 16-bit storage,
-    where it is held in FP32 and receives the storage roundings of the moving
-    populations: at most one half-ulp (rel = 2^-11 FP16, 2^-8 BF16) of each
-    moving population.  phi_rows: the scalar populations (NS, ...) of the
-    reference, population 0 first."""
+def rest_row_tol(p, pre, rel):
+    """Bound on the error of the scalar's rest population after one step
+    under 16-bit storage, where it is held in FP32 and receives the storage
+    roundings of the node's post-collision moving populations: at most one
+    half-ulp (rel = 2^-11 FP16, 2^-8 BF16) of each of them.  The rest
+    population never moves, so the populations whose roundings it receives
+    are those the node's own collision produced (they stream away
+    afterwards).  pre: canonical columns [Q + NS, M] of the nodes before the
+    step; returns the bound for each of the M nodes (FP64 oracle collision)."""
     import numpy as np
-    return rel * np.abs(np.asarray(phi_rows)[1:]).sum(0) * 1.01
+    op = oracle_params(p)
+    pre = np.asarray(pre, dtype=np.float64)
+    w, ws = weights(p.model), wscalar(p)
+    out = np.zeros(pre.shape[1])
+    for m in range(pre.shape[1]):
+        _, po = O.collide_node(op, pre[: p.Q, m] + w, pre[p.Q:, m] + ws)
+        out[m] = rel * np.abs(po[1:] - ws[1:]).sum() * 1.01
+    return out

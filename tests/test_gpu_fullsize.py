@@ -63,7 +63,8 @@ def test_full_size_sampled_nodes(model, storage):
             tol_f = rel * np.abs(f_o) * 1.001 + 1e-5 * scale
             tol_p = rel * np.abs(phi_o) * 1.001 + 1e-6
             if rel:   # FP32 rest population with rounding feedback
-                tol_p[0] = rest_row_tol(phi_o, rel)[()] + 1e-6
+                col = s0v[:, z, y, x].cpu().numpy().astype(np.float64)[:, None]
+                tol_p[0] = rest_row_tol(p, col, rel)[0] + 1e-6
             assert np.all(np.abs(got[: p.Q] - f_o) <= tol_f), (parity, node)
             assert np.all(np.abs(got[p.Q:] - phi_o) <= tol_p), (parity, node)
         del s0, s1

@@ -84,6 +84,13 @@ def test_gradient_vs_fp64_reference_sub_case():
     rel = np.linalg.norm(g - g_ref.ravel()) / np.linalg.norm(g_ref)
     assert rel < 1e-3, rel
     assert cs.grad.item() == pytest.approx(gcs_ref, rel=1e-3)
+    # and against the full central-difference gradient of the C oracle
+    # (tests/golden/fd_gradient_32x4x8.txt, same sub-case and steps)
+    from test_oracle_adjoint import _load_fd_golden
+    J_fd, g_fd, cs_fd = _load_fd_golden()
+    assert J.item() == pytest.approx(J_fd, rel=1e-4)
+    assert np.linalg.norm(g - g_fd) / np.linalg.norm(g_fd) < 1e-3
+    assert cs.grad.item() == pytest.approx(cs_fd, rel=1e-3)
 
 
 def test_checkpoint_interval_does_not_change_gradient():

@@ -3,6 +3,8 @@
 Its forward step is a second, independent restatement of the BGK step and must
 agree with the C oracle to round-off; its gradient must agree with central
 finite differences of the objective computed by the C oracle."""
+import os
+
 import numpy as np
 import pytest
 
@@ -183,3 +185,34 @@ def test_cumulant_gradient_matches_central_differences(objective):
         d = inputs.unit_direction(chi0.shape, seed)
         fd = (Jc(p, chi0 + eps * d, n) - Jc(p, chi0 - eps * d, n)) / (2 * eps)
         assert np.sum(g * d) == pytest.approx(fd, rel=1e-4, abs=1e-9)
+
+
+def _load_fd_golden():
+    path = os.path.join(os.path.dirname(__file__), "golden", "fd_gradient_32x4x8.txt")
+    head = {}
+    vals = []
+    for line in open(path):
+        if line.startswith("# J "):
+            head["J"] = float(line.split()[2])
+        elif line.startswith("# dJ/dC_s "):
+            head["cs"] = float(line.split()[2])
+        elif not line.startswith("#"):
+            vals.append(float(line))
+    return head["J"], np.array(vals), head["cs"]
+
+
+def test_reference_gradient_matches_full_fd_golden():
+    """The FP64 reference gradient over 2,000 steps of the 32 x 4 x 8
+    sub-case against the full central-difference gradient (all 1,024 chi0
+    values and C_s) that tests/golden/make_fd_gradient.py computed with the C
+    oracle."""
+    J_fd, g_fd, cs_fd = _load_fd_golden()
+    p = O.OracleParams(32, 4, 8, model=0, nu=9.6e-4, D=9.6e-4, cs_smag=0.17, sc_t=1.0,
+                       gprime=1.40625e-5)
+    chi0 = O.lock_chi0(32, 4, 8, 8, 1e-3, 2112)
+    J, g, gcs = A.gradient(p, chi0, 0.17, 2000)
+    assert J == pytest.approx(J_fd, rel=1e-12)
+    g = g.ravel()
+    assert np.linalg.norm(g - g_fd) < 1e-7 * np.linalg.norm(g_fd)
+    assert np.abs(g - g_fd).max() < 1e-6 * np.abs(g_fd).max()
+    assert gcs == pytest.approx(cs_fd, rel=1e-6)

@@ -281,32 +281,39 @@ def side_variant(torch, model, storage, scalar="q7", steps=3):
     return {"mnups": mnups, "ms_per_time_step": kern * 1e3, "achieved_gbs": gbs}
 
 
-def adjoint_ratio(torch, dims=(256, 32, 64), K=100, model="bgk", reps=5):
-    """Forward step vs one reverse step (out-of-place recompute from the
-    checkpoint + adjoint step) on a lock-exchange box (default the 256 x 32 x
-    64 differentiation box, H = nz, Re = 2000), over a K-step segment
-    (lbm_adjoint_segment)."""
+def adjoint_ratio(torch, dims=(256, 32, 64), K=100, model="bgk", nseg=4, reps=2):
+    """Forward step vs one reverse step on a lock-exchange box (default the
+    256 x 32 x 64 differentiation box, H = nz, Re = 2000): the reverse sweep
+    of the autograd backward (objective.reverse_sweep: recompute of each
+    K-step segment from its checkpoint + adjoint steps, the next segment's
+    recompute overlapped with the current sweep on a second stream) over
+    nseg segments, and the same sweep without the overlap."""
     from paper_2112_08479_gb300 import lbm
+    from paper_2112_08479_gb300.objective import reverse_sweep
     nx, ny, nz = dims
     p = lbm.lock_exchange(nx, ny, nz, H=nz, x0=nz, u_b=0.03, Re=2000.0, model=model)
     lat = lbm.Lattice(p, device="cuda")
     S = p.Q + p.NS
     s = lat.stream
+    n = nseg * K
     lat.step(200)
-    ck = lat.get_state()
-    seg = torch.empty(K, S, p.N, device="cuda")
+    ckpts = torch.empty(nseg, S, p.N, device="cuda")
+    lat.objective_forward(n, K, ckpts, None)
     lam = torch.zeros(S, p.N, device="cuda")
     tmp = torch.empty(S, p.N, device="cuda")
     dcs = torch.zeros(1, dtype=torch.float64, device="cuda")
 
     def fwd():
-        lat.step(K)
+        lat.step(n)
 
     def rev():
-        lat.adjoint_segment(ck, 200, K, seg, lam, tmp, dcs)
+        reverse_sweep(lat, ckpts, n, K, lam, tmp, dcs, 1.0, overlap=True)
+
+    def rev_seq():
+        reverse_sweep(lat, ckpts, n, K, lam, tmp, dcs, 1.0, overlap=False)
 
     out = {}
-    for name, fn in (("forward", fwd), ("reverse", rev)):
+    for name, fn in (("forward", fwd), ("reverse", rev), ("reverse_sequential", rev_seq)):
         fn()
         torch.cuda.synchronize()
         a = torch.cuda.Event(enable_timing=True)
@@ -316,13 +323,14 @@ def adjoint_ratio(torch, dims=(256, 32, 64), K=100, model="bgk", reps=5):
             fn()
         b.record(s)
         torch.cuda.synchronize()
-        out[name] = a.elapsed_time(b) / reps / K
-    del lat, seg, lam, tmp
+        out[name] = a.elapsed_time(b) / reps / n
+    del lat, ckpts, lam, tmp
     torch.cuda.empty_cache()
     model_name = "BGK-Smagorinsky" if model == "bgk" else "cumulant"
-    return {"workload": f"{nx}x{ny}x{nz} {model_name} FP32, K={K} segment",
+    return {"workload": f"{nx}x{ny}x{nz} {model_name} FP32, {nseg} segments of K={K}",
             "fwd_ms_per_step": out["forward"], "adj_ms_per_step": out["reverse"],
-            "ratio": out["reverse"] / out["forward"]}
+            "ratio": out["reverse"] / out["forward"],
+            "ratio_without_overlap": out["reverse_sequential"] / out["forward"]}
 
 
 def run_ours(args, ws, rank, local):
@@ -395,7 +403,7 @@ def run_ours(args, ws, rank, local):
         extra["variants"] = variants
         extra["adjoint"] = adjoint_ratio(torch)
         extra["adjoint_cumulant"] = adjoint_ratio(torch, model="cumulant")
-        extra["adjoint_1024x64x128"] = adjoint_ratio(torch, (1024, 64, 128), K=20, reps=3)
+        extra["adjoint_1024x64x128"] = adjoint_ratio(torch, (1024, 64, 128), K=20, nseg=3, reps=1)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         cpu = oracle_sample()

@@ -239,6 +239,28 @@ LBM_API lbm_status lbm_adjoint_segment(lbm_ctx* ctx, const float* ckpt, int64_t 
                                        float* seg, float* lam, float* tmp, double* dJdCs_dev,
                                        double w_fw);
 
+/* The two halves of lbm_adjoint_segment, for callers that overlap the
+ * recompute of one segment with the adjoint sweep of the next (two streams):
+ *
+ * lbm_recompute_segment: from ckpt = s_{n0}, writes s_{n0+1} .. s_{n0+k-1}
+ * into seg + j (Q + NS) N, j = 1 .. k-1 (out-of-place steps of the same
+ * arithmetic as lbm_step).
+ *
+ * lbm_adjoint_sweep: applies k adjoint steps backwards through ckpt (j = 0)
+ * and seg + j (Q + NS) N (j = 1 .. k-1): on entry lam holds lam_{n0+k}, on
+ * return lam_{n0}; w_fw, tmp and dJdCs_dev as for lbm_adjoint_segment.
+ *
+ * Both read ckpt and seg, both enqueue on `stream` (a cudaStream_t of the
+ * context's device; NULL selects the context's stream) and neither
+ * synchronises: ordering between the two calls (seg written before it is
+ * swept, not overwritten while it is swept) is the caller's.  Device
+ * buffers; LBM_ERR_STATE for 16-bit storage or the D3Q6 and D3Q27 scalars. */
+LBM_API lbm_status lbm_recompute_segment(lbm_ctx* ctx, const float* ckpt, int32_t k, float* seg,
+                                         void* stream);
+LBM_API lbm_status lbm_adjoint_sweep(lbm_ctx* ctx, const float* ckpt, const float* seg,
+                                     int64_t n0, int32_t k, float* lam, float* tmp,
+                                     double* dJdCs_dev, double w_fw, void* stream);
+
 /* Front position of a state and its derivative (Sec. 3.1 with reading R11:
  * chibar(x, z) = mean over y of chi, m(x) = max over z of chibar, x_f = the
  * largest searched x (see lbm_diagnostics.front_node) with m(x) >=

@@ -322,16 +322,29 @@ lbm_status lbm_set_state(lbm_ctx* c, const float* src, int64_t step) {
 namespace {
 // One reverse step of the model's adjoint (BGK: with the C_s term).
 cudaError_t adjoint_step_any(lbm_ctx* c, const float* state, const float* lam_next, float* lam,
-                             double* dcs, float wfw) {
+                             double* dcs, float wfw, cudaStream_t st) {
     if (c->p.model == LBM_CUMULANT_Q27)
-        return launch_cumulant_adjoint_step(c->kp, state, lam_next, lam, wfw, c->stream);
+        return launch_cumulant_adjoint_step(c->kp, state, lam_next, lam, wfw, st);
     const float dAdCs = (float)(36.0 * sqrt(2.0) * c->p.cs_smag);
-    return launch_adjoint_step(c->kp, state, lam_next, lam, dcs, wfw, dAdCs, c->stream);
+    return launch_adjoint_step(c->kp, state, lam_next, lam, dcs, wfw, dAdCs, st);
 }
 
-cudaError_t push_step_any(lbm_ctx* c, const float* src, float* dst) {
-    if (c->p.model == LBM_CUMULANT_Q27) return launch_cumulant_push_step(c->kp, src, dst, c->stream);
-    return launch_push_step(c->kp, src, dst, c->stream);
+cudaError_t push_step_any(lbm_ctx* c, const float* src, float* dst, cudaStream_t st) {
+    if (c->p.model == LBM_CUMULANT_Q27) return launch_cumulant_push_step(c->kp, src, dst, st);
+    return launch_push_step(c->kp, src, dst, st);
+}
+
+cudaStream_t stream_or_ctx(lbm_ctx* c, void* stream) {
+    return stream ? (cudaStream_t)stream : c->stream;
+}
+
+lbm_status sweep_check(lbm_ctx* c) {
+    if (c->p.storage != LBM_FP32 || c->p.scalar != LBM_SCALAR_Q7) {
+        snprintf(c->err, sizeof c->err,
+                 "the adjoint sweep exists for the D3Q7 scalar and FP32 storage");
+        return LBM_ERR_STATE;
+    }
+    return LBM_OK;
 }
 
 lbm_status adjoint_model_check(lbm_ctx* c) {
@@ -350,7 +363,7 @@ lbm_status lbm_adjoint_step(lbm_ctx* c, const float* state_n, const float* lam_n
     if (!state_n || !lam_n) return arg_fail(c, "state_n and lam_n must not be NULL");
     if (lam_n == lam_next || lam_n == state_n) return arg_fail(c, "lam_n must not alias its inputs");
     if (!isfinite(w_fw)) return arg_fail(c, "w_fw must be finite");
-    cudaError_t e = adjoint_step_any(c, state_n, lam_next, lam_n, dJdCs_dev, (float)w_fw);
+    cudaError_t e = adjoint_step_any(c, state_n, lam_next, lam_n, dJdCs_dev, (float)w_fw, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "adjoint launch");
     return LBM_OK;
 }
@@ -379,39 +392,59 @@ lbm_status lbm_objective_forward(lbm_ctx* c, int32_t nsteps, int32_t K, float* c
     return LBM_OK;
 }
 
-lbm_status lbm_adjoint_segment(lbm_ctx* c, const float* ckpt, int64_t n0, int32_t k, float* seg,
-                               float* lam, float* tmp, double* dJdCs_dev, double w_fw) {
+lbm_status lbm_recompute_segment(lbm_ctx* c, const float* ckpt, int32_t k, float* seg,
+                                 void* stream) {
     if (!c) return arg_fail(nullptr, "ctx is NULL");
-    if (c->p.storage != LBM_FP32 || c->p.scalar != LBM_SCALAR_Q7) {
-        snprintf(c->err, sizeof c->err,
-                 "the adjoint sweep exists for the D3Q7 scalar and FP32 storage");
-        return LBM_ERR_STATE;
+    if (lbm_status s = sweep_check(c); s != LBM_OK) return s;
+    if (k < 1) return arg_fail(c, "k must be >= 1");
+    if (!ckpt || (k > 1 && !seg)) return arg_fail(c, "NULL buffer");
+    const size_t S = (size_t)(q_of(&c->p) + ns_of(&c->p)) * c->kp.N;
+    const cudaStream_t st = stream_or_ctx(c, stream);
+    cudaError_t e = cudaSuccess;
+    // s_{n0+1} .. s_{n0+k-1} into seg[1 .. k-1]
+    const float* prev = ckpt;
+    for (int32_t j = 1; j < k && e == cudaSuccess; ++j) {
+        e = push_step_any(c, prev, seg + (size_t)j * S, st);
+        prev = seg + (size_t)j * S;
     }
+    if (e != cudaSuccess) return cuda_fail(c, e, "recompute segment");
+    return LBM_OK;
+}
+
+lbm_status lbm_adjoint_sweep(lbm_ctx* c, const float* ckpt, const float* seg, int64_t n0,
+                             int32_t k, float* lam, float* tmp, double* dJdCs_dev, double w_fw,
+                             void* stream) {
+    if (!c) return arg_fail(nullptr, "ctx is NULL");
+    if (lbm_status s = sweep_check(c); s != LBM_OK) return s;
     if (k < 1 || n0 < 0) return arg_fail(c, "k must be >= 1 and n0 >= 0");
     if (!ckpt || !lam || !tmp || (k > 1 && !seg)) return arg_fail(c, "NULL buffer");
     if (lam == tmp) return arg_fail(c, "lam and tmp must differ");
     if (!isfinite(w_fw)) return arg_fail(c, "w_fw must be finite");
     const size_t S = (size_t)(q_of(&c->p) + ns_of(&c->p)) * c->kp.N;
+    const cudaStream_t st = stream_or_ctx(c, stream);
     cudaError_t e = cudaSuccess;
-    // recompute s_{n0+1} .. s_{n0+k-1} into seg[1 .. k-1]
-    const float* prev = ckpt;
-    for (int32_t j = 1; j < k && e == cudaSuccess; ++j) {
-        e = push_step_any(c, prev, seg + (size_t)j * S);
-        prev = seg + (size_t)j * S;
-    }
     // lam_{n0+k} -> lam_{n0}
     float* cur = lam;
     float* nxt = tmp;
     for (int32_t j = k - 1; j >= 0 && e == cudaSuccess; --j) {
         const int64_t n = n0 + j;
-        const float* st = j == 0 ? ckpt : seg + (size_t)j * S;
-        e = adjoint_step_any(c, st, cur, nxt, dJdCs_dev, n >= 1 ? (float)w_fw : 0.0f);
+        const float* sn = j == 0 ? ckpt : seg + (size_t)j * S;
+        e = adjoint_step_any(c, sn, cur, nxt, dJdCs_dev, n >= 1 ? (float)w_fw : 0.0f, st);
         float* t = cur; cur = nxt; nxt = t;
     }
     if (e == cudaSuccess && cur != lam)
-        e = cudaMemcpyAsync(lam, cur, S * sizeof(float), cudaMemcpyDeviceToDevice, c->stream);
-    if (e != cudaSuccess) return cuda_fail(c, e, "adjoint segment");
+        e = cudaMemcpyAsync(lam, cur, S * sizeof(float), cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "adjoint sweep");
     return LBM_OK;
+}
+
+lbm_status lbm_adjoint_segment(lbm_ctx* c, const float* ckpt, int64_t n0, int32_t k, float* seg,
+                               float* lam, float* tmp, double* dJdCs_dev, double w_fw) {
+    if (!c) return arg_fail(nullptr, "ctx is NULL");
+    if (k < 1 || n0 < 0) return arg_fail(c, "k must be >= 1 and n0 >= 0");
+    lbm_status s = lbm_recompute_segment(c, ckpt, k, seg, nullptr);
+    if (s != LBM_OK) return s;
+    return lbm_adjoint_sweep(c, ckpt, seg, n0, k, lam, tmp, dJdCs_dev, w_fw, nullptr);
 }
 
 lbm_status lbm_front_adjoint(lbm_ctx* c, const float* state, float* lam, double* front_dev) {

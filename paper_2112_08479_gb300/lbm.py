@@ -75,6 +75,9 @@ SIGNATURES = [
     ("lbm_adjoint_segment", C.c_int, [_CTX, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p,
                                       C.c_void_p, C.c_void_p, C.c_void_p, C.c_double]),
     ("lbm_front_adjoint", C.c_int, [_CTX, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("lbm_recompute_segment", C.c_int, [_CTX, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
+    ("lbm_adjoint_sweep", C.c_int, [_CTX, C.c_void_p, C.c_void_p, C.c_int64, C.c_int32,
+                                    C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_void_p]),
     ("lbm_adjoint_chi0", C.c_int, [_CTX, C.c_void_p, C.c_void_p]),
     ("lbm_diag_static", C.c_int, [_P, C.c_void_p, C.c_int64, C.c_void_p,
                                   C.POINTER(lbm_diagnostics)]),
@@ -187,6 +190,16 @@ def lbm_adjoint_segment(ctx, ckpt_ptr, n0: int, k: int, seg_ptr, lam_ptr, tmp_pt
                         w_fw: float = 1.0):
     _check(load().lbm_adjoint_segment(ctx, ckpt_ptr, n0, k, seg_ptr, lam_ptr, tmp_ptr, dcs_ptr,
                                       w_fw), ctx)
+
+
+def lbm_recompute_segment(ctx, ckpt_ptr, k: int, seg_ptr, stream=None):
+    _check(load().lbm_recompute_segment(ctx, ckpt_ptr, k, seg_ptr, stream), ctx)
+
+
+def lbm_adjoint_sweep(ctx, ckpt_ptr, seg_ptr, n0: int, k: int, lam_ptr, tmp_ptr, dcs_ptr,
+                      w_fw: float = 1.0, stream=None):
+    _check(load().lbm_adjoint_sweep(ctx, ckpt_ptr, seg_ptr, n0, k, lam_ptr, tmp_ptr, dcs_ptr, w_fw,
+                                    stream), ctx)
 
 
 def lbm_front_adjoint(ctx, state_ptr, lam_ptr, front_ptr):
@@ -375,6 +388,20 @@ class Lattice:
     def adjoint_segment(self, ckpt, n0: int, k: int, seg, lam, tmp, dcs, w_fw: float = 1.0):
         lbm_adjoint_segment(self.ctx, ckpt.data_ptr(), n0, k, _ptr(seg), lam.data_ptr(),
                             tmp.data_ptr(), dcs.data_ptr() if dcs is not None else None, w_fw)
+
+    def recompute_segment(self, ckpt, k: int, seg, stream=None):
+        """States n0+1 .. n0+k-1 from the checkpoint into seg[1 .. k-1] on
+        `stream` (a torch.cuda.Stream; None: the lattice's stream)."""
+        lbm_recompute_segment(self.ctx, ckpt.data_ptr(), k, _ptr(seg),
+                              stream.cuda_stream if stream is not None else None)
+
+    def adjoint_sweep(self, ckpt, seg, n0: int, k: int, lam, tmp, dcs, w_fw: float = 1.0,
+                      stream=None):
+        """k reverse steps through ckpt and seg on `stream` (None: the
+        lattice's stream)."""
+        lbm_adjoint_sweep(self.ctx, ckpt.data_ptr(), _ptr(seg), n0, k, lam.data_ptr(),
+                          tmp.data_ptr(), dcs.data_ptr() if dcs is not None else None, w_fw,
+                          stream.cuda_stream if stream is not None else None)
 
     def front_adjoint(self, state, lam=None, value=None):
         """Front of `state` (canonical layout) into `value` (one device double)

@@ -13,8 +13,10 @@ on the GPU and returns J (FP64):
 Its backward returns dJ/dchi0 and dJ/dC_s (0 for the cumulant model, which
 has no Smagorinsky closure) from the library's discrete adjoint: the forward keeps a checkpoint of the state every K steps, and the
 reverse sweep recomputes each K-step segment from its checkpoint before
-stepping the adjoint back through it (lbm_adjoint_segment).  Device memory:
-N/K + 1 checkpoints plus one K-state segment buffer.
+stepping the adjoint back through it (lbm_recompute_segment,
+lbm_adjoint_sweep), the recompute of the next segment overlapping the sweep
+of the current one on a second stream.  Device memory: N/K + 1 checkpoints
+plus two K-state segment buffers.
 """
 from __future__ import annotations
 
@@ -68,16 +70,54 @@ class LBMObjective(torch.autograd.Function):
             lat.adjoint_step(ctx.final, None, lam, None, 1.0)   # lam_N = dF_w(s_N)/ds_N
         else:
             lat.front_adjoint(ctx.final, lam, None)             # lam_N = d front(s_N)/ds_N
-        seg_buf = torch.empty(min(K, nsteps), S, N, device=dev)
-        for seg in range(ctx.ckpts.shape[0] - 1, -1, -1):
-            n0 = seg * K
-            lat.adjoint_segment(ctx.ckpts[seg], n0, min(K, nsteps - n0), seg_buf, lam, tmp, dcs,
-                                w_fw)
+        reverse_sweep(lat, ctx.ckpts, nsteps, K, lam, tmp, dcs, w_fw)
         grad = torch.empty(N, device=dev)
         lat.adjoint_chi0(lam, grad)
         g = gJ.to(torch.float64)
         return ((g * grad.to(torch.float64)).to(ctx.chi_dtype),
                 (g * dcs[0]).to(ctx.cs_dtype), None, None, None, None)
+
+
+def reverse_sweep(lat, ckpts, nsteps: int, K: int, lam, tmp, dcs, w_fw: float,
+                  overlap: bool = True):
+    """lam_N -> lam_0 through all segments of checkpoints `ckpts` (state n0 =
+    s K of segment s).  With `overlap` the recompute of segment s - 1 runs on
+    a second stream while segment s is swept on the lattice's stream (two
+    segment buffers); the two phases have different bottlenecks (the sweep is
+    issue-bound, the recompute streams memory), so they share the GPU."""
+    nseg = ckpts.shape[0]
+    dev = lam.device
+    S, N = lam.shape
+    kmax = min(K, nsteps)
+    main = lat.stream
+    ks = [min(K, nsteps - s * K) for s in range(nseg)]
+    if not overlap or nseg == 1:
+        buf = torch.empty(kmax, S, N, device=dev)
+        for s in range(nseg - 1, -1, -1):
+            lat.recompute_segment(ckpts[s], ks[s], buf)
+            lat.adjoint_sweep(ckpts[s], buf, s * K, ks[s], lam, tmp, dcs, w_fw)
+        return
+    side = torch.cuda.Stream(device=dev)
+    bufs = [torch.empty(kmax, S, N, device=dev) for _ in range(2)]
+    for b in bufs:
+        b.record_stream(side)
+    side.wait_stream(main)                    # checkpoints and lam_N are ready
+    rec_done, sweep_done = {}, {}
+
+    def recompute(s):
+        if s + 2 in sweep_done:               # its buffer was swept by segment s + 2
+            side.wait_event(sweep_done[s + 2])
+        lat.recompute_segment(ckpts[s], ks[s], bufs[s % 2], stream=side)
+        rec_done[s] = side.record_event()
+
+    recompute(nseg - 1)
+    for s in range(nseg - 1, -1, -1):
+        if s >= 1:
+            recompute(s - 1)
+        main.wait_event(rec_done[s])
+        lat.adjoint_sweep(ckpts[s], bufs[s % 2], s * K, ks[s], lam, tmp, dcs, w_fw)
+        sweep_done[s] = main.record_event()
+    main.wait_stream(side)
 
 
 def _cs(cs, chi0):

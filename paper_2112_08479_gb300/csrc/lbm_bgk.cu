@@ -58,8 +58,14 @@ __global__ void __launch_bounds__(128, LBM_STEP_MINB) bgk_step_kernel(KParams kp
 
 // Two x-adjacent nodes per thread (nx even): paired population accesses, see
 // lbm_aa2.cuh.  Same arithmetic per node as bgk_step_kernel.
+// The 16-bit instantiations are issue-bound rather than HBM-bound, so they
+// may trade registers for resident warps differently (LBM_STEP2_MINB16).
+#ifndef LBM_STEP2_MINB16
+#define LBM_STEP2_MINB16 LBM_STEP2_MINB
+#endif
+
 template <bool ODD, bool SAVE, typename S, int SL>
-__global__ void __launch_bounds__(128, LBM_STEP2_MINB) bgk_step2_kernel(KParams kp, S* __restrict__ f,
+__global__ void __launch_bounds__(128, std::is_same<S, float>::value ? LBM_STEP2_MINB : LBM_STEP2_MINB16) bgk_step2_kernel(KParams kp, S* __restrict__ f,
                                                                     S* __restrict__ phi,
                                                                     float* __restrict__ save) {
     const int x = 2 * (blockIdx.x * blockDim.x + threadIdx.x);

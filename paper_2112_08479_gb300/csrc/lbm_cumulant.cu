@@ -19,9 +19,12 @@ namespace lbmgpu {
 #ifndef LBM_Q27_MINB
 #define LBM_Q27_MINB 3
 #endif
+#ifndef LBM_CUM_MINB
+#define LBM_CUM_MINB LBM_STEP_MINB
+#endif
 
 template <bool ODD, bool SAVE, typename S, int SL>
-__global__ void __launch_bounds__(128, SL == 27 ? LBM_Q27_MINB : LBM_STEP_MINB) cumulant_step_kernel(KParams kp, S* __restrict__ f,
+__global__ void __launch_bounds__(128, SL == 27 ? LBM_Q27_MINB : LBM_CUM_MINB) cumulant_step_kernel(KParams kp, S* __restrict__ f,
                                                             S* __restrict__ phi,
                                                             float* __restrict__ save) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;

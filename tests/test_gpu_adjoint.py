@@ -93,8 +93,15 @@ def test_gradient_vs_fp64_reference_sub_case():
     assert cs.grad.item() == pytest.approx(cs_fd, rel=1e-3)
 
 
-def test_checkpoint_interval_does_not_change_gradient():
-    p = _sub_case()
+@pytest.mark.parametrize("model", [lbm.LBM_BGK_SMAG_Q19, lbm.LBM_CUMULANT_Q27])
+def test_checkpoint_interval_does_not_change_gradient(model):
+    """K = 300 is one segment (no overlap); K = 7 and 100 overlap the
+    recompute of each segment with the sweep of the next on a second stream.
+    The adjoint arithmetic is the same; the checkpoints come from the in-place
+    forward kernel and the recomputed states from the out-of-place one, which
+    for BGK agree bit for bit (so do the gradients), for the cumulant to
+    FP32 rounding."""
+    p = _sub_case(model=model)
     chi0 = torch.tensor(O.lock_chi0(p.nx, p.ny, p.nz, p.x0, p.noise_amp, p.seed).ravel(),
                         dtype=torch.float32, device="cuda")
     grads = []
@@ -102,7 +109,12 @@ def test_checkpoint_interval_does_not_change_gradient():
         x = chi0.clone().requires_grad_(True)
         friction_objective(x, p.cs_smag, p, 300, K=K).backward()
         grads.append(x.grad.clone())
-    assert torch.equal(grads[0], grads[1]) and torch.equal(grads[1], grads[2])
+    if model == lbm.LBM_BGK_SMAG_Q19:
+        assert torch.equal(grads[0], grads[1]) and torch.equal(grads[1], grads[2])
+    else:
+        scale = grads[2].abs().max()
+        for g in grads[:2]:
+            assert (g - grads[2]).abs().max() <= 1e-5 * scale
 
 
 def test_gradient_vs_central_differences_full_box():

@@ -24,9 +24,11 @@ def _static_diag(lat, state, step):
     return d.as_dict()
 
 
-@pytest.mark.parametrize("model", ["bgk", "cumulant"])
-def test_static_diag_matches_workspace_diag_on_consecutive_calls(model):
-    p = lbm.lock_exchange(128, 8, 16, H=16, x0=16, u_b=0.05, Re=1000.0, model=model)
+@pytest.mark.parametrize("model,geometry", [("bgk", "walls"), ("cumulant", "walls"),
+                                            ("bgk", "periodic")])
+def test_static_diag_matches_workspace_diag_on_consecutive_calls(model, geometry):
+    p = lbm.lock_exchange(128, 8, 16, H=16, x0=16, u_b=0.05, Re=1000.0, model=model,
+                          geometry=geometry)
     lat = lbm.Lattice(p, device="cuda")
     for steps in (37, 64):
         lat.step(steps)

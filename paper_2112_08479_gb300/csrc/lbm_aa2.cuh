@@ -117,7 +117,9 @@ __device__ __forceinline__ Stencil2 make_stencil2(const KParams& kp, int x, int 
 // A z wall (uniform over the block) turns a direction into a bounce-back from
 // the node's own slot, selected without branching.
 // R32: population 0 (direction 0) lives in the FP32 rest row (rest_row).
-template <int Q, bool ODD, typename S, int D0 = 0, bool R32 = false>
+// ZW: the node pair may lie next to a z wall; false for the z-interior rows,
+// which then skip the wall selects (every z neighbour is in the fluid).
+template <int Q, bool ODD, typename S, int D0 = 0, bool R32 = false, bool ZW = true>
 __device__ __forceinline__ void gather2(const KParams& kp, const S* __restrict__ a,
                                         const Stencil2& st, float (&v0)[Q], float (&v1)[Q]) {
     const unsigned N = kp.N;
@@ -134,7 +136,7 @@ __device__ __forceinline__ void gather2(const KParams& kp, const S* __restrict__
         if (ODD && i != 0) {
             const int dy = -cy27(i), dz = -cz27(i);
             const unsigned row = (unsigned)(opp(i) - D0) * N + st.zr[dz + 1] + st.yr[dy + 1];
-            off = st.zo[dz + 1] ? row + st.x : off;
+            off = (!ZW || st.zo[dz + 1]) ? row + st.x : off;
         }
         P0[k] = 0.0f; P1[k] = 0.0f;
         if (st.active) PairIO<S>::ld(a + off, P0[k], P1[k]);
@@ -151,7 +153,7 @@ __device__ __forceinline__ void gather2(const KParams& kp, const S* __restrict__
             bool need;
             if (dx < 0) { need = st.left; off = st.xmo ? row + st.xm : own; }
             else { need = st.right; off = st.xp2o ? row + st.xp2 : own + 1; }
-            need = need && st.active && st.zo[dz + 1];
+            need = need && st.active && (!ZW || st.zo[dz + 1]);
             if (need) E[k] = Store<S>::ld(a + off);
         }
     }
@@ -161,7 +163,7 @@ __device__ __forceinline__ void gather2(const KParams& kp, const S* __restrict__
         const int dx = -cx27(i), dz = -cz27(i);
         v0[k] = P0[k]; v1[k] = P1[k];
         if (ODD && i != 0 && dx != 0) {
-            const bool in = st.zo[dz + 1];
+            const bool in = !ZW || st.zo[dz + 1];
             if (dx < 0) {
                 // node x needs element x - 1, node x + 1 needs element x
                 const float e = __shfl_up_sync(0xffffffffu, P1[k], 1);
@@ -180,7 +182,7 @@ __device__ __forceinline__ void gather2(const KParams& kp, const S* __restrict__
 // The scatter first exchanges the shifted elements, then issues every store
 // under a predicate (pair stores for the interior lanes, single-element
 // stores for the edge lanes, pair stores into the own slots at a z wall).
-template <int Q, bool ODD, typename S, int D0 = 0, bool R32 = false>
+template <int Q, bool ODD, typename S, int D0 = 0, bool R32 = false, bool ZW = true>
 __device__ __forceinline__ void scatter2(const KParams& kp, S* __restrict__ a, const Stencil2& st,
                                          const float (&v0)[Q], const float (&v1)[Q]) {
     const unsigned N = kp.N;
@@ -206,7 +208,7 @@ __device__ __forceinline__ void scatter2(const KParams& kp, S* __restrict__ a, c
             if (st.active) PairIO<S>::st(a + own, v0[k], v1[k]);
             continue;
         }
-        const bool in = st.zo[dz + 1];
+        const bool in = !ZW || st.zo[dz + 1];
         const unsigned row = (unsigned)k * N + st.zr[dz + 1] + st.yr[dy + 1];
         if (st.active && !in) PairIO<S>::st(a + own, v0[k], v1[k]);
         if (dx == 0) {

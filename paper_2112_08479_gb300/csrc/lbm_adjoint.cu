@@ -46,11 +46,9 @@ __global__ void __launch_bounds__(128, LBM_STEP_MINB) bgk_push_kernel(KParams kp
 // own slots is the AA even-step gather and pushing to slot i of node x + c_i
 // (own slot opp(i) across a wall) is the AA odd-step scatter, both with
 // paired accesses (lbm_aa2.cuh), here between two arrays.
-__global__ void __launch_bounds__(128, LBM_STEP2_MINB) bgk_push2_kernel(KParams kp,
-                                                                      const float* __restrict__ src,
-                                                                      float* __restrict__ dst) {
-    const int x = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
-    const Stencil2 st = make_stencil2(kp, x, blockIdx.y, blockIdx.z);
+template <bool ZW>
+__device__ __forceinline__ void bgk_push2_body(const KParams& kp, const float* __restrict__ src,
+                                               float* __restrict__ dst, const Stencil2& st) {
     const unsigned N = kp.N;
     float f0[19], f1[19], p0[7], p1[7];
     gather2<19, false>(kp, src, st, f0, f1);
@@ -59,8 +57,21 @@ __global__ void __launch_bounds__(128, LBM_STEP2_MINB) bgk_push2_kernel(KParams 
         collide_bgk(kp, f0, p0);
         collide_bgk(kp, f1, p1);
     }
-    scatter2<19, true>(kp, dst, st, f0, f1);
-    scatter2<7, true>(kp, dst + (size_t)19 * N, st, p0, p1);
+    scatter2<19, true, float, 0, false, ZW>(kp, dst, st, f0, f1);
+    scatter2<7, true, float, 0, false, ZW>(kp, dst + (size_t)19 * N, st, p0, p1);
+}
+
+__global__ void __launch_bounds__(128, LBM_STEP2_MINB) bgk_push2_kernel(KParams kp,
+                                                                      const float* __restrict__ src,
+                                                                      float* __restrict__ dst) {
+    const int x = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const Stencil2 st = make_stencil2(kp, x, blockIdx.y, blockIdx.z);
+    const int z = blockIdx.z;
+    // rows away from the z walls (uniform per block) skip the wall selects
+    if ((kp.flags & LBM_FLAG_PERIODIC_Z) || (z > 0 && z < kp.nz - 1))
+        bgk_push2_body<false>(kp, src, dst, st);
+    else
+        bgk_push2_body<true>(kp, src, dst, st);
 }
 
 cudaError_t launch_push_step(const KParams& kp, const float* src, float* dst, cudaStream_t st) {

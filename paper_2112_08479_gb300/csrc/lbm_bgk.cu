@@ -56,25 +56,25 @@ __global__ void __launch_bounds__(128, LBM_STEP_MINB) bgk_step_kernel(KParams kp
 }
 
 
-// Two x-adjacent nodes per thread (nx even): paired population accesses, see
-// lbm_aa2.cuh.  Same arithmetic per node as bgk_step_kernel.
+#ifndef LBM_BGK_ZSPLIT
+#define LBM_BGK_ZSPLIT 1
+#endif
+
 // The 16-bit instantiations are issue-bound rather than HBM-bound, so they
 // may trade registers for resident warps differently (LBM_STEP2_MINB16).
 #ifndef LBM_STEP2_MINB16
 #define LBM_STEP2_MINB16 LBM_STEP2_MINB
 #endif
 
-template <bool ODD, bool SAVE, typename S, int SL>
-__global__ void __launch_bounds__(128, std::is_same<S, float>::value ? LBM_STEP2_MINB : LBM_STEP2_MINB16) bgk_step2_kernel(KParams kp, S* __restrict__ f,
-                                                                    S* __restrict__ phi,
-                                                                    float* __restrict__ save) {
-    const int x = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
-    const Stencil2 st = make_stencil2(kp, x, blockIdx.y, blockIdx.z);
+template <bool ODD, bool SAVE, typename S, int SL, bool ZW>
+__device__ __forceinline__ void bgk_step2_body(const KParams& kp, S* __restrict__ f,
+                                               S* __restrict__ phi, float* __restrict__ save,
+                                               const Stencil2& st) {
     constexpr int NS = ScalarLat<SL>::NS, D0 = ScalarLat<SL>::D0;
     constexpr bool R32 = rest32<S, SL>();
     float f0[19], f1[19], p0[NS], p1[NS];
-    gather2<19, ODD>(kp, f, st, f0, f1);
-    gather2<NS, ODD, S, D0, R32>(kp, phi, st, p0, p1);
+    gather2<19, ODD, S, 0, false, ZW>(kp, f, st, f0, f1);
+    gather2<NS, ODD, S, D0, R32, ZW>(kp, phi, st, p0, p1);
     constexpr bool s16 = !std::is_same<S, float>::value;   // populations in storage units
     if (SAVE && st.active) {
         const unsigned N = kp.N;
@@ -92,8 +92,25 @@ __global__ void __launch_bounds__(128, std::is_same<S, float>::value ? LBM_STEP2
         collide_bgk<s16, SL>(kp, f1, p1);
     }
     if constexpr (R32) feed_rest2<S>(p0, p1);
-    scatter2<19, ODD>(kp, f, st, f0, f1);
-    scatter2<NS, ODD, S, D0, R32>(kp, phi, st, p0, p1);
+    scatter2<19, ODD, S, 0, false, ZW>(kp, f, st, f0, f1);
+    scatter2<NS, ODD, S, D0, R32, ZW>(kp, phi, st, p0, p1);
+}
+
+// Two x-adjacent nodes per thread (nx even): paired population accesses, see
+// lbm_aa2.cuh.  Same arithmetic per node as bgk_step_kernel.  On odd steps
+// the rows away from the z walls (uniform per block) take a body without the
+// wall selects.
+template <bool ODD, bool SAVE, typename S, int SL>
+__global__ void __launch_bounds__(128, std::is_same<S, float>::value ? LBM_STEP2_MINB : LBM_STEP2_MINB16) bgk_step2_kernel(KParams kp, S* __restrict__ f,
+                                                                    S* __restrict__ phi,
+                                                                    float* __restrict__ save) {
+    const int x = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const Stencil2 st = make_stencil2(kp, x, blockIdx.y, blockIdx.z);
+    const int z = blockIdx.z;
+    const bool zwall = ODD && (!LBM_BGK_ZSPLIT ||
+                               (!(kp.flags & LBM_FLAG_PERIODIC_Z) && (z == 0 || z == kp.nz - 1)));
+    if (!ODD || !zwall) bgk_step2_body<ODD, SAVE, S, SL, false>(kp, f, phi, save, st);
+    else bgk_step2_body<ODD, SAVE, S, SL, true>(kp, f, phi, save, st);
 }
 
 template <typename S, int SL>

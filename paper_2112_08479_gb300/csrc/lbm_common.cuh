@@ -249,7 +249,9 @@ __device__ __forceinline__ unsigned nbr(const Stencil& s, int dx, int dy, int dz
 // Population k is direction dk = k + D0 and lives in row k; its opposite
 // direction's row is opp(dk) - D0.
 // R32: population 0 (direction 0) lives in the FP32 rest row (rest_row).
-template <int Q, bool ODD, typename S, int D0 = 0, bool R32 = false>
+// W: the node may have a wall neighbour; false when every neighbour is known
+// to be in the fluid (the wall selects are then skipped).
+template <int Q, bool ODD, typename S, int D0 = 0, bool R32 = false, bool W = true>
 __device__ __forceinline__ void gather(const KParams& kp, const S* __restrict__ a,
                                        const Stencil& st, float (&v)[Q]) {
     const unsigned N = kp.N;
@@ -264,13 +266,13 @@ __device__ __forceinline__ void gather(const KParams& kp, const S* __restrict__ 
         if (ODD && d != 0) {
             bool in;
             const unsigned s = nbr(st, -cx27(d), -cy27(d), -cz27(d), in);
-            off = in ? (unsigned)(opp(d) - D0) * N + s : off;
+            off = (!W || in) ? (unsigned)(opp(d) - D0) * N + s : off;
         }
         v[k] = Store<S>::ld(a + off);
     }
 }
 
-template <int Q, bool ODD, typename S, int D0 = 0, bool R32 = false>
+template <int Q, bool ODD, typename S, int D0 = 0, bool R32 = false, bool W = true>
 __device__ __forceinline__ void scatter(const KParams& kp, S* __restrict__ a, const Stencil& st,
                                         const float (&v)[Q]) {
     const unsigned N = kp.N;
@@ -285,7 +287,7 @@ __device__ __forceinline__ void scatter(const KParams& kp, S* __restrict__ a, co
         if (ODD && d != 0) {
             bool in;
             const unsigned t = nbr(st, cx27(d), cy27(d), cz27(d), in);
-            off = in ? (unsigned)k * N + t : off;
+            off = (!W || in) ? (unsigned)k * N + t : off;
         }
         Store<S>::st(a + off, v[k]);
     }
@@ -300,6 +302,15 @@ __host__ __device__ inline int front_xlim(int nx, int x0, int flags) {
     if (!(flags & LBM_FLAG_PERIODIC_X)) return nx;
     const int h = (nx + x0) / 2;
     return h < 1 ? 1 : h;
+}
+
+// True when no node of this block of blockDim.x x-consecutive nodes has a
+// wall neighbour (uniform over the block).
+__device__ __forceinline__ bool block_interior(const KParams& kp) {
+    const int x0 = blockIdx.x * blockDim.x, z = blockIdx.z;
+    const bool ix = (kp.flags & LBM_FLAG_PERIODIC_X) || (x0 >= 1 && x0 + (int)blockDim.x <= kp.nx - 1);
+    const bool iz = (kp.flags & LBM_FLAG_PERIODIC_Z) || (z >= 1 && z <= kp.nz - 2);
+    return ix && iz;
 }
 
 // Legacy form used by the auxiliary kernels: neighbour of (x, y, z) displaced

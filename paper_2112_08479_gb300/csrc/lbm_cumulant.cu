@@ -22,21 +22,20 @@ namespace lbmgpu {
 #ifndef LBM_CUM_MINB
 #define LBM_CUM_MINB LBM_STEP_MINB
 #endif
+#ifndef LBM_CUM_WSPLIT
+#define LBM_CUM_WSPLIT 1
+#endif
 
-template <bool ODD, bool SAVE, typename S, int SL>
-__global__ void __launch_bounds__(128, SL == 27 ? LBM_Q27_MINB : LBM_CUM_MINB) cumulant_step_kernel(KParams kp, S* __restrict__ f,
-                                                            S* __restrict__ phi,
-                                                            float* __restrict__ save) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= kp.nx) return;
-    const Stencil st = make_stencil(kp, x, blockIdx.y, blockIdx.z);
+template <bool ODD, bool SAVE, typename S, int SL, bool W>
+__device__ __forceinline__ void cumulant_step_body(const KParams& kp, S* __restrict__ f,
+                                                   S* __restrict__ phi, float* __restrict__ save,
+                                                   const Stencil& st) {
     const unsigned n = st.n;
-
     constexpr int NS = ScalarLat<SL>::NS;
     constexpr bool R32 = rest32<S, SL>();
     float fv[27], pv[NS];
-    gather<27, ODD>(kp, f, st, fv);
-    gather<NS, ODD, S, 0, R32>(kp, phi, st, pv);
+    gather<27, ODD, S, 0, false, W>(kp, f, st, fv);
+    gather<NS, ODD, S, 0, R32, W>(kp, phi, st, pv);
     if (!std::is_same<S, float>::value) {
 #pragma unroll
         for (int i = 0; i < 27; ++i) fv[i] *= kp.isf;
@@ -58,10 +57,30 @@ __global__ void __launch_bounds__(128, SL == 27 ? LBM_Q27_MINB : LBM_CUM_MINB) c
         for (int k = 0; k < NS; ++k) pv[k] *= kp.sp;
     }
     if constexpr (R32) feed_rest<S>(pv);
-    scatter<27, ODD>(kp, f, st, fv);
-    scatter<NS, ODD, S, 0, R32>(kp, phi, st, pv);
+    scatter<27, ODD, S, 0, false, W>(kp, f, st, fv);
+    scatter<NS, ODD, S, 0, R32, W>(kp, phi, st, pv);
 }
 
+// One node per thread.  On odd steps the blocks with no wall neighbour
+// (uniform per block) take a body without the wall selects (D3Q7 scalar:
+// measured 0.6-0.9 % faster; with the D3Q27 scalar the second body costs
+// registers and was 4 % slower, so that instantiation keeps one body).
+template <bool ODD, bool SAVE, typename S, int SL>
+__global__ void __launch_bounds__(128, SL == 27 ? LBM_Q27_MINB : LBM_CUM_MINB) cumulant_step_kernel(KParams kp, S* __restrict__ f,
+                                                            S* __restrict__ phi,
+                                                            float* __restrict__ save) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= kp.nx) return;
+    const Stencil st = make_stencil(kp, x, blockIdx.y, blockIdx.z);
+    if constexpr (SL == 27) {
+        cumulant_step_body<ODD, SAVE, S, SL, true>(kp, f, phi, save, st);
+    } else {
+        if (!ODD || (LBM_CUM_WSPLIT && block_interior(kp)))
+            cumulant_step_body<ODD, SAVE, S, SL, false>(kp, f, phi, save, st);
+        else
+            cumulant_step_body<ODD, SAVE, S, SL, true>(kp, f, phi, save, st);
+    }
+}
 
 template <typename S, int SL>
 static cudaError_t launch_cumulant_typed(const KParams& kp, bool odd, S* f, S* phi, float* save,

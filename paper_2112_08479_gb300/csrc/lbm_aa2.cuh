@@ -111,6 +111,14 @@ __device__ __forceinline__ Stencil2 make_stencil2(const KParams& kp, int x, int 
     return s;
 }
 
+// True when every node pair of this block is active and has all its
+// neighbours inside the box (x - 1 >= 0, x + 2 <= nx - 1, 1 <= z <= nz - 2):
+// the condition of the FAST accesses below, uniform over the block.
+__device__ __forceinline__ bool block_interior2(const KParams& kp) {
+    const int x0 = 2 * blockIdx.x * blockDim.x, z = blockIdx.z;
+    return x0 >= 1 && x0 + 2 * (int)blockDim.x <= kp.nx - 1 && z >= 1 && z <= kp.nz - 2;
+}
+
 // The gather runs in three phases so that no shuffle waits on a load issued
 // after it: (1) every aligned pair load, (2) the edge lanes' single-element
 // loads, predicated, (3) the shuffles that hand the shifted element across.
@@ -119,10 +127,18 @@ __device__ __forceinline__ Stencil2 make_stencil2(const KParams& kp, int x, int 
 // R32: population 0 (direction 0) lives in the FP32 rest row (rest_row).
 // ZW: the node pair may lie next to a z wall; false for the z-interior rows,
 // which then skip the wall selects (every z neighbour is in the fluid).
-template <int Q, bool ODD, typename S, int D0 = 0, bool R32 = false, bool ZW = true>
+// FAST (odd steps of blocks whose every node has all its neighbours in the
+// fluid and every lane active): the x-shifted populations are read and
+// written as two single elements per thread, x + dx and x + 1 + dx, instead
+// of an aligned pair, a shuffle and the warp-edge element.  Each node still
+// reads and writes exactly the elements it owns in the AA step, so the
+// in-place update stays race-free.
+template <int Q, bool ODD, typename S, int D0 = 0, bool R32 = false, bool ZW = true,
+          bool FAST = false>
 __device__ __forceinline__ void gather2(const KParams& kp, const S* __restrict__ a,
                                         const Stencil2& st, float (&v0)[Q], float (&v1)[Q]) {
     const unsigned N = kp.N;
+    constexpr bool ZWe = ZW && !FAST;
     float P0[Q], P1[Q], E[Q];
 #pragma unroll
     for (int k = 0; k < Q; ++k) {
@@ -134,9 +150,15 @@ __device__ __forceinline__ void gather2(const KParams& kp, const S* __restrict__
         }
         unsigned off = (unsigned)k * N + st.n;
         if (ODD && i != 0) {
-            const int dy = -cy27(i), dz = -cz27(i);
+            const int dx = -cx27(i), dy = -cy27(i), dz = -cz27(i);
             const unsigned row = (unsigned)(opp(i) - D0) * N + st.zr[dz + 1] + st.yr[dy + 1];
-            off = (!ZW || st.zo[dz + 1]) ? row + st.x : off;
+            if (FAST && dx != 0) {
+                const unsigned e = row + st.x + (unsigned)dx;
+                P0[k] = Store<S>::ld(a + e);
+                P1[k] = Store<S>::ld(a + e + 1);
+                continue;
+            }
+            off = (!ZWe || st.zo[dz + 1]) ? row + st.x : off;
         }
         P0[k] = 0.0f; P1[k] = 0.0f;
         if (st.active) PairIO<S>::ld(a + off, P0[k], P1[k]);
@@ -146,14 +168,14 @@ __device__ __forceinline__ void gather2(const KParams& kp, const S* __restrict__
         const int i = k + D0;
         E[k] = 0.0f;
         const int dx = -cx27(i), dy = -cy27(i), dz = -cz27(i);
-        if (ODD && i != 0 && dx != 0) {
+        if (ODD && !FAST && i != 0 && dx != 0) {
             const unsigned row = (unsigned)(opp(i) - D0) * N + st.zr[dz + 1] + st.yr[dy + 1];
             const unsigned own = (unsigned)k * N + st.n;
             unsigned off;
             bool need;
             if (dx < 0) { need = st.left; off = st.xmo ? row + st.xm : own; }
             else { need = st.right; off = st.xp2o ? row + st.xp2 : own + 1; }
-            need = need && st.active && (!ZW || st.zo[dz + 1]);
+            need = need && st.active && (!ZWe || st.zo[dz + 1]);
             if (need) E[k] = Store<S>::ld(a + off);
         }
     }
@@ -162,8 +184,8 @@ __device__ __forceinline__ void gather2(const KParams& kp, const S* __restrict__
         const int i = k + D0;
         const int dx = -cx27(i), dz = -cz27(i);
         v0[k] = P0[k]; v1[k] = P1[k];
-        if (ODD && i != 0 && dx != 0) {
-            const bool in = !ZW || st.zo[dz + 1];
+        if (ODD && !FAST && i != 0 && dx != 0) {
+            const bool in = !ZWe || st.zo[dz + 1];
             if (dx < 0) {
                 // node x needs element x - 1, node x + 1 needs element x
                 const float e = __shfl_up_sync(0xffffffffu, P1[k], 1);
@@ -182,18 +204,20 @@ __device__ __forceinline__ void gather2(const KParams& kp, const S* __restrict__
 // The scatter first exchanges the shifted elements, then issues every store
 // under a predicate (pair stores for the interior lanes, single-element
 // stores for the edge lanes, pair stores into the own slots at a z wall).
-template <int Q, bool ODD, typename S, int D0 = 0, bool R32 = false, bool ZW = true>
+template <int Q, bool ODD, typename S, int D0 = 0, bool R32 = false, bool ZW = true,
+          bool FAST = false>
 __device__ __forceinline__ void scatter2(const KParams& kp, S* __restrict__ a, const Stencil2& st,
                                          const float (&v0)[Q], const float (&v1)[Q]) {
     const unsigned N = kp.N;
+    constexpr bool ZWe = ZW && !FAST;
     float X[Q];
 #pragma unroll
     for (int k = 0; k < Q; ++k) {
         const int i = k + D0;
         const int dx = cx27(i);
         X[k] = 0.0f;
-        if (ODD && i != 0 && dx > 0) X[k] = __shfl_up_sync(0xffffffffu, v1[k], 1);
-        if (ODD && i != 0 && dx < 0) X[k] = __shfl_down_sync(0xffffffffu, v0[k], 1);
+        if (ODD && !FAST && i != 0 && dx > 0) X[k] = __shfl_up_sync(0xffffffffu, v1[k], 1);
+        if (ODD && !FAST && i != 0 && dx < 0) X[k] = __shfl_down_sync(0xffffffffu, v0[k], 1);
     }
 #pragma unroll
     for (int k = 0; k < Q; ++k) {
@@ -208,8 +232,14 @@ __device__ __forceinline__ void scatter2(const KParams& kp, S* __restrict__ a, c
             if (st.active) PairIO<S>::st(a + own, v0[k], v1[k]);
             continue;
         }
-        const bool in = !ZW || st.zo[dz + 1];
+        const bool in = !ZWe || st.zo[dz + 1];
         const unsigned row = (unsigned)k * N + st.zr[dz + 1] + st.yr[dy + 1];
+        if (FAST && dx != 0) {
+            const unsigned e = row + st.x + (unsigned)dx;
+            Store<S>::st(a + e, v0[k]);
+            Store<S>::st(a + e + 1, v1[k]);
+            continue;
+        }
         if (st.active && !in) PairIO<S>::st(a + own, v0[k], v1[k]);
         if (dx == 0) {
             if (st.active && in) PairIO<S>::st(a + row + st.x, v0[k], v1[k]);

@@ -59,6 +59,9 @@ __global__ void __launch_bounds__(128, LBM_STEP_MINB) bgk_step_kernel(KParams kp
 #ifndef LBM_BGK_ZSPLIT
 #define LBM_BGK_ZSPLIT 1
 #endif
+#ifndef LBM_BGK_FAST
+#define LBM_BGK_FAST 1
+#endif
 
 // The 16-bit instantiations are issue-bound rather than HBM-bound, so they
 // may trade registers for resident warps differently (LBM_STEP2_MINB16).
@@ -66,15 +69,15 @@ __global__ void __launch_bounds__(128, LBM_STEP_MINB) bgk_step_kernel(KParams kp
 #define LBM_STEP2_MINB16 LBM_STEP2_MINB
 #endif
 
-template <bool ODD, bool SAVE, typename S, int SL, bool ZW>
+template <bool ODD, bool SAVE, typename S, int SL, bool ZW, bool FAST>
 __device__ __forceinline__ void bgk_step2_body(const KParams& kp, S* __restrict__ f,
                                                S* __restrict__ phi, float* __restrict__ save,
                                                const Stencil2& st) {
     constexpr int NS = ScalarLat<SL>::NS, D0 = ScalarLat<SL>::D0;
     constexpr bool R32 = rest32<S, SL>();
     float f0[19], f1[19], p0[NS], p1[NS];
-    gather2<19, ODD, S, 0, false, ZW>(kp, f, st, f0, f1);
-    gather2<NS, ODD, S, D0, R32, ZW>(kp, phi, st, p0, p1);
+    gather2<19, ODD, S, 0, false, ZW, FAST>(kp, f, st, f0, f1);
+    gather2<NS, ODD, S, D0, R32, ZW, FAST>(kp, phi, st, p0, p1);
     constexpr bool s16 = !std::is_same<S, float>::value;   // populations in storage units
     if (SAVE && st.active) {
         const unsigned N = kp.N;
@@ -92,8 +95,8 @@ __device__ __forceinline__ void bgk_step2_body(const KParams& kp, S* __restrict_
         collide_bgk<s16, SL>(kp, f1, p1);
     }
     if constexpr (R32) feed_rest2<S>(p0, p1);
-    scatter2<19, ODD, S, 0, false, ZW>(kp, f, st, f0, f1);
-    scatter2<NS, ODD, S, D0, R32, ZW>(kp, phi, st, p0, p1);
+    scatter2<19, ODD, S, 0, false, ZW, FAST>(kp, f, st, f0, f1);
+    scatter2<NS, ODD, S, D0, R32, ZW, FAST>(kp, phi, st, p0, p1);
 }
 
 // Two x-adjacent nodes per thread (nx even): paired population accesses, see
@@ -109,8 +112,11 @@ __global__ void __launch_bounds__(128, std::is_same<S, float>::value ? LBM_STEP2
     const int z = blockIdx.z;
     const bool zwall = ODD && (!LBM_BGK_ZSPLIT ||
                                (!(kp.flags & LBM_FLAG_PERIODIC_Z) && (z == 0 || z == kp.nz - 1)));
-    if (!ODD || !zwall) bgk_step2_body<ODD, SAVE, S, SL, false>(kp, f, phi, save, st);
-    else bgk_step2_body<ODD, SAVE, S, SL, true>(kp, f, phi, save, st);
+    if (!ODD) bgk_step2_body<ODD, SAVE, S, SL, false, false>(kp, f, phi, save, st);
+    else if (LBM_BGK_FAST && block_interior2(kp))
+        bgk_step2_body<ODD, SAVE, S, SL, false, true>(kp, f, phi, save, st);
+    else if (!zwall) bgk_step2_body<ODD, SAVE, S, SL, false, false>(kp, f, phi, save, st);
+    else bgk_step2_body<ODD, SAVE, S, SL, true, false>(kp, f, phi, save, st);
 }
 
 template <typename S, int SL>

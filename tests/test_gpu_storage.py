@@ -113,7 +113,7 @@ def test_lock_exchange_runs_close_to_oracle(storage):
 @pytest.mark.parametrize("storage", [lbm.LBM_FP16S, lbm.LBM_BF16S])
 @pytest.mark.parametrize("model,scalar", [(0, lbm.LBM_SCALAR_Q7), (1, lbm.LBM_SCALAR_Q7),
                                           (1, lbm.LBM_SCALAR_Q27)])
-@pytest.mark.parametrize("nx", [33, 34])
+@pytest.mark.parametrize("nx", [33, 34, 1030])
 def test_fp32_rest_row_is_not_rounded(storage, model, scalar, nx):
     """Collision off: the scalar's rest population, held in FP32, passes even
     and odd steps (one- and two-node kernels) bit for bit, while the moving

@@ -36,21 +36,23 @@ __device__ __forceinline__ void cumulant_step_body(const KParams& kp, S* __restr
     float fv[27], pv[NS];
     gather<27, ODD, S, 0, false, W>(kp, f, st, fv);
     gather<NS, ODD, S, 0, R32, W>(kp, phi, st, pv);
-    if (!std::is_same<S, float>::value) {
+    constexpr bool s16 = !std::is_same<S, float>::value;   // populations in storage units
+    constexpr bool fold = s16 && SL == 7;                  // the collision applies the scales
+    if (SAVE) {
+        const size_t N = kp.N;
+#pragma unroll
+        for (int i = 0; i < 27; ++i) save[(size_t)i * N + n] = s16 ? fv[i] * kp.isf : fv[i];
+#pragma unroll
+        for (int k = 0; k < NS; ++k) save[(size_t)(27 + k) * N + n] = s16 ? pv[k] * kp.isp : pv[k];
+    }
+    if (s16 && !fold) {
 #pragma unroll
         for (int i = 0; i < 27; ++i) fv[i] *= kp.isf;
 #pragma unroll
         for (int k = 0; k < NS; ++k) pv[k] *= kp.isp;
     }
-    if (SAVE) {
-        const size_t N = kp.N;
-#pragma unroll
-        for (int i = 0; i < 27; ++i) save[(size_t)i * N + n] = fv[i];
-#pragma unroll
-        for (int k = 0; k < NS; ++k) save[(size_t)(27 + k) * N + n] = pv[k];
-    }
-    if (!(kp.flags & LBM_FLAG_NO_COLLIDE)) collide_cumulant<SL>(kp, fv, pv);
-    if (!std::is_same<S, float>::value) {
+    if (!(kp.flags & LBM_FLAG_NO_COLLIDE)) collide_cumulant<SL, fold>(kp, fv, pv);
+    if (s16 && !fold) {
 #pragma unroll
         for (int i = 0; i < 27; ++i) fv[i] *= kp.sf;
 #pragma unroll

@@ -52,14 +52,19 @@ __host__ __device__ constexpr int dir27(int x, int y, int z) {
 }
 
 // SL: scalar lattice, D3Q7 BGK or D3Q27 factorized central moments.
-template <int SL = 7>
+// SCALED (16-bit storage, D3Q7 scalar): f and p hold the storage units
+// scale_f (f - w) and scale_phi (Phi - w); the scales are applied to the few
+// moments and output coefficients instead of to every population.
+template <int SL = 7, bool SCALED = false>
 __device__ __forceinline__ void collide_cumulant(const KParams& kp, float (&f)[27],
                                                  float (&p)[ScalarLat<SL>::NS]) {
     static_assert(SL == 7 || SL == 27, "the cumulant model runs with the D3Q7 or D3Q27 scalar");
+    static_assert(!(SCALED && SL == 27), "the D3Q27 scalar takes unscaled populations");
     constexpr int NS = ScalarLat<SL>::NS;
-    float chit = 0.0f;  // chi - 1 (Phi is held as Phi - w)
+    float chs = 0.0f;  // chi - 1 in storage units (Phi is held as Phi - w)
 #pragma unroll
-    for (int k = 0; k < NS; ++k) chit += p[k];
+    for (int k = 0; k < NS; ++k) chs += p[k];
+    const float chit = SCALED ? chs * kp.isp : chs;
     const float chi = 1.0f + chit;
     const float Fx = kp.gx * chi, Fy = kp.gy * chi, Fz = kp.gz * chi;
 
@@ -75,6 +80,10 @@ __device__ __forceinline__ void collide_cumulant(const KParams& kp, float (&f)[2
         if (cx27(i) * cy27(i)) mxy += cx27(i) * cy27(i) * v;
         if (cx27(i) * cz27(i)) mxz += cx27(i) * cz27(i) * v;
         if (cy27(i) * cz27(i)) myz += cy27(i) * cz27(i) * v;
+    }
+    if (SCALED) {
+        drho *= kp.isf; jx *= kp.isf; jy *= kp.isf; jz *= kp.isf;
+        mxx *= kp.isf; myy *= kp.isf; mzz *= kp.isf; mxy *= kp.isf; mxz *= kp.isf; myz *= kp.isf;
     }
     const float rho = 1.0f + drho;
     const float irho = 1.0f / rho;
@@ -134,18 +143,19 @@ __device__ __forceinline__ void collide_cumulant(const KParams& kp, float (&f)[2
         for (int c = 0; c < 3; ++c)
             axis_inverse(R[a] * W1[c], uy, A[a][0][c], A[a][1][c], A[a][2][c], B[a][0][c],
                          B[a][1][c], B[a][2][c]);
+    // f*_i - w_i = drho w_i + rho (P_i - w_i), in storage units when SCALED
+    const float ds = SCALED ? drho * kp.sf : drho, rs = SCALED ? rho * kp.sf : rho;
 #pragma unroll
     for (int b = 0; b < 3; ++b)
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             float pm, p0, pp;
             axis_inverse(W1[b] * W1[c], ux, B[0][b][c], B[1][b][c], B[2][b][c], pm, p0, pp);
-            // f*_i - w_i = drho w_i + rho (P_i - w_i)
             const int im = dir27(-1, b - 1, c - 1), i0 = dir27(0, b - 1, c - 1),
                       ip = dir27(1, b - 1, c - 1);
-            f[im] = drho * w27(im) + rho * pm;
-            f[i0] = drho * w27(i0) + rho * p0;
-            f[ip] = drho * w27(ip) + rho * pp;
+            f[im] = ds * w27(im) + rs * pm;
+            f[i0] = ds * w27(i0) + rs * p0;
+            f[ip] = ds * w27(ip) + rs * pp;
         }
 
     const float hx = (jx + 0.5f * Fx) * irho, hy = (jy + 0.5f * Fy) * irho,
@@ -155,7 +165,7 @@ __device__ __forceinline__ void collide_cumulant(const KParams& kp, float (&f)[2
         // non-equilibrium form whose parts sum to zero, so sum Phi is conserved
         // up to the rounding of the stored results (see collide_bgk)
         const float omp = 1.0f / kp.taup0;
-        const float pe = w7(1) * chit, pa = w7(1) * 4.0f * chi;
+        const float pe = w7(1) * chs, pa = (SCALED ? kp.sp : 1.0f) * w7(1) * 4.0f * chi;
         float nq[7];
         nq[1] = p[1] - (pe + pa * hx);
         nq[2] = p[2] - (pe - pa * hx);

@@ -29,7 +29,8 @@ namespace lbmgpu {
 //
 // SCALED: f and p hold the 16-bit storage units scale_f (f - w) and
 // scale_phi (Phi - w); the scales are applied to the few moments and output
-// terms instead of to every population.
+// terms instead of to every population, and the divisions and square roots
+// use the hardware approximations (crcp, cdiv, csqrt).
 //
 // SL: scalar lattice, D3Q7 (c_s^2 = 1/4) or D3Q6 (Eq. 29-31 as printed,
 // c_s^2 = 1/3, w = 1/6, no rest population).
@@ -65,7 +66,7 @@ __device__ __forceinline__ void collide_bgk(const KParams& kp, float (&f)[19],
         mxx *= isf; myy *= isf; mzz *= isf; mxy *= isf; mxz *= isf; myz *= isf;
     }
     const float rho = 1.0f + drho;
-    const float irho = 1.0f / rho;
+    const float irho = crcp<SCALED>(rho);
     const float ux = (jx + 0.5f * Fx) * irho;
     const float uy = (jy + 0.5f * Fy) * irho;
     const float uz = (jz + 0.5f * Fz) * irho;
@@ -79,13 +80,13 @@ __device__ __forceinline__ void collide_bgk(const KParams& kp, float (&f)[19],
     const float pxy = mxy - rho * ux * uy;
     const float pxz = mxz - rho * ux * uz;
     const float pyz = myz - rho * uy * uz;
-    const float q = sqrtf(pxx * pxx + pyy * pyy + pzz * pzz +
+    const float q = csqrt<SCALED>(pxx * pxx + pyy * pyy + pzz * pzz +
                           2.0f * (pxy * pxy + pxz * pxz + pyz * pyz));
     // tau - tau0 without cancellation: X / (2 (s + tau0)), s = sqrt(tau0^2 + X)
     const float X = kp.A * q * irho;
-    const float s = sqrtf(kp.tau0 * kp.tau0 + X);
-    const float dtau = 0.5f * X / (s + kp.tau0);
-    const float om = 1.0f / (kp.tau0 + dtau);
+    const float s = csqrt<SCALED>(kp.tau0 * kp.tau0 + X);
+    const float dtau = cdiv<SCALED>(0.5f * X, s + kp.tau0);
+    const float om = crcp<SCALED>(kp.tau0 + dtau);
     const float keep = 1.0f - om;
     const float guo = 1.0f - 0.5f * om;
     const float uF = ux * Fx + uy * Fy + uz * Fz;
@@ -113,7 +114,7 @@ __device__ __forceinline__ void collide_bgk(const KParams& kp, float (&f)[19],
         f[i + 1] = fmaf(keep, f[i + 1], even - odd);
     }
 
-    const float omp = 1.0f / (kp.taup0 + kp.kT * dtau);
+    const float omp = crcp<SCALED>(kp.taup0 + kp.kT * dtau);
     if constexpr (SL == 7) {
         // scalar: Phi_eq - w = w (chi - 1 + 4 chi c.u).  Only the non-equilibrium
         // parts are relaxed, and the rest population's part closes their sum to

@@ -333,6 +333,19 @@ __device__ __forceinline__ bool neighbour(const KParams& kp, int x, int y, int z
 }
 
 // ---------------------------------------------------------------------------
+// Reciprocal, quotient and square root inside the collisions: IEEE-rounded
+// on the FP32 path, the hardware approximations (relative error about 1e-7)
+// where the results are rounded to 16-bit storage (2^-11 or 2^-8) anyway.
+template <bool APPROX>
+__device__ __forceinline__ float crcp(float x) { return APPROX ? __fdividef(1.0f, x) : 1.0f / x; }
+template <bool APPROX>
+__device__ __forceinline__ float cdiv(float a, float b) { return APPROX ? __fdividef(a, b) : a / b; }
+template <bool APPROX>
+__device__ __forceinline__ float csqrt(float x) {
+    return APPROX ? (x > 0.0f ? x * rsqrtf(x) : 0.0f) : sqrtf(x);
+}
+
+// ---------------------------------------------------------------------------
 // Error-free transformation used by the compensated FP32 sums.
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     s = __fadd_rn(a, b);

@@ -86,7 +86,7 @@ __device__ __forceinline__ void collide_cumulant(const KParams& kp, float (&f)[2
         mxx *= kp.isf; myy *= kp.isf; mzz *= kp.isf; mxy *= kp.isf; mxz *= kp.isf; myz *= kp.isf;
     }
     const float rho = 1.0f + drho;
-    const float irho = 1.0f / rho;
+    const float irho = crcp<SCALED>(rho);
     // pre-collision mean velocity and second-order cumulants (deviation of
     // the diagonal from 1/3): C_aa - 1/3 = (M_aa - drho/3)/rho - v_a^2
     const float vx = jx * irho, vy = jy * irho, vz = jz * irho;

@@ -126,6 +126,7 @@ KParams kparams(const lbm_params* p) {
     k.sp = s16 ? (float)p->scale_phi : 1.0f;
     k.isp = 1.0f / k.sp;
     k.nu = (float)p->nu;
+    k.omp0 = (float)(1.0 / (0.5 + p->D / cs2));
     return k;
 }
 

@@ -89,6 +89,7 @@ struct KParams {
     float sf, isf;       // storage scale of f - w and its inverse
     float sp, isp;       // storage scale of Phi and its inverse
     float nu;            // molecular viscosity (wall friction, Eq. 62)
+    float omp0;          // 1 / taup0: the scalar rate of the cumulant model (molecular D)
 };
 
 // ---------------------------------------------------------------------------

@@ -164,7 +164,7 @@ __device__ __forceinline__ void collide_cumulant(const KParams& kp, float (&f)[2
         // scalar (Eq. 28-30) with the half-force velocity and the molecular D;
         // non-equilibrium form whose parts sum to zero, so sum Phi is conserved
         // up to the rounding of the stored results (see collide_bgk)
-        const float omp = 1.0f / kp.taup0;
+        const float omp = kp.omp0;
         const float pe = w7(1) * chs, pa = (SCALED ? kp.sp : 1.0f) * w7(1) * 4.0f * chi;
         float nq[7];
         nq[1] = p[1] - (pe + pa * hx);

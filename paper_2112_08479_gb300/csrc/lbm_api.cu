@@ -126,7 +126,9 @@ KParams kparams(const lbm_params* p) {
     k.sp = s16 ? (float)p->scale_phi : 1.0f;
     k.isp = 1.0f / k.sp;
     k.nu = (float)p->nu;
-    k.omp0 = (float)(1.0 / (0.5 + p->D / cs2));
+    // the correctly rounded FP32 quotient, bit-identical to 1.0f / taup0 on
+    // the device, so that a kernel may take either form
+    k.omp0 = 1.0f / k.taup0;
     return k;
 }
 

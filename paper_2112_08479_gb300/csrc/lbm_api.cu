@@ -59,7 +59,8 @@ const char* check(const lbm_params* p) {
         return "(Q+NS)*nx*ny*nz must be < 2^32 (32-bit element offsets)";
     if (p->storage != LBM_FP32 && p->storage != LBM_FP16S && p->storage != LBM_BF16S)
         return "unknown storage";
-    if (p->flags & ~(LBM_FLAG_NO_COLLIDE | LBM_FLAG_PERIODIC_X | LBM_FLAG_PERIODIC_Z))
+    if (p->flags & ~(LBM_FLAG_NO_COLLIDE | LBM_FLAG_PERIODIC_X | LBM_FLAG_PERIODIC_Z |
+                     LBM_FLAG_ONE_NODE))
         return "unknown flag bits";
     if (!finite(p->nu) || p->nu <= 0.0) return "nu must be finite and > 0";
     if (!finite(p->D) || p->D <= 0.0) return "D must be finite and > 0";

@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(128, std::is_same<S, float>::value ? LBM_STEP2
 template <typename S, int SL>
 static cudaError_t launch_bgk_typed(const KParams& kp, bool odd, S* f, S* phi, float* save,
                                    cudaStream_t st) {
-    if constexpr (LBM_BGK_PAIR) if (kp.nx % 2 == 0) {
+    if constexpr (LBM_BGK_PAIR) if (kp.nx % 2 == 0 && !(kp.flags & LBM_FLAG_ONE_NODE)) {
         dim3 block(128), grid((kp.nx / 2 + 127) / 128, kp.ny, kp.nz);
         if (save) {
             if (odd) bgk_step2_kernel<true, true, S, SL><<<grid, block, 0, st>>>(kp, f, phi, save);

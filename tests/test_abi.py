@@ -65,6 +65,13 @@ def test_validate_rejects(lib, field, value):
     assert lbm.lbm_workspace_bytes(p) == 0
 
 
+def test_one_node_flag_accepted(lib):
+    """LBM_FLAG_ONE_NODE (a test hook selecting the one-node step kernels)
+    combines with the geometry flags."""
+    flags = lbm.LBM_FLAG_ONE_NODE | lbm.LBM_FLAG_PERIODIC_X | lbm.LBM_FLAG_PERIODIC_Z
+    assert lbm.lbm_validate(_good(flags=flags)) == lbm.LBM_OK
+
+
 def test_scalar_lattice_pairs(lib):
     """BGK runs with D3Q7 or D3Q6, the cumulant model with D3Q7 or D3Q27."""
     assert lbm.lbm_validate(_good(scalar=lbm.LBM_SCALAR_Q6)) == lbm.LBM_OK

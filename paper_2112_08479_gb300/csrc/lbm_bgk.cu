@@ -119,9 +119,114 @@ __global__ void __launch_bounds__(128, std::is_same<S, float>::value ? LBM_STEP2
     else bgk_step2_body<ODD, SAVE, S, SL, true, false>(kp, f, phi, save, st);
 }
 
+#ifndef LBM_BGK_QUAD
+#define LBM_BGK_QUAD 1
+#endif
+#ifndef LBM_STEP4_MINB
+#define LBM_STEP4_MINB 3
+#endif
+
+// Two 16-bit values packed in a 32-bit word: the lower node in the low half
+// (hi = 0), the upper in the high half (hi = 1).
+template <typename S> struct Half16;
+template <> struct Half16<__half> {
+    static __device__ __forceinline__ float get(unsigned w, int hi) {
+        return __half2float(__ushort_as_half((unsigned short)(hi ? w >> 16 : w & 0xffffu)));
+    }
+    static __device__ __forceinline__ unsigned bits(float v) {
+        return __half_as_ushort(__float2half_rn(v));
+    }
+};
+template <> struct Half16<__nv_bfloat16> {
+    static __device__ __forceinline__ float get(unsigned w, int hi) {
+        return __uint_as_float(hi ? w & 0xffff0000u : w << 16);   // exact widening
+    }
+    static __device__ __forceinline__ unsigned bits(float v) {
+        return __bfloat16_as_ushort(__float2bfloat16_rn(v));
+    }
+};
+// w with its low (hi = 0) or high (hi = 1) half replaced by the low half of b.
+__device__ __forceinline__ unsigned put16(unsigned w, unsigned b, int hi) {
+    return __byte_perm(w, b, hi ? 0x5410 : 0x3254);
+}
+
+// Even steps with 16-bit storage and nx a multiple of 4: four x-adjacent
+// nodes per thread, each population row moved as one aligned 8-byte word
+// (a warp reads and writes 256-byte row segments, as the FP32 pair kernel
+// does, against 128 for 16-bit pairs).  Even steps are local (slot i of node
+// n is read, slot opp(i) of the same node written), so the words need no
+// shifting; the four nodes are unpacked, collided and packed back one at a
+// time.  Same arithmetic per node as bgk_step_kernel.  Odd steps stay with
+// bgk_step2_kernel: there the x-shifted rows of a packed quad need shuffles
+// and byte permutes and measured slower than the paired form.
+template <typename S, int SL>
+__global__ void __launch_bounds__(128, LBM_STEP4_MINB) bgk_even4_kernel(KParams kp, S* __restrict__ f,
+                                                                       S* __restrict__ phi) {
+    const unsigned x = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (x >= (unsigned)kp.nx) return;
+    constexpr int NS = ScalarLat<SL>::NS, D0 = ScalarLat<SL>::D0;
+    constexpr bool R32 = rest32<S, SL>();
+    const unsigned N = kp.N;
+    const unsigned n = blockIdx.z * kp.nxny + blockIdx.y * kp.nx + x;
+    uint2* __restrict__ fw = reinterpret_cast<uint2*>(f);
+    uint2* __restrict__ pw = reinterpret_cast<uint2*>(phi);
+    float4* __restrict__ rest = reinterpret_cast<float4*>(rest_row(phi, NS, N) + n);
+    uint2 wf[19], wp[NS];
+    float4 r = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll
+    for (int i = 0; i < 19; ++i) wf[i] = ld_pop(fw + (((unsigned)i * N + n) >> 2));
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+        if (R32 && k == 0) r = ld_pop(rest);
+        else wp[k] = ld_pop(pw + (((unsigned)k * N + n) >> 2));
+    }
+    const bool collide = !(kp.flags & LBM_FLAG_NO_COLLIDE);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {       // node x + j: word half j / 2, 16-bit half j % 2
+        float fv[19], pv[NS];
+#pragma unroll
+        for (int i = 0; i < 19; ++i) fv[i] = Half16<S>::get(j < 2 ? wf[i].x : wf[i].y, j & 1);
+#pragma unroll
+        for (int k = 0; k < NS; ++k) {
+            if (R32 && k == 0) pv[0] = j == 0 ? r.x : j == 1 ? r.y : j == 2 ? r.z : r.w;
+            else pv[k] = Half16<S>::get(j < 2 ? wp[k].x : wp[k].y, j & 1);
+        }
+        if (collide) collide_bgk<true, SL>(kp, fv, pv);
+        if constexpr (R32) feed_rest<S>(pv);
+#pragma unroll
+        for (int i = 0; i < 19; ++i) {
+            unsigned& w = j < 2 ? wf[i].x : wf[i].y;
+            w = put16(w, Half16<S>::bits(fv[i]), j & 1);
+        }
+#pragma unroll
+        for (int k = 0; k < NS; ++k) {
+            if (R32 && k == 0) {
+                (j == 0 ? r.x : j == 1 ? r.y : j == 2 ? r.z : r.w) = pv[0];
+            } else {
+                unsigned& w = j < 2 ? wp[k].x : wp[k].y;
+                w = put16(w, Half16<S>::bits(pv[k]), j & 1);
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 19; ++i) st_pop(fw + (((unsigned)opp(i) * N + n) >> 2), wf[i]);
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+        if (R32 && k == 0) st_pop(rest, r);
+        else st_pop(pw + (((unsigned)(opp(k + D0) - D0) * N + n) >> 2), wp[k]);
+    }
+}
+
 template <typename S, int SL>
 static cudaError_t launch_bgk_typed(const KParams& kp, bool odd, S* f, S* phi, float* save,
                                    cudaStream_t st) {
+    if constexpr (LBM_BGK_QUAD && !std::is_same<S, float>::value) {
+        if (!odd && !save && kp.nx % 4 == 0 && !(kp.flags & LBM_FLAG_ONE_NODE)) {
+            dim3 block(128), grid((kp.nx / 4 + 127) / 128, kp.ny, kp.nz);
+            bgk_even4_kernel<S, SL><<<grid, block, 0, st>>>(kp, f, phi);
+            return cudaGetLastError();
+        }
+    }
     if constexpr (LBM_BGK_PAIR) if (kp.nx % 2 == 0 && !(kp.flags & LBM_FLAG_ONE_NODE)) {
         dim3 block(128), grid((kp.nx / 2 + 127) / 128, kp.ny, kp.nz);
         if (save) {

@@ -1,10 +1,12 @@
 """The two-node step kernels against the one-node kernels.
 
 With nx even the BGK step runs two x-adjacent nodes per thread, with paired
-FP32 / 16-bit accesses and, on odd steps, the block-uniform wall-free and
-interior bodies.  LBM_FLAG_ONE_NODE selects the one-node kernel.  Cases: x and z walls,
-periodic ends, warp and block edges (nx = 770: three blocks of 128 pairs,
-the middle one wholly interior), both scalar lattices of the BGK fluid.
+FP32 accesses and, on odd steps, the block-uniform wall-free and interior
+bodies; with 16-bit storage and nx a multiple of 4 it runs four nodes per
+thread on packed 8-byte words (nx = 34 and 770 take the two-node form).
+LBM_FLAG_ONE_NODE selects the one-node kernel.  Cases: x and z walls,
+periodic ends, warp and block edges (nx = 770, 1028: three blocks, the
+middle one wholly interior), both scalar lattices of the BGK fluid.
 
 Pure streaming (collisions off) moves stored values only, so the two must
 agree bit for bit: this checks every index, wall and edge path.  With
@@ -62,7 +64,7 @@ def _params(model, storage, scalar, geometry, nx, extra=0):
 
 @pytest.mark.parametrize("geometry", sorted(GEOMETRIES))
 @pytest.mark.parametrize("model,storage,scalar", CASES)
-@pytest.mark.parametrize("nx", [34, 770])
+@pytest.mark.parametrize("nx", [34, 36, 770, 1028])
 def test_streaming_matches_one_node_exactly(model, storage, scalar, geometry, nx):
     p2, p1 = _params(model, storage, scalar, geometry, nx, lbm.LBM_FLAG_NO_COLLIDE)
     s0 = _state(p2, 11)
@@ -78,7 +80,7 @@ def test_streaming_matches_one_node_exactly(model, storage, scalar, geometry, nx
 
 @pytest.mark.parametrize("geometry", sorted(GEOMETRIES))
 @pytest.mark.parametrize("model,storage,scalar", CASES)
-@pytest.mark.parametrize("nx", [34, 770])
+@pytest.mark.parametrize("nx", [34, 36, 770, 1028])
 def test_collision_steps_match_one_node(model, storage, scalar, geometry, nx):
     p2, p1 = _params(model, storage, scalar, geometry, nx)
     s = _state(p2, 11)

@@ -385,6 +385,8 @@ def run_ours(args, ws, rank, local):
     achieved = bpn * N / kern / 1e9
     headline = (args.model, args.storage) == ("bgk", "fp32") and args.workload == "config3"
     kname = "bgk_step2_kernel" if args.model == "bgk" and WORKLOAD["nx"] % 2 == 0 else f"{args.model}_step_kernel"
+    if args.model == "bgk" and args.storage != "fp32" and WORKLOAD["nx"] % 4 == 0:
+        kname = "bgk_even4_kernel + bgk_step2_kernel"
     roof = {"bound": "hbm",
             "kernel": f"{kname} (AA even/odd, {args.storage.upper()})",
             "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
@@ -396,6 +398,7 @@ def run_ours(args, ws, rank, local):
         variants = {}
         for model, storage, scalar in (("bgk", "fp16s", "q7"), ("bgk", "bf16s", "q7"),
                                        ("cumulant", "fp32", "q7"), ("cumulant", "fp16s", "q7"),
+                                       ("cumulant", "bf16s", "q7"),
                                        ("bgk", "fp32", "q6"), ("cumulant", "fp32", "q27")):
             r = side_variant(torch, model, storage, scalar)
             r["hbm_frac"] = r.pop("achieved_gbs") / peak

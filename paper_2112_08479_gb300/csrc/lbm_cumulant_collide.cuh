@@ -30,15 +30,16 @@ namespace lbmgpu {
 // values s * (1, 0, 1/3) plus the deviations (d0, d1, d2); the populations at
 // c = -1, 0, +1 are the rest values s * (1/6, 2/3, 1/6) plus the returned
 // deviations:
-//   p(0)  = d0 - (s + d0) v^2 - 2 v d1 - d2
-//   p(+-) = ((v^2 +- v)(s + d0) + (2 v +- 1) d1 + d2) / 2
+//   p(0)  = d0 - (s + d0) v^2 - 2 v d1 - d2 = d0 - a
+//   p(+-) = ((v^2 +- v)(s + d0) + (2 v +- 1) d1 + d2) / 2 = (a +- b) / 2
+// with a = (s + d0) v^2 + 2 v d1 + d2 and b = (s + d0) v + d1.
 __device__ __forceinline__ void axis_inverse(float s, float v, float d0, float d1, float d2,
                                              float& pm, float& p0, float& pp) {
     const float k0 = s + d0;
     const float v2 = v * v;
-    p0 = d0 - k0 * v2 - 2.0f * v * d1 - d2;
     const float a = v2 * k0 + 2.0f * v * d1 + d2;
     const float b = v * k0 + d1;
+    p0 = d0 - a;
     pp = 0.5f * (a + b);
     pm = 0.5f * (a - b);
 }

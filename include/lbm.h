@@ -89,7 +89,7 @@ typedef enum lbm_storage {
 #define LBM_FLAG_PERIODIC_X 2  /* periodic instead of walls at the x ends */
 #define LBM_FLAG_PERIODIC_Z 4  /* periodic instead of walls at the z ends */
 #define LBM_FLAG_ONE_NODE 8    /* one node per thread in the step kernels (test hook: the
-                                  two-node kernels must agree with it bit for bit) */
+                                  two- and four-node kernels are checked against it) */
 
 /* sticky device flags reported in lbm_diagnostics.flags */
 #define LBM_DEVFLAG_NONFINITE 1   /* a macroscopic value was NaN or Inf */

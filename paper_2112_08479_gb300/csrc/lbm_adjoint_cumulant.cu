@@ -5,6 +5,12 @@
 #include "lbm_cumulant_collide.cuh"
 #include "lbm_internal.h"
 
+// Minimum resident blocks per SM for the adjoint kernel's register allocation
+// (4: 128 registers).
+#ifndef LBM_CUM_ADJ_MINB
+#define LBM_CUM_ADJ_MINB 4
+#endif
+
 namespace lbmgpu {
 
 // Out-of-place step on the canonical FP32 layout: the own slots are read as
@@ -53,7 +59,7 @@ __device__ __forceinline__ void axis_inverse_vjp(float s, float v, float d0, flo
 // (in exact arithmetic the rest populations' closing sums equal their
 // formulas, which are what is differentiated).  The cumulant model has no
 // Smagorinsky closure, so there is no C_s term.
-__global__ void __launch_bounds__(128) cumulant_adjoint_kernel(KParams kp, const float* __restrict__ st,
+__global__ void __launch_bounds__(128, LBM_CUM_ADJ_MINB) cumulant_adjoint_kernel(KParams kp, const float* __restrict__ st,
                                                                const float* __restrict__ lamn,
                                                                float* __restrict__ lam, float wfw) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -247,15 +253,25 @@ __global__ void __launch_bounds__(128) cumulant_adjoint_kernel(KParams kp, const
     // F = g' chi e^g
     gchit += gFx * kp.gx + gFy * kp.gy + gFz * kp.gz;
     // f enters through drho, j and the second moments
-    lam[n] = gdrho;
+    // d/df_i of the moments: gdrho + c.gj + sum_ab c_a c_b gm_ab, built by
+    // lines (49 operations): E, the part without c_x, and X, the coefficient
+    // of c_x, per (c_y, c_z), then E (c_x = 0) and E + gmxx +- X (c_x = +-1)
+    const float u = gdrho + gmzz;
 #pragma unroll
-    for (int i = 1; i < 27; i += 2) {
-        const float cxi = cx27(i), cyi = cy27(i), czi = cz27(i);
-        const float te = gdrho + gmxx * cxi * cxi + gmyy * cyi * cyi + gmzz * czi * czi +
-                         gmxy * cxi * cyi + gmxz * cxi * czi + gmyz * cyi * czi;
-        const float to = cxi * gjx + cyi * gjy + czi * gjz;
-        lam[(size_t)i * N + n] = te + to;
-        lam[(size_t)(i + 1) * N + n] = te - to;
+    for (int c = 0; c < 3; ++c) {
+        const float Ez = c == 1 ? gdrho : (c == 2 ? u + gjz : u - gjz);
+        const float Xz = c == 1 ? gjx : (c == 2 ? gjx + gmxz : gjx - gmxz);
+        const float Yz = c == 1 ? gjy : (c == 2 ? gjy + gmyz : gjy - gmyz);
+        const float t = Ez + gmyy;
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const float E = b == 1 ? Ez : (b == 2 ? t + Yz : t - Yz);
+            const float X = b == 1 ? Xz : (b == 2 ? Xz + gmxy : Xz - gmxy);
+            const float gx = E + gmxx;
+            lam[(size_t)dir27(-1, b - 1, c - 1) * N + n] = gx - X;
+            lam[(size_t)dir27(0, b - 1, c - 1) * N + n] = E;
+            lam[(size_t)dir27(1, b - 1, c - 1) * N + n] = gx + X;
+        }
     }
 #pragma unroll
     for (int k = 0; k < 7; ++k) lam[(size_t)(27 + k) * N + n] = gp[k] + gchit;

@@ -407,6 +407,8 @@ def run_ours(args, ws, rank, local):
         extra["adjoint"] = adjoint_ratio(torch)
         extra["adjoint_cumulant"] = adjoint_ratio(torch, model="cumulant")
         extra["adjoint_1024x64x128"] = adjoint_ratio(torch, (1024, 64, 128), K=20, nseg=3, reps=1)
+        extra["adjoint_cumulant_1024x64x128"] = adjoint_ratio(torch, (1024, 64, 128), K=20,
+                                                             model="cumulant", nseg=3, reps=1)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         cpu = oracle_sample()

@@ -109,9 +109,6 @@ struct KParams {
 #ifndef LBM_BGK_PAIR
 #define LBM_BGK_PAIR 1
 #endif
-#ifndef LBM_CUMULANT_PAIR
-#define LBM_CUMULANT_PAIR 0
-#endif
 #ifndef LBM_STEP2_MINB
 #define LBM_STEP2_MINB 4
 #endif

@@ -63,17 +63,28 @@ def kernel_hash() -> str:
 
 
 def profiled_traffic(nodes: int):
-    """DRAM bytes per launch of the step kernel from the committed ncu summary,
-    scaled to `nodes`; None when the kernel changed since the capture."""
+    """DRAM bytes (read + write) per launch of the step kernel from the
+    committed ncu summary: the mean over the captured even and odd launches
+    when they ran on a box of `nodes` nodes, else the per-node figure scaled
+    to `nodes`.  (None, why) when the kernel changed since the capture."""
     try:
         txt = open(PROFILE).read()
     except OSError:
-        return None
+        return None, "no profile"
     m = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", txt)
+    if not m or m.group(1) != kernel_hash():
+        return None, "kernel changed since the capture"
+    full = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+-]+)", txt)
+    box = re.search(r"box_nodes:\s*([0-9]+)", txt)
+    if full and box and int(box.group(1)) == nodes:
+        return float(full.group(1)), "ncu capture of this box (one even and one odd launch)"
     b = re.search(r"dram_bytes_per_node_update:\s*([0-9.eE+-]+)", txt)
-    if not m or not b or m.group(1) != kernel_hash():
-        return None
-    return float(b.group(1)) * nodes
+    if not b:
+        return None, "no per-node figure"
+    return float(b.group(1)) * nodes, "per-node figure of a smaller box scaled by nodes"
+
+
+NOMINAL_HBM_GBS = 8000.0
 
 
 def measured_peak_hbm():
@@ -175,50 +186,132 @@ def max_over_ranks(v: float, ws: int) -> float:
 
 
 # ---------------------------------------------------------------------------
-def oracle_sample(seconds_hint: float = 15.0):
-    """The FP64 C oracle (single thread, as it stands) on a bounded sample of
-    the workload's physics: a 1024 x 64 x 128 box with the same lattice
-    parameters, 2 time steps."""
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def host_mem_available() -> int | None:
+    """Bytes the process may still allocate: MemAvailable, bounded by the
+    cgroup (v2) limit when one is set."""
+    avail = None
+    try:
+        with open("/proc/meminfo") as fh:
+            for line in fh:
+                if line.startswith("MemAvailable:"):
+                    avail = int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    try:
+        lim = open("/sys/fs/cgroup/memory.max").read().strip()
+        cur = int(open("/sys/fs/cgroup/memory.current").read().strip())
+        if lim != "max":
+            room = int(lim) - cur
+            avail = room if avail is None else min(avail, room)
+    except (OSError, ValueError):
+        pass
+    return avail
+
+
+ORACLE_BYTES_PER_NODE = (19 + 7) * 8 * 2 + 8   # f, Phi and their post-collision copies, chi0
+
+
+def oracle_box(nz_max: int | None = None):
+    """The workload's lock-exchange box for the FP64 oracle (BGK-Smagorinsky
+    D3Q19 + D3Q7), or its lower z-slab of nz_max layers when the full box does
+    not fit in the host memory; returns (params, f, phi, nz)."""
     import oracle as O
-    nx, ny, nz, steps = 1024, 64, 128, 2
+    nx, ny, nz = WORKLOAD["nx"], WORKLOAD["ny"], WORKLOAD["nz"]
+    avail = host_mem_available()
+    if avail is not None:
+        fit = int(0.6 * avail / (ORACLE_BYTES_PER_NODE * nx * ny))
+        nz = max(2, min(nz, fit))
+    if nz_max is not None:
+        nz = max(2, min(nz, nz_max))
     u_b, H, Re = WORKLOAD["u_b"], WORKLOAD["H"], WORKLOAD["Re"]
     nu = u_b * H / Re
     p = O.OracleParams(nx, ny, nz, model=0, nu=nu, D=nu, cs_smag=0.17, gprime=u_b * u_b / H)
-    f, phi = O.init(p, O.lock_chi0(nx, ny, nz, 128, 1e-3, 2112))
+    f, phi = O.init(p, O.lock_chi0(nx, ny, nz, WORKLOAD["x0"], 1e-3, 2112))
+    return p, f, phi, nz
+
+
+def box_label(nz: int) -> str:
+    nx, ny, full = WORKLOAD["nx"], WORKLOAD["ny"], WORKLOAD["nz"]
+    if nz == full:
+        return f"the full {nx}x{ny}x{full} workload box"
+    return (f"the lower {nz} of {full} z-layers of the {nx}x{ny}x{full} workload box "
+            "(host memory)")
+
+
+def time_oracle(steps: int, threads: int, nz_max: int | None = None):
+    """The FP64 C oracle as it stands (node loops on `threads` host threads)
+    stepping the workload box (all lattice parameters of the workload) in
+    place; returns (MNUPS, seconds, nz, threads used)."""
+    import oracle as O
+    O.build()
+    used = O.set_threads(threads)
+    p, f, phi, nz = oracle_box(nz_max)
     t = time.perf_counter()
-    O.run(p, steps, f, phi)
+    O.run_inplace(p, steps, f, phi)
     dt = time.perf_counter() - t
-    return {"value": nx * ny * nz * steps / dt / 1e6, "unit": "MNUPS", "cores": 1, "kind": "oracle",
-            "sample": f"{steps} steps of a {nx}x{ny}x{nz} box with the workload's lattice "
-                      f"parameters (BGK-Smagorinsky D3Q19 + D3Q7, FP64, single thread), {dt:.1f} s"}
+    return p.nx * p.ny * nz * steps / dt / 1e6, dt, nz, used
+
+
+def oracle_baselines():
+    """cpu_baseline of the GPU arm: the oracle on every host core over two
+    time steps of the workload box, and on one thread over one step of a
+    16-layer z-slab of it (about 10-30 s of CPU work together)."""
+    cores = host_cores()
+    v, dt, nz, used = time_oracle(2, cores)
+    main = {"value": v, "unit": "MNUPS", "cores": used, "kind": "oracle",
+            "sample": f"2 time steps of {box_label(nz)} (BGK-Smagorinsky D3Q19 + D3Q7, FP64, "
+                      f"{used} threads), {dt:.1f} s"}
+    v1, dt1, nz1, _ = time_oracle(1, 1, nz_max=16)
+    single = {"value": v1, "unit": "MNUPS", "cores": 1, "kind": "oracle",
+              "sample": f"1 time step of {box_label(nz1)} (FP64, single thread), {dt1:.1f} s"}
+    return main, single
 
 
 def run_reference(args, ws, rank):
-    """Reference arm: the FP64 oracle as it stands on the host cores."""
+    """Reference arm: the FP64 oracle as it stands on the host cores, one
+    time step of the workload box per bench step (shrunk to a z-slab when
+    the host memory or a few minutes of run time require it)."""
     if rank != 0:
         return
     import oracle as O
     O.build()
-    nx, ny, nz = 256, 64, 128
-    u_b, H, Re = WORKLOAD["u_b"], WORKLOAD["H"], WORKLOAD["Re"]
-    nu = u_b * H / Re
-    p = O.OracleParams(nx, ny, nz, model=0, nu=nu, D=nu, cs_smag=0.17, gprime=u_b * u_b / H)
-    f, phi = O.init(p, O.lock_chi0(nx, ny, nz, 32, 1e-3, 2112))
-    for _ in range(args.warmup):
-        f, phi = O.run(p, 1, f, phi)
+    cores = O.set_threads(host_cores())
+    p, f, phi, nz = oracle_box()
+    # bound the whole run to a few minutes: time one step first
+    t = time.perf_counter()
+    O.run_inplace(p, 1, f, phi)
+    t1 = time.perf_counter() - t
+    budget = 200.0
+    total = args.steps + max(args.warmup - 1, 0)
+    if t1 * total > budget:
+        nz_s = max(2, int(nz * budget / (t1 * total)))
+        del f, phi
+        p, f, phi, nz = oracle_box(nz_s)
+    for _ in range(max(args.warmup - 1, 0)):
+        O.run_inplace(p, 1, f, phi)
     t = time.perf_counter()
     for _ in range(args.steps):
-        f, phi = O.run(p, 1, f, phi)
+        O.run_inplace(p, 1, f, phi)
     dt = time.perf_counter() - t
-    v = nx * ny * nz * args.steps / dt / 1e6
+    v = p.nx * p.ny * nz * args.steps / dt / 1e6
+    cfg = config_dict(ws)
+    if nz != WORKLOAD["nz"]:
+        cfg["sample"] = box_label(nz)
     line = {"metric": "MNUPS (lattice node updates per second / 1e6), fused LBM step",
             "value": v, "unit": "MNUPS", "impl": "reference", "n_gpus": 0, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config_dict(ws),
-            "cpu_baseline": {"value": v, "unit": "MNUPS", "cores": 1, "kind": "oracle",
-                             "sample": f"one time step per bench step of a {nx}x{ny}x{nz} box "
-                                       "with the workload's lattice parameters"},
+            "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": v, "unit": "MNUPS", "cores": cores, "kind": "oracle",
+                             "sample": f"one time step of {box_label(nz)} per bench step "
+                                       f"(BGK-Smagorinsky D3Q19 + D3Q7, FP64, {cores} threads)"},
             "e2e": {"value": v, "unit": "MNUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -387,11 +480,17 @@ def run_ours(args, ws, rank, local):
     kname = "bgk_step2_kernel" if args.model == "bgk" and WORKLOAD["nx"] % 2 == 0 else f"{args.model}_step_kernel"
     if args.model == "bgk" and args.storage != "fp32" and WORKLOAD["nx"] % 4 == 0:
         kname = "bgk_even4_kernel + bgk_step2_kernel"
+    traffic, tsrc = profiled_traffic(N) if headline else (None, "not captured for this variant")
     roof = {"bound": "hbm",
             "kernel": f"{kname} (AA even/odd, {args.storage.upper()})",
             "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": profiled_traffic(N) if headline else None,
-            "algorithmic_bytes_per_launch": bpn * N, "mean_launch_ms": kern * 1e3}
+            "frac": achieved / peak, "traffic": traffic, "traffic_source": tsrc,
+            "algorithmic_bytes_per_launch": bpn * N, "mean_launch_ms": kern * 1e3,
+            # the same launch time against the DRAM bytes ncu counted, and the
+            # algorithmic rate against the nominal 8 TB/s of the part
+            "achieved_dram": traffic / kern / 1e9 if traffic else None,
+            "frac_dram": traffic / kern / 1e9 / peak if traffic else None,
+            "frac_nominal": achieved / NOMINAL_HBM_GBS}
 
     extra = {}
     if rank == 0 and ws == 1 and not args.no_side and args.workload == "config3":
@@ -409,9 +508,9 @@ def run_ours(args, ws, rank, local):
         extra["adjoint_1024x64x128"] = adjoint_ratio(torch, (1024, 64, 128), K=20, nseg=3, reps=1)
         extra["adjoint_cumulant_1024x64x128"] = adjoint_ratio(torch, (1024, 64, 128), K=20,
                                                              model="cumulant", nseg=3, reps=1)
-    cpu = None
+    cpu = cpu1 = None
     if rank == 0 and ws == 1 and not args.no_cpu:
-        cpu = oracle_sample()
+        cpu, cpu1 = oracle_baselines()
 
     if rank == 0:
         line = {"metric": "MNUPS (lattice node updates per second / 1e6), fused LBM step",
@@ -421,7 +520,8 @@ def run_ours(args, ws, rank, local):
                 "dtype": "f32", "data": "synthetic (lock-exchange initial condition)",
                 "config": config_dict(ws, args.model, args.storage), "e2e": e2e,
                 "gpu_launches": launches,
-                "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
+                "roofline": roof, "cpu_baseline": cpu, "cpu_baseline_single_thread": cpu1,
+                "clocks": clocks,
                 "diag_at_end": {"front": d["front"], "Fw": d["Fw"], "step": d["step"]}}
         line.update(extra)
         print(json.dumps(line), flush=True)

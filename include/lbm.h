@@ -151,8 +151,11 @@ LBM_API const char* lbm_last_error(const lbm_ctx* ctx);
 LBM_API lbm_status lbm_validate(const lbm_params* p);
 
 /* Bytes of device workspace lbm_init needs for p; 0 when p is invalid.
- * Populations take (Q + NS) * N * (4 or 2) bytes; the rest is a few N/nx-sized
- * staging and reduction buffers. */
+ * The workspace holds what the flowchart of Sec. 2.3 (Fig. 3) exports to the
+ * GPU once the set-up on the CPU is done: the distributions of the fluid and
+ * the scalar (Eq. 17, 28), one copy each in the AA pattern, (Q + NS) * N *
+ * (4 or 2) bytes; plus a few N- and nx-sized staging and reduction buffers
+ * of the diagnostics (Sec. 3.1, 3.2). */
 LBM_API size_t lbm_workspace_bytes(const lbm_params* p);
 
 /* Creates a context over a caller-owned device workspace of `bytes` bytes
@@ -166,7 +169,10 @@ LBM_API lbm_status lbm_init(const lbm_params* p, void* workspace, size_t bytes,
 
 /* Re-initialises the state from a caller-given scalar field chi0 (N floats,
  * host or device memory; copied on the stream before return of control to
- * the device queue): f = w, Phi_k = w_k chi0.  Resets the step counter. */
+ * the device queue): the fluid at rest, f = w (rho = 1, u = 0), and the
+ * scalar at its equilibrium for that field, Phi_k = w_k chi0 (Eq. 29 at
+ * u = 0), as in the initial condition of Sec. 2.5 with chi0 in place of the
+ * lock field.  Resets the step counter. */
 LBM_API lbm_status lbm_set_scalar(lbm_ctx* ctx, const float* chi0);
 
 /* Advances nsteps >= 0 time steps (Eq. 17): one fused in-place kernel per
@@ -195,11 +201,15 @@ LBM_API lbm_status lbm_diag(lbm_ctx* ctx, lbm_diagnostics* out_host);
 LBM_API lbm_status lbm_fw_accumulate(lbm_ctx* ctx, double* acc_dev, double weight);
 
 /* Copies the current state to dst ((Q + NS) * N floats, canonical layout,
- * device).  Asynchronous. */
+ * device): the streamed, pre-collision distributions f_i(x, t) and Phi_k(x, t)
+ * of Eq. 17 and 28 at the current step, i.e. the data the flowchart of
+ * Sec. 2.3 (Fig. 3) transfers back from the GPU for output.  Asynchronous. */
 LBM_API lbm_status lbm_get_state(lbm_ctx* ctx, float* dst);
 
-/* Loads a state in the canonical layout (device) and sets the step counter.
- * Asynchronous. */
+/* Loads a state in the canonical layout (device): pre-collision
+ * distributions of Eq. 17 and 28 as lbm_get_state writes them (the export
+ * to the GPU of Fig. 3, from a caller's state instead of the initial
+ * condition of Sec. 2.5), and sets the step counter.  Asynchronous. */
 LBM_API lbm_status lbm_set_state(lbm_ctx* ctx, const float* src, int64_t step);
 
 /* One reverse step of the discrete adjoint of the time step with the D3Q7
@@ -296,10 +306,14 @@ LBM_API lbm_status lbm_adjoint_chi0(lbm_ctx* ctx, const float* lam0, float* grad
  * serves nx <= 16384 and ceil(nx / 128) * nz <= 32768 and returns
  * LBM_ERR_ARG beyond that (message in lbm_last_error(NULL)).  The first call
  * on each device looks up the array's device address; make that first call
- * with the device current and before any stream capture.  All calls share
- * the array: calls that overlap on the GPU race and must be serialised.
- * Enqueued on cuda_stream (its device must be current), then synchronised;
- * flags holds only what this call saw; LBM_ERR_UNSTABLE as lbm_diag. */
+ * with the device current.  Every call synchronises cuda_stream, so no call
+ * may be made while that stream is being captured into a CUDA graph: such a
+ * call returns LBM_ERR_ARG without enqueueing anything.  state must be
+ * device memory of the current device (checked: LBM_ERR_ARG otherwise).
+ * All calls share the array: calls that overlap on the GPU race and must be
+ * serialised.  Enqueued on cuda_stream (its device must be current), then
+ * synchronised; flags holds only what this call saw; LBM_ERR_UNSTABLE as
+ * lbm_diag. */
 LBM_API lbm_status lbm_diag_static(const lbm_params* p, const float* state, int64_t step,
                                    void* cuda_stream, lbm_diagnostics* out_host);
 

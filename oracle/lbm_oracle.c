@@ -56,6 +56,25 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads of the node loops (collision, streaming, macroscopic fields).
+ * Every node is computed on its own from the previous arrays, so the result
+ * does not depend on the thread count; reductions (F_w, budgets, front)
+ * stay serial.  1 unless orc_set_threads says otherwise. */
+static int g_threads = 1;
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+    g_threads = n < 1 ? 1 : n;
+#else
+    (void)n;
+    g_threads = 1;
+#endif
+    return g_threads;
+}
+int orc_threads(void) { return g_threads; }
 
 typedef struct {
     int nx, ny, nz;
@@ -520,6 +539,9 @@ void orc_stream(const orc_params* p, const double* fpost, const double* phipost,
                 double* f, double* phi) {
     int q = nq(p);
     const int (*c)[3] = cset(p);
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(g_threads) schedule(static)
+#endif
     for (int z = 0; z < p->nz; ++z)
     for (int y = 0; y < p->ny; ++y)
     for (int x = 0; x < p->nx; ++x) {
@@ -546,6 +568,9 @@ void orc_macros(const orc_params* p, const double* f, const double* phi,
                 double* rho, double* u, double* chi) {
     int q = nq(p);
     long N = (long)p->nx * p->ny * p->nz;
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(g_threads) schedule(static)
+#endif
     for (long n = 0; n < N; ++n) {
         double r, uu[3], x, F[3];
         node_moments(p, f + n*q, phi + n*ns(p), &r, uu, &x, F);
@@ -636,6 +661,9 @@ void orc_step(const orc_params* p, double* f, double* phi) {
     double* fpost = (double*)malloc(sizeof(double) * N * q);
     const int S = ns(p);
     double* phipost = (double*)malloc(sizeof(double) * N * S);
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(g_threads) schedule(static)
+#endif
     for (long n = 0; n < N; ++n)
         orc_collide_node(p, f + n*q, phi + n*S, fpost + n*q, phipost + n*S);
     orc_stream(p, fpost, phipost, f, phi);

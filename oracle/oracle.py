@@ -24,17 +24,20 @@ __all__ = [
     "feq_q19", "phieq_q7", "tau_eff", "collide_node", "cumulants27",
     "f_from_cumulants27", "bgk_nu_t", "lock_chi0", "init", "step", "run", "stream",
     "macros", "wall_friction", "front_node", "diag", "splitmix64", "velocities_scalar",
-    "phieq_q6", "front_xlim",
+    "phieq_q6", "front_xlim", "set_threads", "threads", "run_inplace",
 ]
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with plain gcc (IEEE arithmetic, no fast-math)."""
+    """Compile the oracle with plain gcc (IEEE arithmetic, no fast-math), with
+    OpenMP for the node loops where the compiler has it (the arithmetic and
+    its order per node are the same with and without)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared",
-                               "-fno-fast-math", "-ffp-contract=off",
-                               "-o", tmp, _SRC, "-lm"])
+        base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fno-fast-math",
+                "-ffp-contract=off", "-o", tmp, _SRC, "-lm"]
+        if subprocess.call(base[:1] + ["-fopenmp"] + base[1:], stderr=subprocess.DEVNULL) != 0:
+            subprocess.check_call(base)
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -131,6 +134,8 @@ def lib():
             "orc_splitmix64": (C.c_uint64, [C.c_uint64]),
             "orc_lock_chi0": (None, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_uint64, d]),
             "orc_init": (None, [P, d, d, d]),
+            "orc_set_threads": (C.c_int, [C.c_int]),
+            "orc_threads": (C.c_int, []),
         }
         for name, (res, args) in sig.items():
             fn = getattr(_lib, name)
@@ -146,6 +151,17 @@ def _d(a: np.ndarray):
 
 def _f64(a) -> np.ndarray:
     return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def set_threads(n: int) -> int:
+    """Threads of the node loops (1 = the plain serial oracle); returns the
+    count in effect (1 when built without OpenMP).  Results do not depend on
+    it: each node is computed on its own and the reductions stay serial."""
+    return lib().orc_set_threads(int(n))
+
+
+def threads() -> int:
+    return lib().orc_threads()
 
 
 def q_of(model: int) -> int:
@@ -274,6 +290,13 @@ def run(p: OracleParams, nsteps: int, f, phi, record_fw: bool = False):
     if record_fw:
         return f, phi, fw[:nsteps]
     return f, phi
+
+
+def run_inplace(p: OracleParams, nsteps: int, f: np.ndarray, phi: np.ndarray) -> None:
+    """nsteps time steps on the caller's arrays (float64, C-contiguous), no
+    copies: for timing large boxes."""
+    pc = p.c()
+    lib().orc_run(C.byref(pc), nsteps, _d(f), _d(phi), None)
 
 
 def stream(p: OracleParams, fpost, phipost):

@@ -224,6 +224,24 @@ lbm_status lbm_diag_static(const lbm_params* p, const float* state, int64_t step
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) return LBM_ERR_CUDA;
+    // the call ends with a stream synchronisation, which a stream under
+    // capture does not allow: refuse before enqueueing anything
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if ((e = cudaStreamIsCapturing((cudaStream_t)cuda_stream, &cap)) != cudaSuccess)
+        return LBM_ERR_CUDA;
+    if (cap != cudaStreamCaptureStatusNone) {
+        lbmgpu::lbm_set_thread_error("lbm_diag_static cannot run while its stream is captured");
+        return LBM_ERR_ARG;
+    }
+    // the state must be device (or managed) memory of the current device
+    cudaPointerAttributes pa;
+    if (cudaPointerGetAttributes(&pa, state) != cudaSuccess ||
+        (pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged) ||
+        (pa.type == cudaMemoryTypeDevice && pa.device != dev)) {
+        cudaGetLastError();   // clear a lookup error of an unknown pointer
+        lbmgpu::lbm_set_thread_error("lbm_diag_static: state is not memory of the current device");
+        return LBM_ERR_ARG;
+    }
     void* scratch;
     {
         // set-up, once per device, with that device current: the device

@@ -13,6 +13,15 @@ def pytest_configure(config):
     config.addinivalue_line("markers", "slow: long-running CPU test")
 
 
+@pytest.fixture(autouse=True, scope="session")
+def _oracle_threads():
+    """The oracle's node loops on every host core (results do not depend on
+    the thread count, tests/test_oracle_flows.py checks that)."""
+    import oracle as O
+    O.set_threads(os.cpu_count() or 1)
+    yield
+
+
 def pytest_collection_modifyitems(config, items):
     try:
         import torch

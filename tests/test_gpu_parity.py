@@ -101,7 +101,7 @@ def test_lock_exchange_one_step(model):
     assert e_rho < 1e-5 and e_u < 1e-5 and e_chi < 1e-5, (e_rho, e_u, e_chi)
 
 
-@pytest.mark.parametrize("model,steps", [("bgk", 1000), ("cumulant", 400)])
+@pytest.mark.parametrize("model,steps", [("bgk", 1000), ("cumulant", 1000)])
 def test_lock_exchange_long_run(model, steps):
     p = _config1(model)
     lat = _lat(p)

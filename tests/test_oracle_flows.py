@@ -328,3 +328,26 @@ def test_front_window_with_periodic_ends():
     edge[:, :, :xlim] = 1.0
     edge[:, :, xlim:] = 0.5
     assert O.front_node(edge, 0.02, xlim) == xlim - 1
+
+
+@pytest.mark.parametrize("model,scalar", [(0, 0), (1, 0), (0, 1), (1, 2)])
+def test_threads_do_not_change_results(model, scalar):
+    """The node loops of the oracle run on several threads; every node is
+    computed on its own from the previous arrays, so a run on one thread and
+    on several is bit for bit the same (collision, streaming, macros)."""
+    p = O.OracleParams(13, 5, 6, model=model, scalar=scalar, nu=0.01, D=0.01, gprime=1e-3)
+    chi0 = O.lock_chi0(13, 5, 6, 5, 0.1, 3)
+    f0, phi0 = O.init(p, chi0)
+    old = O.threads()
+    try:
+        out = []
+        for t in (1, 4):
+            O.set_threads(t)
+            f, phi = O.run(p, 6, f0.copy(), phi0.copy())
+            out.append((f, phi, O.macros(p, f, phi)))
+    finally:
+        O.set_threads(old)
+    (fa, pa, ma), (fb, pb, mb) = out
+    assert np.array_equal(fa, fb) and np.array_equal(pa, pb)
+    for a, b in zip(ma, mb):
+        assert np.array_equal(a, b)

@@ -327,12 +327,12 @@ def config_dict(ws, model="bgk", storage="fp32"):
 
 
 # ---------------------------------------------------------------------------
-def make_lattice(model="bgk", storage="fp32", scalar="q7", **over):
+def make_lattice(model="bgk", storage="fp32", scalar="q7", flags=0, **over):
     from paper_2112_08479_gb300 import lbm
     w = dict(WORKLOAD)
     w.update(over)
     p = lbm.lock_exchange(w["nx"], w["ny"], w["nz"], H=w["H"], x0=w["x0"], u_b=w["u_b"],
-                          Re=w["Re"], model=model, storage=storage, scalar=scalar)
+                          Re=w["Re"], model=model, storage=storage, scalar=scalar, flags=flags)
     return lbm.Lattice(p, device="cuda")
 
 
@@ -363,8 +363,8 @@ def timed_loop(lat, steps, warmup, torch, inner=INNER, with_diag=True, kernel_ev
     return total, kern, launches
 
 
-def side_variant(torch, model, storage, scalar="q7", steps=3):
-    lat = make_lattice(model, storage, scalar)
+def side_variant(torch, model, storage, scalar="q7", steps=3, flags=0):
+    lat = make_lattice(model, storage, scalar, flags=flags)
     total, kern, _ = timed_loop(lat, steps, 1, torch, with_diag=False)
     n = lat.N
     mnups = n / kern / 1e6
@@ -502,6 +502,12 @@ def run_ours(args, ws, rank, local):
             r = side_variant(torch, model, storage, scalar)
             r["hbm_frac"] = r.pop("achieved_gbs") / peak
             variants[f"{model}_{storage}" + ("" if scalar == "q7" else f"_{scalar}")] = r
+        # the opt-in TMA-staged form of the cumulant FP16 step (bulk copies
+        # through shared memory), for comparison with the default kernel
+        from paper_2112_08479_gb300 import lbm as _l
+        r = side_variant(torch, "cumulant", "fp16s", flags=_l.LBM_FLAG_TMA_STAGED)
+        r["hbm_frac"] = r.pop("achieved_gbs") / peak
+        variants["cumulant_fp16s_tma_staged"] = r
         extra["variants"] = variants
         extra["adjoint"] = adjoint_ratio(torch)
         extra["adjoint_cumulant"] = adjoint_ratio(torch, model="cumulant")

@@ -90,10 +90,19 @@ typedef enum lbm_storage {
 #define LBM_FLAG_PERIODIC_Z 4  /* periodic instead of walls at the z ends */
 #define LBM_FLAG_ONE_NODE 8    /* one node per thread in the step kernels (test hook: the
                                   two- and four-node kernels are checked against it) */
+#define LBM_FLAG_TMA_STAGED 16 /* cumulant model, D3Q7 scalar, 16-bit storage, nx a multiple
+                                  of 256: run each step through the TMA-staged kernel (row
+                                  segments moved by bulk copies through shared memory by a
+                                  producer warp); same results bit for bit, measured slower
+                                  than the default kernel on GB300; ignored elsewhere */
 
 /* sticky device flags reported in lbm_diagnostics.flags */
 #define LBM_DEVFLAG_NONFINITE 1   /* a macroscopic value was NaN or Inf */
 #define LBM_DEVFLAG_RHO_NONPOS 2  /* rho <= 0 at some node */
+#define LBM_DEVFLAG_TIMEOUT 4     /* a step kernel could not move its populations
+                                     through shared memory (a bounded wait for its
+                                     own bulk copies gave up, or the shared memory
+                                     was misaligned): the step is incomplete */
 
 typedef struct lbm_params {
     int32_t nx, ny, nz;       /* nodes; 1 <= nx, ny, nz; nx*ny*nz < 2^31;
@@ -120,11 +129,21 @@ typedef struct lbm_params {
     double scale_f;           /* 16-bit storage scale of f - w (power of two) */
     double scale_phi;         /* 16-bit storage scale of Phi - w (power of two) */
     int32_t scalar;           /* lbm_scalar */
+    int32_t x_offset;         /* x-slab of a larger box: global x of local column 0
+                                 (0 for a whole box) */
+    int32_t nx_global;        /* x-slab: nx of the whole box (0: nx, a whole box).  With
+                                 nx_global > nx the local x ends are slab faces: walls
+                                 to the kernels, made fluid by the halo exchange of
+                                 lbm_halo_pack / lbm_halo_unpack around every odd step;
+                                 x0, the lock noise (keyed by the global node index)
+                                 and the front refer to the whole box */
     int32_t pad_;
 } lbm_params;
 
 typedef struct lbm_diagnostics {
-    double front;        /* (x_f + 1/2 - x0) / H, Sec. 3.1 */
+    double front;        /* (x_f + 1/2 - x0) / H, Sec. 3.1 (an x-slab: over its own
+                            columns, in box coordinates; the box's front comes
+                            from lbm_column_max of every slab) */
     double front_node;   /* x_f in node coordinates, -1 when no column reaches
                             the threshold; searched over all x with walls at
                             the x ends, over x < (nx + x0) / 2 with
@@ -192,8 +211,9 @@ LBM_API lbm_status lbm_macros(lbm_ctx* ctx, float* rho, float* u, float* chi);
 
 /* Diagnostics of the current state (Sec. 3.1 front, Eq. 62-64 F_w, FP64
  * mass and scalar budgets) into a host struct.  Synchronises the stream.
- * Returns LBM_ERR_UNSTABLE when a sticky device flag is set (the struct is
- * still filled), LBM_ERR_CUDA on an asynchronous fault. */
+ * Returns LBM_ERR_TIMEOUT when LBM_DEVFLAG_TIMEOUT is set, otherwise
+ * LBM_ERR_UNSTABLE when another sticky device flag is set (the struct is
+ * still filled in both cases), LBM_ERR_CUDA on an asynchronous fault. */
 LBM_API lbm_status lbm_diag(lbm_ctx* ctx, lbm_diagnostics* out_host);
 
 /* Adds weight * F_w(current state) to *acc_dev (one device double).
@@ -316,6 +336,50 @@ LBM_API lbm_status lbm_adjoint_chi0(lbm_ctx* ctx, const float* lam0, float* grad
  * lbm_diag. */
 LBM_API lbm_status lbm_diag_static(const lbm_params* p, const float* state, int64_t step,
                                    void* cuda_stream, lbm_diagnostics* out_host);
+
+/* --- x-slab decomposition (one slab of a box per GPU) ---------------------
+ * A box of nx_global columns is cut along x into slabs (lbm_params.x_offset,
+ * nx_global); each slab is a context of its own, with walls at its x ends
+ * to the step kernels.  In the AA pattern even steps are local; around every
+ * odd step, once before it and once after it, each pair of touching faces
+ * swaps face buffers: both sides lbm_halo_pack their face, exchange the
+ * buffers, then lbm_halo_unpack the neighbour's buffer into their face.
+ * With periodic x the last slab's face 1 touches the first slab's face 0.
+ * Unpacking sets, at every face node (y, z), each population i whose c_ix
+ * points into the slab to the neighbour's population opp(i) at its face node
+ * (y - c_iy, z - c_iz) (y periodic; skipped where z - c_iz lies beyond the
+ * top or bottom wall): the populations crossing the face in the streaming
+ * of Eq. 17 under the AA pattern.  Steps, packs and unpacks of a slab
+ * execute in stream order; results equal those of the whole box bit for bit.
+ *
+ * lbm_halo_bytes: bytes of one face buffer (device memory, caller-owned):
+ * the populations with c_x = +1 of both lattices (5 + 1 for D3Q19 + D3Q7,
+ * 9 + 1 cumulant + D3Q7, 9 + 9 cumulant + D3Q27), ny nz storage elements
+ * each; 0 when p is invalid.
+ * lbm_halo_pack: face 0 (x = 0) or 1 (x = nx - 1) of the current state into
+ * buf.  lbm_halo_unpack: the buffer the neighbour packed from its touching
+ * face, into face `face`.  Asynchronous.
+ * lbm_next_step_odd: 1 when the context's next step is an odd AA step (the
+ * steps to exchange around), 0 otherwise, -1 for NULL. */
+LBM_API size_t lbm_halo_bytes(const lbm_params* p);
+LBM_API lbm_status lbm_halo_pack(lbm_ctx* ctx, int32_t face, void* buf);
+LBM_API lbm_status lbm_halo_unpack(lbm_ctx* ctx, int32_t face, const void* buf);
+LBM_API int32_t lbm_next_step_odd(const lbm_ctx* ctx);
+
+/* Column maxima of the front search (Sec. 3.1, reading R11) of the current
+ * state: m[x] = max over z of the span-averaged chi of column x, for the
+ * context's nx columns (device, nx floats).  A slab's columns, gathered in
+ * x order over all slabs, give the whole box's.  Asynchronous. */
+LBM_API lbm_status lbm_column_max(lbm_ctx* ctx, float* m);
+
+/* Front of a whole box from its column maxima m[0 .. nx) (device):
+ * out2[0] = (x_f + 1/2 - x0) / H and out2[1] = x_f as in lbm_diagnostics
+ * (search window of periodic_x as there), two device doubles.  Enqueued on
+ * `stream` (a cudaStream_t, NULL = legacy default stream).  Asynchronous;
+ * LBM_ERR_ARG (message in lbm_last_error(NULL)) for invalid arguments. */
+LBM_API lbm_status lbm_front_of_columns(const float* m, int32_t nx, double threshold,
+                                        int32_t x0, int32_t H, int32_t periodic_x,
+                                        double* out2, void* stream);
 
 /* Current step counter. */
 LBM_API int64_t lbm_get_step(const lbm_ctx* ctx);

@@ -60,7 +60,7 @@ const char* check(const lbm_params* p) {
     if (p->storage != LBM_FP32 && p->storage != LBM_FP16S && p->storage != LBM_BF16S)
         return "unknown storage";
     if (p->flags & ~(LBM_FLAG_NO_COLLIDE | LBM_FLAG_PERIODIC_X | LBM_FLAG_PERIODIC_Z |
-                     LBM_FLAG_ONE_NODE))
+                     LBM_FLAG_ONE_NODE | LBM_FLAG_TMA_STAGED))
         return "unknown flag bits";
     if (!finite(p->nu) || p->nu <= 0.0) return "nu must be finite and > 0";
     if (!finite(p->D) || p->D <= 0.0) return "D must be finite and > 0";
@@ -71,7 +71,13 @@ const char* check(const lbm_params* p) {
     if (p->model == LBM_CUMULANT_Q27 && (!finite(p->omega_bulk) || p->omega_bulk <= 0.0 ||
                                          p->omega_bulk >= 2.0))
         return "omega_bulk must lie in (0, 2)";
-    if (p->x0 < 0 || p->x0 > p->nx) return "x0 must lie in [0, nx]";
+    if (p->nx_global != 0 && p->nx_global < p->nx) return "nx_global must be 0 or >= nx";
+    if (p->x_offset < 0 || (double)p->x_offset + p->nx > (p->nx_global ? p->nx_global : p->nx))
+        return "x_offset + nx must not exceed nx_global";
+    if (p->nx_global > p->nx && (p->flags & LBM_FLAG_PERIODIC_X))
+        return "an x-slab takes no LBM_FLAG_PERIODIC_X (its x ends are slab faces)";
+    if (p->x0 < 0 || p->x0 > (p->nx_global ? p->nx_global : p->nx))
+        return "x0 must lie in [0, nx_global]";
     if (p->H <= 0) return "H must be > 0";
     if (!finite(p->noise_amp) || p->noise_amp < 0.0) return "noise_amp must be finite and >= 0";
     if (!finite(p->front_threshold)) return "front_threshold must be finite";
@@ -130,6 +136,8 @@ KParams kparams(const lbm_params* p) {
     // the correctly rounded FP32 quotient, bit-identical to 1.0f / taup0 on
     // the device, so that a kernel may take either form
     k.omp0 = 1.0f / k.taup0;
+    k.x_off = p->x_offset;
+    k.nxg = p->nx_global ? p->nx_global : p->nx;
     return k;
 }
 
@@ -208,6 +216,7 @@ lbm_status lbm_init(const lbm_params* p, void* workspace, size_t bytes, void* cu
     c->v.devflags = (int*)(w + L.ddiag + sizeof(DevDiag));
     c->v.fgrad = (FrontGrad*)(w + L.fgrad);
     c->v.diag_blocks = L.nblocks;
+    c->kp.devflags = c->v.devflags;
     cudaError_t e = launch_init(c->kp, kind(p), c->v, nullptr, p->x0, p->noise_amp,
                                 p->seed, c->stream);
     if (e != cudaSuccess) {
@@ -288,7 +297,7 @@ lbm_status lbm_diag(lbm_ctx* c, lbm_diagnostics* out) {
     out->pad_ = 0;
     if (rec.flags[0]) {
         snprintf(c->err, sizeof c->err, "sticky device flags 0x%x", rec.flags[0]);
-        return LBM_ERR_UNSTABLE;
+        return (rec.flags[0] & LBM_DEVFLAG_TIMEOUT) ? LBM_ERR_TIMEOUT : LBM_ERR_UNSTABLE;
     }
     return LBM_OK;
 }
@@ -468,6 +477,55 @@ lbm_status lbm_adjoint_chi0(lbm_ctx* c, const float* lam0, float* grad_chi0) {
     if (lbm_status s = adjoint_model_check(c); s != LBM_OK) return s;
     cudaError_t e = launch_adjoint_chi0(c->kp, q_of(&c->p), lam0, grad_chi0, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "adjoint_chi0 launch");
+    return LBM_OK;
+}
+
+size_t lbm_halo_bytes(const lbm_params* p) {
+    if (check(p)) return 0;
+    return halo_elems(q_of(p), ns_of(p), p->ny, p->nz) * elem_size(p);
+}
+
+lbm_status lbm_halo_pack(lbm_ctx* c, int32_t face, void* buf) {
+    if (!c) return arg_fail(nullptr, "ctx is NULL");
+    if (face != 0 && face != 1) return arg_fail(c, "face must be 0 (x = 0) or 1 (x = nx - 1)");
+    if (!buf) return arg_fail(c, "buf is NULL");
+    cudaError_t e = launch_halo(c->kp, kind(&c->p), face, true, c->v.f, c->v.phi, buf, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "halo_pack launch");
+    return LBM_OK;
+}
+
+lbm_status lbm_halo_unpack(lbm_ctx* c, int32_t face, const void* buf) {
+    if (!c) return arg_fail(nullptr, "ctx is NULL");
+    if (face != 0 && face != 1) return arg_fail(c, "face must be 0 (x = 0) or 1 (x = nx - 1)");
+    if (!buf) return arg_fail(c, "buf is NULL");
+    cudaError_t e = launch_halo(c->kp, kind(&c->p), face, false, c->v.f, c->v.phi,
+                                const_cast<void*>(buf), c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "halo_unpack launch");
+    return LBM_OK;
+}
+
+int32_t lbm_next_step_odd(const lbm_ctx* c) { return c ? c->odd : -1; }
+
+lbm_status lbm_column_max(lbm_ctx* c, float* m) {
+    if (!c) return arg_fail(nullptr, "ctx is NULL");
+    if (!m) return arg_fail(c, "m is NULL");
+    cudaError_t e = launch_column_max(c->kp, kind(&c->p), c->odd != 0, c->v, m, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "column_max launch");
+    return LBM_OK;
+}
+
+lbm_status lbm_front_of_columns(const float* m, int32_t nx, double threshold, int32_t x0,
+                                int32_t H, int32_t periodic_x, double* out2, void* stream) {
+    if (!m || !out2) return arg_fail(nullptr, "m and out2 must not be NULL");
+    if (nx < 1 || H < 1 || x0 < 0 || x0 > nx || !isfinite(threshold))
+        return arg_fail(nullptr, "nx >= 1, H >= 1, 0 <= x0 <= nx, finite threshold");
+    cudaError_t e = launch_front_of_columns(
+        m, nx, threshold, x0, (double)H, front_xlim(nx, x0, periodic_x ? LBM_FLAG_PERIODIC_X : 0),
+        out2, (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        snprintf(g_err, sizeof g_err, "front_of_columns launch: %s", cudaGetErrorString(e));
+        return LBM_ERR_CUDA;
+    }
     return LBM_OK;
 }
 

@@ -78,9 +78,15 @@ __global__ void init_kernel(KParams kp, S* __restrict__ f, S* __restrict__ phi,
     if (chi0) {
         c = chi0[n] - 1.0f;
     } else {
-        double v = x < x0 ? 0.0 : -1.0;
-        if (x == x0 - 1) {
-            const double r = (double)(splitmix64(seed ^ (unsigned long long)n) >> 11) * 0x1.0p-53;
+        // global column and node index (an x-slab keys the noise by the
+        // node's index in the whole box)
+        const int xg = x + kp.x_off;
+        const unsigned long long ng =
+            (unsigned long long)xg +
+            (unsigned long long)kp.nxg * ((unsigned long long)y + (unsigned long long)kp.ny * z);
+        double v = xg < x0 ? 0.0 : -1.0;
+        if (xg == x0 - 1) {
+            const double r = (double)(splitmix64(seed ^ ng) >> 11) * 0x1.0p-53;
             v += amp * (2.0 * r - 1.0);
         }
         c = (float)v;
@@ -247,7 +253,7 @@ constexpr int FIN_T = 512;
 __global__ void __launch_bounds__(FIN_T) diag_finalize_kernel(
     int nx, double nodes, unsigned nblocks, const double* __restrict__ part,
     const float* __restrict__ fwpart, unsigned* __restrict__ colmax, DevDiag* __restrict__ out,
-    double thr, int x0, double H, int xlim) {
+    double thr, int x0, double H, int xlim, int x_off) {
     __shared__ double sa[FIN_T], sb[FIN_T];
     __shared__ float ss[FIN_T], sc[FIN_T];
     __shared__ int sx[FIN_T];
@@ -284,6 +290,7 @@ __global__ void __launch_bounds__(FIN_T) diag_finalize_kernel(
             const double m0 = fkey_inv(colmax[x]), m1 = fkey_inv(colmax[x + 1]);
             xn = x + (m0 - thr) / (m0 - m1);
         }
+        if (xn >= 0.0) xn += x_off;   // an x-slab reports its columns in box coordinates
         out->front_node = xn;
         out->front = (xn + 0.5 - x0) / H;
         out->Fw = (double)ss[0] + (double)sc[0];
@@ -450,6 +457,7 @@ static cudaError_t dispatch(Kind k, Fn&& fn) {
 
 cudaError_t launch_step(const KParams& kp, Kind k, bool odd, void* f, void* phi, float* save,
                         cudaStream_t st) {
+    if (!save && staged_step_applies(kp, k)) return launch_staged_step(kp, k, odd, f, phi, st);
     if (k.model == LBM_BGK_SMAG_Q19) return launch_bgk_step(kp, k.storage, k.scalar, odd, f, phi, save, st);
     if (k.model == LBM_CUMULANT_Q27)
         return launch_cumulant_step(kp, k.storage, k.scalar, odd, f, phi, save, st);
@@ -512,9 +520,73 @@ cudaError_t launch_diag(const KParams& kp, Kind k, bool odd, const Views& v, dou
         if (e != cudaSuccess) return e;
         diag_finalize_kernel<<<1, FIN_T, 0, st>>>(kp.nx, (double)kp.N, v.diag_blocks, v.part,
                                                   v.fwpart, v.colmax, v.ddiag, threshold, x0, H,
-                                                  front_xlim(kp.nx, x0, kp.flags));
+                                                  front_xlim(kp.nx, x0, kp.flags), kp.x_off);
         return cudaGetLastError();
     });
+}
+
+// m[x] = max over z of the span-averaged chi of column x (the keys of the
+// columns kernel decoded), keys reset for the next diagnostics.
+__global__ void column_max_kernel(int nx, unsigned* __restrict__ colmax, float* __restrict__ m) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= nx) return;
+    m[x] = fkey_inv(colmax[x]);
+    colmax[x] = 0x007fffffu;
+}
+
+// Front of a whole box from its column maxima m[0 .. nx) (Sec. 3.1, reading
+// R11, the search window of front_xlim): out[0] = (x_f + 1/2 - x0) / H,
+// out[1] = x_f (-1 when no column reaches the threshold).
+__global__ void __launch_bounds__(FIN_T) front_of_columns_kernel(const float* __restrict__ m,
+                                                                 int nx, double thr, int x0,
+                                                                 double H, int xlim,
+                                                                 double* __restrict__ out) {
+    __shared__ int sx[FIN_T];
+    const int t = threadIdx.x;
+    int xf = -1;
+    for (int x = t; x < xlim; x += FIN_T)
+        if ((double)m[x] >= thr) xf = x;
+    sx[t] = xf;
+    __syncthreads();
+    for (int w = FIN_T / 2; w > 0; w >>= 1) {
+        if (t < w) sx[t] = max(sx[t], sx[t + w]);
+        __syncthreads();
+    }
+    if (t == 0) {
+        const int x = sx[0];
+        double xn;
+        if (x < 0) xn = -1.0;
+        else if (x == xlim - 1) xn = (double)x;
+        else {
+            const double m0 = m[x], m1 = m[x + 1];
+            xn = x + (m0 - thr) / (m0 - m1);
+        }
+        out[0] = (xn + 0.5 - x0) / H;
+        out[1] = xn;
+    }
+}
+
+cudaError_t launch_column_max(const KParams& kp, Kind k, bool odd, const Views& v, float* m,
+                              cudaStream_t st) {
+    cudaError_t e = dispatch(k, [&]<int Q, int SL, typename S>() {
+        dim3 grid((kp.nx + DIAG_BX - 1) / DIAG_BX, kp.nz);
+        if (odd)
+            diag_columns_kernel<Q, SL, true, S><<<grid, DIAG_BX, 0, st>>>(
+                kp, (const S*)v.f, (const S*)v.phi, v.chibar, v.colmax, v.part, v.fwpart, v.devflags);
+        else
+            diag_columns_kernel<Q, SL, false, S><<<grid, DIAG_BX, 0, st>>>(
+                kp, (const S*)v.f, (const S*)v.phi, v.chibar, v.colmax, v.part, v.fwpart, v.devflags);
+        return cudaGetLastError();
+    });
+    if (e != cudaSuccess) return e;
+    column_max_kernel<<<(kp.nx + 255) / 256, 256, 0, st>>>(kp.nx, v.colmax, m);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_front_of_columns(const float* m, int nx, double thr, int x0, double H,
+                                    int xlim, double* out, cudaStream_t st) {
+    front_of_columns_kernel<<<1, FIN_T, 0, st>>>(m, nx, thr, x0, H, xlim, out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_fw_accumulate(const KParams& kp, Kind k, bool odd, const Views& v,

@@ -90,6 +90,8 @@ struct KParams {
     float sp, isp;       // storage scale of Phi and its inverse
     float nu;            // molecular viscosity (wall friction, Eq. 62)
     float omp0;          // 1 / taup0: the scalar rate of the cumulant model (molecular D)
+    int* devflags;       // sticky device flags (LBM_DEVFLAG_*) of the context
+    int x_off, nxg;      // x-slab: global x of local column 0, nx of the whole box
 };
 
 // ---------------------------------------------------------------------------

@@ -25,7 +25,6 @@ namespace lbmgpu {
 #ifndef LBM_CUM_WSPLIT
 #define LBM_CUM_WSPLIT 1
 #endif
-
 template <bool ODD, bool SAVE, typename S, int SL, bool W>
 __device__ __forceinline__ void cumulant_step_body(const KParams& kp, S* __restrict__ f,
                                                    S* __restrict__ phi, float* __restrict__ save,

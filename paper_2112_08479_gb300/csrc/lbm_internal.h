@@ -50,6 +50,12 @@ struct Kind {
     int model, scalar, storage;
 };
 
+// The TMA-staged step kernels (lbm_staged.cu): whether they serve this box
+// and kind, and their launcher.
+bool staged_step_applies(const KParams& kp, Kind k);
+cudaError_t launch_staged_step(const KParams& kp, Kind k, bool odd, void* f, void* phi,
+                               cudaStream_t st);
+
 // odd: parity of the AA step.
 cudaError_t launch_step(const KParams& kp, Kind k, bool odd, void* f, void* phi, float* save,
                         cudaStream_t st);
@@ -80,5 +86,15 @@ cudaError_t launch_adjoint_chi0(const KParams& kp, int Q, const float* lam0, flo
                                 cudaStream_t st);
 
 unsigned diag_block_count(int nx, int nz);
+
+// x-slabs (lbm_slab.cu, lbm_aux.cu): face buffers of the halo exchange and
+// the column maxima of the front.
+size_t halo_elems(int Q, int NS, int ny, int nz);
+cudaError_t launch_halo(const KParams& kp, Kind k, int face, bool pack, void* f, void* phi,
+                        void* buf, cudaStream_t st);
+cudaError_t launch_column_max(const KParams& kp, Kind k, bool odd, const Views& v, float* m,
+                              cudaStream_t st);
+cudaError_t launch_front_of_columns(const float* m, int nx, double thr, int x0, double H,
+                                    int xlim, double* out, cudaStream_t st);
 
 }  // namespace lbmgpu

@@ -18,7 +18,8 @@ LBM_OK, LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_NOMEM, LBM_ERR_UNSTABLE, LBM_ERR_STAT
 LBM_BGK_SMAG_Q19, LBM_CUMULANT_Q27 = 0, 1
 LBM_FP32, LBM_FP16S, LBM_BF16S = 0, 1, 2
 LBM_FLAG_NO_COLLIDE, LBM_FLAG_PERIODIC_X, LBM_FLAG_PERIODIC_Z, LBM_FLAG_ONE_NODE = 1, 2, 4, 8
-LBM_DEVFLAG_NONFINITE, LBM_DEVFLAG_RHO_NONPOS = 1, 2
+LBM_FLAG_TMA_STAGED = 16
+LBM_DEVFLAG_NONFINITE, LBM_DEVFLAG_RHO_NONPOS, LBM_DEVFLAG_TIMEOUT = 1, 2, 4
 
 LBM_SCALAR_Q7, LBM_SCALAR_Q6, LBM_SCALAR_Q27 = 0, 1, 2
 
@@ -41,7 +42,8 @@ class lbm_params(C.Structure):
                 ("omega_bulk", C.c_double), ("x0", C.c_int32), ("H", C.c_int32),
                 ("noise_amp", C.c_double), ("seed", C.c_uint64),
                 ("front_threshold", C.c_double), ("scale_f", C.c_double),
-                ("scale_phi", C.c_double), ("scalar", C.c_int32), ("pad_", C.c_int32)]
+                ("scale_phi", C.c_double), ("scalar", C.c_int32), ("x_offset", C.c_int32),
+                ("nx_global", C.c_int32), ("pad_", C.c_int32)]
 
 
 class lbm_diagnostics(C.Structure):
@@ -81,6 +83,13 @@ SIGNATURES = [
     ("lbm_adjoint_chi0", C.c_int, [_CTX, C.c_void_p, C.c_void_p]),
     ("lbm_diag_static", C.c_int, [_P, C.c_void_p, C.c_int64, C.c_void_p,
                                   C.POINTER(lbm_diagnostics)]),
+    ("lbm_halo_bytes", C.c_size_t, [_P]),
+    ("lbm_halo_pack", C.c_int, [_CTX, C.c_int32, C.c_void_p]),
+    ("lbm_halo_unpack", C.c_int, [_CTX, C.c_int32, C.c_void_p]),
+    ("lbm_next_step_odd", C.c_int32, [_CTX]),
+    ("lbm_column_max", C.c_int, [_CTX, C.c_void_p]),
+    ("lbm_front_of_columns", C.c_int, [C.c_void_p, C.c_int32, C.c_double, C.c_int32, C.c_int32,
+                                       C.c_int32, C.c_void_p, C.c_void_p]),
     ("lbm_get_step", C.c_int64, [_CTX]),
     ("lbm_sync", C.c_int, [_CTX]),
     ("lbm_destroy", None, [_CTX]),
@@ -210,6 +219,32 @@ def lbm_adjoint_chi0(ctx, lam0_ptr, grad_ptr):
     _check(load().lbm_adjoint_chi0(ctx, lam0_ptr, grad_ptr), ctx)
 
 
+def lbm_halo_bytes(p: lbm_params) -> int:
+    return load().lbm_halo_bytes(C.byref(p))
+
+
+def lbm_halo_pack(ctx, face: int, buf_ptr: int):
+    _check(load().lbm_halo_pack(ctx, face, buf_ptr), ctx)
+
+
+def lbm_halo_unpack(ctx, face: int, buf_ptr: int):
+    _check(load().lbm_halo_unpack(ctx, face, buf_ptr), ctx)
+
+
+def lbm_next_step_odd(ctx) -> int:
+    return load().lbm_next_step_odd(ctx)
+
+
+def lbm_column_max(ctx, m_ptr: int):
+    _check(load().lbm_column_max(ctx, m_ptr), ctx)
+
+
+def lbm_front_of_columns(m_ptr: int, nx: int, threshold: float, x0: int, H: int,
+                         periodic_x: bool, out_ptr: int, stream_handle=None):
+    _check(load().lbm_front_of_columns(m_ptr, nx, threshold, x0, H, int(periodic_x), out_ptr,
+                                       stream_handle))
+
+
 def lbm_get_step(ctx) -> int:
     return load().lbm_get_step(ctx)
 
@@ -248,6 +283,8 @@ class Params:
     scale_f: float = 2.0 ** 14
     scale_phi: float = 2.0 ** 14
     scalar: int = LBM_SCALAR_Q7
+    x_offset: int = 0          # x-slab: global x of local column 0
+    nx_global: int = 0         # x-slab: nx of the whole box (0: a whole box)
 
     def c(self) -> lbm_params:
         p = lbm_params()
@@ -410,6 +447,33 @@ class Lattice:
 
     def adjoint_chi0(self, lam0, grad):
         lbm_adjoint_chi0(self.ctx, lam0.data_ptr(), grad.data_ptr())
+
+    def halo_pack(self, face: int, buf):
+        lbm_halo_pack(self.ctx, face, buf.data_ptr())
+
+    def halo_unpack(self, face: int, buf):
+        lbm_halo_unpack(self.ctx, face, buf.data_ptr())
+
+    @property
+    def next_step_odd(self) -> bool:
+        return lbm_next_step_odd(self.ctx) == 1
+
+    def column_max(self, out=None):
+        """m(x) = max over z of the span-averaged chi, one float per column."""
+        if out is None:
+            out = self._empty(self.params.nx)
+        lbm_column_max(self.ctx, out.data_ptr())
+        return out
+
+    def front_of_columns(self, m, nx: int, threshold: float, x0: int, H: int,
+                         periodic_x: bool):
+        """Front of a whole box from its column maxima m (device, nx floats):
+        (value, node coordinate) as in diag()."""
+        out = self._empty(2, dtype=self.torch.float64)
+        lbm_front_of_columns(m.data_ptr(), nx, threshold, x0, H, periodic_x, out.data_ptr(),
+                             self.stream.cuda_stream)
+        v = out.cpu()
+        return float(v[0]), float(v[1])
 
     @property
     def step_count(self) -> int:

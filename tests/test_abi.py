@@ -37,7 +37,7 @@ def test_header_symbols_exported(lib):
 
 def test_struct_layouts():
     # sizes computed from the C declarations with natural alignment
-    assert C.sizeof(lbm.lbm_params) == 6 * 4 + 5 * 8 + 3 * 8 + 8 + 2 * 4 + 8 + 8 + 3 * 8 + 2 * 4
+    assert C.sizeof(lbm.lbm_params) == 6 * 4 + 5 * 8 + 3 * 8 + 8 + 2 * 4 + 8 + 8 + 3 * 8 + 4 * 4
     assert C.sizeof(lbm.lbm_diagnostics) == 5 * 8 + 8 + 4 + 4
 
 
@@ -57,7 +57,8 @@ def test_validate_accepts_defaults(lib):
     ("nx", 0), ("ny", 70000), ("nz", -1), ("model", 5), ("storage", 9), ("flags", 64),
     ("nu", 0.0), ("nu", float("nan")), ("D", -1.0), ("cs_smag", -0.1), ("sc_t", 0.0),
     ("gprime", float("inf")), ("x0", 17), ("x0", -1), ("H", 0), ("noise_amp", -1.0),
-    ("scale_f", 0.0), ("front_threshold", float("nan")),
+    ("scale_f", 0.0), ("front_threshold", float("nan")), ("nx_global", 8), ("x_offset", -1),
+    ("x_offset", 1),
 ])
 def test_validate_rejects(lib, field, value):
     p = _good(**{field: value})
@@ -155,3 +156,17 @@ def test_lock_exchange_parameters():
     assert q.sc_t == pytest.approx(0.17**2)               # literal Sc_T = C_s^2
     with pytest.raises(ValueError):
         lbm.lock_exchange(8, 2, 4, H=4, x0=2, u_b=0.03, Re=100.0, geometry="open")
+
+
+def test_slab_fields_checked(lib):
+    """An x-slab: x_offset + nx within nx_global, x0 within the whole box, no
+    periodic flag on the slab itself; the face buffer size."""
+    assert lbm.lbm_validate(_good(nx_global=64, x_offset=48, x0=40)) == lbm.LBM_OK
+    assert lbm.lbm_validate(_good(nx_global=64, x_offset=49)) == lbm.LBM_ERR_ARG
+    assert lbm.lbm_validate(_good(nx_global=64, x_offset=0, x0=65)) == lbm.LBM_ERR_ARG
+    assert lbm.lbm_validate(_good(nx_global=64, flags=lbm.LBM_FLAG_PERIODIC_X)) == lbm.LBM_ERR_ARG
+    # D3Q19 + D3Q7: 5 + 1 populations with c_x = +1, ny nz elements each
+    assert lbm.lbm_halo_bytes(_good()) == (5 + 1) * 4 * 8 * 4
+    assert lbm.lbm_halo_bytes(_good(model=1)) == (9 + 1) * 4 * 8 * 4
+    assert lbm.lbm_halo_bytes(_good(model=1, scalar=2)) == (9 + 9) * 4 * 8 * 4
+    assert lbm.lbm_halo_bytes(_good(scalar=1, storage=1)) == (5 + 1) * 4 * 8 * 2

@@ -1,4 +1,4 @@
-"""The two-node step kernels against the one-node kernels.
+"""The two-node and TMA-staged step kernels against the one-node kernels.
 
 With nx even the BGK step runs two x-adjacent nodes per thread, with paired
 FP32 accesses and, on odd steps, the block-uniform wall-free and interior
@@ -15,7 +15,16 @@ fuse multiply-adds differently where it inlines two collisions, so FP32
 results can differ in the last bit; stored as FP32 they agree exactly in
 every case here, and where such a difference decides a rounding to 16 bits
 the stored values differ by one ulp of the storage type, at a few elements.
-Each collision step therefore starts both kernels from the same state."""
+Each collision step therefore starts both kernels from the same state.
+
+With LBM_FLAG_TMA_STAGED the cumulant model with the D3Q7 scalar and 16-bit
+storage runs the TMA-staged kernel (tiles of 256 nodes whose population rows
+move by bulk copies through shared memory); nx = 512, 1024 and 2560 give two,
+four and ten tiles per row, so the first and last tiles meet the x ends
+(clamped load windows, bounce-back or periodic wrap by direct loads and
+stores), the others take the widened windows on both sides, and z = 0 and
+nz - 1 take the wall body.  It must agree with the one-node kernel bit for
+bit, with collisions too: the collision is the same inlined function."""
 import numpy as np
 import pytest
 
@@ -109,3 +118,44 @@ def test_collision_steps_match_one_node(model, storage, scalar, geometry, nx):
                                                          for r, c in bad[:5]])
             assert np.count_nonzero(d) <= max(8, 1e-3 * d.size), (n, np.count_nonzero(d))
         s = y
+
+
+STAGED = [("cumulant", "fp16s", "q7"), ("cumulant", "bf16s", "q7")]
+
+
+def _pair(model, storage, scalar, geometry, nx, extra=0):
+    staged, one = _params(model, storage, scalar, geometry, nx, extra | lbm.LBM_FLAG_TMA_STAGED)
+    return staged, one
+
+
+@pytest.mark.parametrize("geometry", sorted(GEOMETRIES))
+@pytest.mark.parametrize("model,storage,scalar", STAGED)
+@pytest.mark.parametrize("nx", [512, 1024, 2560])
+def test_staged_streaming_matches_one_node_exactly(model, storage, scalar, geometry, nx):
+    p2, p1 = _pair(model, storage, scalar, geometry, nx, lbm.LBM_FLAG_NO_COLLIDE)
+    s0 = _state(p2, 11)
+    a, b = _lat(p2, s0, 0), _lat(p1, s0, 0)
+    for n in range(1, 5):
+        a.step(1)
+        b.step(1)
+        x, y = a.get_state().cpu().numpy(), b.get_state().cpu().numpy()
+        bad = np.argwhere(x != y)
+        assert bad.size == 0, (n, bad[:5].tolist())
+    assert not np.array_equal(x, s0)
+    assert a.diag()["flags"] == 0
+
+
+@pytest.mark.parametrize("geometry", sorted(GEOMETRIES))
+@pytest.mark.parametrize("model,storage,scalar", STAGED)
+@pytest.mark.parametrize("nx", [512, 1024, 2560])
+def test_staged_collision_steps_match_one_node_exactly(model, storage, scalar, geometry, nx):
+    p2, p1 = _pair(model, storage, scalar, geometry, nx)
+    s = _state(p2, 11)
+    a, b = _lat(p2, s, 0), _lat(p1, s, 0)
+    for n in range(4):                      # two even and two odd steps, one run each
+        a.step(1)
+        b.step(1)
+        x, y = a.get_state().cpu().numpy(), b.get_state().cpu().numpy()
+        bad = np.argwhere(x != y)
+        assert bad.size == 0, (n, bad[:5].tolist())
+    assert a.diag()["flags"] == 0

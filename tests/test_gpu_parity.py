@@ -41,7 +41,8 @@ def _to_dev(a):
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("model", [0, 1])
 @pytest.mark.parametrize("shape", [(5, 3, 4), (7, 4, 6), (130, 2, 3), (2, 3, 4), (64, 2, 3),
-                                   (66, 3, 2), (258, 2, 2), (1030, 2, 4)])
+                                   (66, 3, 2), (258, 2, 2), (1030, 2, 4), (512, 3, 2),
+                                   (1536, 2, 2)])
 @pytest.mark.parametrize("flags", [0, lbm.LBM_FLAG_PERIODIC_X, lbm.LBM_FLAG_PERIODIC_Z])
 def test_streaming_permutation_bit_exact(model, shape, flags):
     """Collision off: after n steps (even and odd AA parities) the GPU state is
@@ -49,7 +50,8 @@ def test_streaming_permutation_bit_exact(model, shape, flags):
     Odd nx runs the one-node-per-thread kernels, even nx the paired kernels
     (one active lane, one full warp, a warp plus one lane, a block edge;
     1030 x 2 x 4 has blocks away from every wall, which take the
-    single-element shifted accesses on odd steps)."""
+    single-element shifted accesses on odd steps; nx = 512 and 1536 give
+    several 128-node blocks per row)."""
     nx, ny, nz = shape
     p = lbm.Params(nx, ny, nz, model=model, flags=lbm.LBM_FLAG_NO_COLLIDE | flags, x0=1, H=nz)
     lat = _lat(p)
@@ -121,7 +123,7 @@ def test_lock_exchange_long_run(model, steps):
 
 @pytest.mark.parametrize("model", [0, 1])
 @pytest.mark.parametrize("shape", [(33, 5, 6), (130, 3, 2), (17, 1, 1), (66, 3, 4), (2, 2, 3),
-                                   (1030, 2, 3)])
+                                   (1030, 2, 3), (512, 3, 4), (256, 1, 1)])
 def test_random_state_two_steps(model, shape):
     """Random near-equilibrium state with an oblique force: one even and one odd
     step, whole state compared population by population."""

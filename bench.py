@@ -152,20 +152,28 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-def dist_setup():
+def dist_setup(backend=None):
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if ws > 1:
         import torch
         import torch.distributed as dist
-        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        backend = backend or ("nccl" if torch.cuda.is_available() else "gloo")
         if backend == "nccl":
             torch.cuda.set_device(local)
             dist.init_process_group(backend, device_id=torch.device("cuda", local))
         else:
             dist.init_process_group(backend)
     return ws, rank, local
+
+
+def device_index(local: int) -> int:
+    """GPU of this rank: LOCAL_RANK, or 0 when fewer GPUs than ranks exist
+    (ranks sharing one GPU through host-staged gloo exchanges)."""
+    import torch
+    n = torch.cuda.device_count()
+    return local if local < n else 0
 
 
 def barrier(ws):
@@ -316,13 +324,14 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
-def config_dict(ws, model="bgk", storage="fp32"):
+def config_dict(ws, model="bgk", storage="fp32", slabs=False):
     fluid = "D3Q19 BGK-Smagorinsky" if model == "bgk" else "D3Q27 cumulant"
     return {"workload": f"lock-exchange {WORKLOAD['nx']}x{WORKLOAD['ny']}x{WORKLOAD['nz']}, "
                         f"{fluid} + D3Q7 scalar, {storage.upper()} storage, Re={WORKLOAD['Re']:g}, "
                         "100 steps + diagnostics per bench step",
             "nodes": WORKLOAD["nx"] * WORKLOAD["ny"] * WORKLOAD["nz"],
-            "steps_per_bench_step": INNER, "parallelism": f"replicas x{ws}",
+            "steps_per_bench_step": INNER,
+            "parallelism": f"x-slabs x{ws} (one box, halo exchange)" if slabs else f"replicas x{ws}",
             "l2": "inputs larger than L2 (state >= 436 MB), no flush"}
 
 
@@ -430,10 +439,22 @@ def run_ours(args, ws, rank, local):
     import torch
     from paper_2112_08479_gb300 import lbm
     lbm.load()
+    local = device_index(local)
     torch.cuda.set_device(local)
     sampler = ClockSampler(torch.cuda.current_device() if ws == 1 else local)
 
-    lat = make_lattice(args.model, args.storage)
+    slabs = ws > 1 and args.decomp == "slab"
+    if slabs:
+        # one box cut into x-slabs, one per rank (strong scaling)
+        from paper_2112_08479_gb300 import slab
+        w = WORKLOAD
+        p = lbm.lock_exchange(w["nx"], w["ny"], w["nz"], H=w["H"], x0=w["x0"], u_b=w["u_b"],
+                              Re=w["Re"], model=args.model, storage=args.storage)
+        lat = slab.SlabLattice(p, rank, ws, device=f"cuda:{local}")
+        nodes_total = p.N
+    else:
+        lat = make_lattice(args.model, args.storage)
+        nodes_total = lat.N * ws
     N = lat.N
     barrier(ws)
     torch.cuda.synchronize()
@@ -442,14 +463,21 @@ def run_ours(args, ws, rank, local):
     sampler.mark_end()
     barrier(ws)
     tmax = max_over_ranks(total, ws)
-    value = N * INNER * args.steps * ws / tmax / 1e6
+    value = nodes_total * INNER * args.steps / tmax / 1e6
+    if slabs:
+        # per bench step: each odd step is bracketed by two exchanges of a pack
+        # and an unpack per touching face; the slab diagnostics add the
+        # column maxima (2 launches) and the front of the gathered columns
+        faces = sum(1 for f in (0, 1) if lat.peer[f] is not None)
+        launches += args.steps * ((INNER // 2) * 2 * 2 * faces + 3)
     d = lat.diag()
 
     # end to end through the public API with host buffers: the step's scalar
     # field comes from pinned host memory, the diagnostics go back to the host
     import numpy as np
+    lo, hi = (lat.local.x_offset, lat.local.x_offset + lat.local.nx) if slabs else (0, WORKLOAD["nx"])
     chi0 = torch.from_numpy(
-        np.where(np.arange(WORKLOAD["nx"]) < WORKLOAD["x0"], 1.0, 0.0).astype(np.float32)
+        np.where(np.arange(lo, hi) < WORKLOAD["x0"], 1.0, 0.0).astype(np.float32)
     ).repeat(WORKLOAD["ny"] * WORKLOAD["nz"]).pin_memory()
     assert chi0.numel() == N
     s = lat.stream
@@ -466,7 +494,7 @@ def run_ours(args, ws, rank, local):
         lat.diag()
     torch.cuda.synchronize()
     e2e_t = max_over_ranks(time.perf_counter() - t0, ws)
-    e2e = {"value": N * INNER * args.steps * ws / e2e_t / 1e6, "unit": "MNUPS",
+    e2e = {"value": nodes_total * INNER * args.steps / e2e_t / 1e6, "unit": "MNUPS",
            "h2d_bytes_per_step": int(chi0.numel() * 4),
            "d2h_bytes_per_step": int(__import__("ctypes").sizeof(lbm.lbm_diagnostics))}
     clocks = sampler.stop()
@@ -522,9 +550,10 @@ def run_ours(args, ws, rank, local):
         line = {"metric": "MNUPS (lattice node updates per second / 1e6), fused LBM step",
                 "value": value, "unit": "MNUPS", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": tmax / args.steps * 1e3,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "higher_is_better": True, "scaling": "strong" if slabs else "weak",
+                "vs_baseline": None,
                 "dtype": "f32", "data": "synthetic (lock-exchange initial condition)",
-                "config": config_dict(ws, args.model, args.storage), "e2e": e2e,
+                "config": config_dict(ws, args.model, args.storage, slabs), "e2e": e2e,
                 "gpu_launches": launches,
                 "roofline": roof, "cpu_baseline": cpu, "cpu_baseline_single_thread": cpu1,
                 "clocks": clocks,
@@ -544,6 +573,11 @@ def main():
     ap.add_argument("--workload", default="config3", choices=sorted(WORKLOADS))
     ap.add_argument("--model", default="bgk", choices=["bgk", "cumulant"])
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16s", "bf16s"])
+    ap.add_argument("--backend", default=None, choices=["nccl", "gloo"],
+                    help="torch.distributed backend for N > 1 (default: nccl with GPUs)")
+    ap.add_argument("--decomp", default="slab", choices=["slab", "replicas"],
+                    help="N > 1: one box cut into x-slabs with a halo exchange (strong "
+                         "scaling), or an independent box per rank (weak scaling)")
     ap.add_argument("--adjoint-only", default=None, metavar="NX,NY,NZ",
                     help="only time the adjoint sweep against the forward step on this "
                          "lock-exchange box (--model, --adjoint-k) and print it")
@@ -559,7 +593,7 @@ def main():
         return
     WORKLOAD.clear()
     WORKLOAD.update(WORKLOADS[args.workload])
-    ws, rank, local = dist_setup()
+    ws, rank, local = dist_setup(args.backend)
     if args.impl == "reference":
         run_reference(args, ws, rank)
     else:

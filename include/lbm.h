@@ -340,17 +340,22 @@ LBM_API lbm_status lbm_diag_static(const lbm_params* p, const float* state, int6
 /* --- x-slab decomposition (one slab of a box per GPU) ---------------------
  * A box of nx_global columns is cut along x into slabs (lbm_params.x_offset,
  * nx_global); each slab is a context of its own, with walls at its x ends
- * to the step kernels.  In the AA pattern even steps are local; around every
- * odd step, once before it and once after it, each pair of touching faces
- * swaps face buffers: both sides lbm_halo_pack their face, exchange the
- * buffers, then lbm_halo_unpack the neighbour's buffer into their face.
- * With periodic x the last slab's face 1 touches the first slab's face 0.
+ * to the step kernels.  After every step each pair of touching faces swaps
+ * face buffers: both sides lbm_halo_pack their face, exchange the buffers,
+ * then lbm_halo_unpack the neighbour's buffer into their face.  With
+ * periodic x the last slab's face 1 touches the first slab's face 0.
  * Unpacking sets, at every face node (y, z), each population i whose c_ix
  * points into the slab to the neighbour's population opp(i) at its face node
  * (y - c_iy, z - c_iz) (y periodic; skipped where z - c_iz lies beyond the
- * top or bottom wall): the populations crossing the face in the streaming
- * of Eq. 17 under the AA pattern.  Steps, packs and unpacks of a slab
- * execute in stream order; results equal those of the whole box bit for bit.
+ * top or bottom wall).  In the AA pattern a node at a face reads, for the
+ * populations whose upwind node lies across the face, the slot a wall would
+ * reflect (its own slot i), and pushes the populations leaving across the
+ * face into the slots a wall would (its own slot opp(i)); the swap after an
+ * even step puts the neighbour's post-collision populations where the next
+ * odd step and any read of the state take them, the swap after an odd step
+ * hands each side the populations the other pushed across (the streaming of
+ * Eq. 17 across the face).  Steps, packs and unpacks of a slab execute in
+ * stream order; results equal those of the whole box bit for bit.
  *
  * lbm_halo_bytes: bytes of one face buffer (device memory, caller-owned):
  * the populations with c_x = +1 of both lattices (5 + 1 for D3Q19 + D3Q7,
@@ -359,8 +364,8 @@ LBM_API lbm_status lbm_diag_static(const lbm_params* p, const float* state, int6
  * lbm_halo_pack: face 0 (x = 0) or 1 (x = nx - 1) of the current state into
  * buf.  lbm_halo_unpack: the buffer the neighbour packed from its touching
  * face, into face `face`.  Asynchronous.
- * lbm_next_step_odd: 1 when the context's next step is an odd AA step (the
- * steps to exchange around), 0 otherwise, -1 for NULL. */
+ * lbm_next_step_odd: 1 when the context's next step is an odd AA step, 0
+ * otherwise, -1 for NULL. */
 LBM_API size_t lbm_halo_bytes(const lbm_params* p);
 LBM_API lbm_status lbm_halo_pack(lbm_ctx* ctx, int32_t face, void* buf);
 LBM_API lbm_status lbm_halo_unpack(lbm_ctx* ctx, int32_t face, const void* buf);

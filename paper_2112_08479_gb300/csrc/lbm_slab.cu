@@ -3,12 +3,12 @@
 // A box of nx_global columns is cut along x into slabs, one per GPU.  Each
 // slab runs the ordinary step kernels with walls at its two x ends; the
 // exchange below turns those walls into fluid.  In the AA pattern (see
-// lbm_common.cuh) even steps are local.  On an odd step a node at a slab
-// face reads, for each population i whose upwind node lies in the
-// neighbouring slab, its own slot i (what a wall would reflect), and it
-// writes each population leaving across the face to its own slot opp(i).  So
-// the same exchange, done once before and once after every odd step, makes
-// the slab behave as part of the whole box:
+// lbm_common.cuh) a node at a slab face reads, for each population i whose
+// upwind node lies in the neighbouring slab, its own slot i (what a wall
+// would reflect) -- on odd steps in the step kernel, after even steps also
+// in every read of the state -- and on odd steps it writes each population
+// leaving across the face to its own slot opp(i).  So one swap after every
+// step makes the slab behave as part of the whole box:
 //
 //   slot i of face node (y, z)  <-  slot opp(i) of the neighbour's face node
 //                                   (y - c_iy, z - c_iz)
@@ -16,12 +16,12 @@
 // for every population i whose c_ix points into the slab (c_ix = +1 at the
 // face x = 0, -1 at x = nx - 1), y periodic, and only where z - c_iz lies
 // inside the box (otherwise the population meets the top or bottom wall and
-// the reflected value in the node's own slot is the right one).  Before the
-// odd step this hands each face node the post-collision populations of its
-// upwind neighbours across the face; after it, it hands each neighbour the
-// populations the face node pushed across.  Both sides pack before either
-// unpacks (a swap), since each unpack overwrites the slots the other side
-// sends.
+// the reflected value in the node's own slot is the right one).  After an
+// even step this hands each face node the post-collision populations of its
+// upwind neighbours across the face; after an odd step it hands each
+// neighbour the populations the face node pushed across.  Both sides pack
+// before either unpacks (a swap), since each unpack overwrites the slots the
+// other side sends.
 //
 // Face buffer of one slab face: the face's populations with c_ix = +1 (face
 // 0) or -1 (face 1), fluid directions in increasing index then scalar ones,

@@ -4,11 +4,12 @@ group, one slab per GPU.
 The box of nx columns is cut along x (the direction the current travels)
 into `world` slabs of whole tiles of `align` columns.  Each rank runs its slab
 as an ordinary context of the library (lbm_params.x_offset / nx_global), with
-walls at its x ends to the step kernels; around every odd AA step, once
-before and once after it, touching faces swap their face buffers
-(lbm_halo_pack, the exchange, lbm_halo_unpack), which makes the slab faces
-fluid.  With periodic x the ring closes over the last and first slab.  The
-result equals the whole-box run bit for bit.
+walls at its x ends to the step kernels; after every step touching faces
+swap their face buffers (lbm_halo_pack, the exchange, lbm_halo_unpack), which
+makes the slab faces fluid for the next step and for every read of the state
+in between (diagnostics, lbm_get_state).  With periodic x the ring closes
+over the last and first slab.  The result equals the whole-box run bit for
+bit.
 
 Exchange: NCCL point-to-point on device buffers, or any other backend (gloo)
 through pinned host copies.  The diagnostics sum F_w and the FP64 budgets
@@ -119,13 +120,24 @@ class SlabLattice:
         for f in faces:
             self.lat.halo_unpack(f, self.recv[f])
 
+    @property
+    def stream(self):
+        return self.lat.stream
+
+    @property
+    def N(self) -> int:
+        """Nodes of this rank's slab."""
+        return self.local.nx * self.local.ny * self.local.nz
+
+    def set_scalar(self, chi0_local):
+        """Re-initialises the slab from its part of a scalar field (the slab's
+        N floats, host or device)."""
+        self.lat.set_scalar(chi0_local)
+
     def step(self, n: int = 1):
         for _ in range(n):
-            odd = self.world > 1 and self.lat.next_step_odd
-            if odd:
-                self._exchange()
             self.lat.step(1)
-            if odd:
+            if self.world > 1:
                 self._exchange()
 
     # -- diagnostics -------------------------------------------------------------

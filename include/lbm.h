@@ -105,8 +105,10 @@ typedef enum lbm_storage {
                                      was misaligned): the step is incomplete */
 
 typedef struct lbm_params {
-    int32_t nx, ny, nz;       /* nodes; 1 <= nx, ny, nz; nx*ny*nz < 2^31;
-                                 (Q+NS)*nx*ny*nz < 2^32; ny, nz <= 65535 */
+    int32_t nx, ny, nz;       /* nodes; 1 <= nx, ny, nz; nx*ny*nz < 2^31; ny, nz <= 65535.
+                                 Boxes with (Q+NS)*nx*ny*nz >= 2^32 step with 64-bit
+                                 element offsets; lbm_step_save and the adjoint entry
+                                 points need (Q+NS)*nx*ny*nz < 2^32 (LBM_ERR_STATE) */
     int32_t model;            /* lbm_model */
     int32_t storage;          /* lbm_storage */
     int32_t flags;            /* LBM_FLAG_* */

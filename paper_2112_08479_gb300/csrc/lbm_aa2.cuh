@@ -134,7 +134,7 @@ __device__ __forceinline__ bool block_interior2(const KParams& kp) {
 // reads and writes exactly the elements it owns in the AA step, so the
 // in-place update stays race-free.
 template <int Q, bool ODD, typename S, int D0 = 0, bool R32 = false, bool ZW = true,
-          bool FAST = false>
+          bool FAST = false, typename Off = unsigned>
 __device__ __forceinline__ void gather2(const KParams& kp, const S* __restrict__ a,
                                         const Stencil2& st, float (&v0)[Q], float (&v1)[Q]) {
     const unsigned N = kp.N;
@@ -148,12 +148,12 @@ __device__ __forceinline__ void gather2(const KParams& kp, const S* __restrict__
             if (st.active) PairIO<float>::ld(rest_row(a, Q, N) + st.n, P0[k], P1[k]);
             continue;
         }
-        unsigned off = (unsigned)k * N + st.n;
+        Off off = (Off)k * N + st.n;
         if (ODD && i != 0) {
             const int dx = -cx27(i), dy = -cy27(i), dz = -cz27(i);
-            const unsigned row = (unsigned)(opp(i) - D0) * N + st.zr[dz + 1] + st.yr[dy + 1];
+            const Off row = (Off)(opp(i) - D0) * N + st.zr[dz + 1] + st.yr[dy + 1];
             if (FAST && dx != 0) {
-                const unsigned e = row + st.x + (unsigned)dx;
+                const Off e = row + st.x + (Off)dx;
                 P0[k] = Store<S>::ld(a + e);
                 P1[k] = Store<S>::ld(a + e + 1);
                 continue;
@@ -169,9 +169,9 @@ __device__ __forceinline__ void gather2(const KParams& kp, const S* __restrict__
         E[k] = 0.0f;
         const int dx = -cx27(i), dy = -cy27(i), dz = -cz27(i);
         if (ODD && !FAST && i != 0 && dx != 0) {
-            const unsigned row = (unsigned)(opp(i) - D0) * N + st.zr[dz + 1] + st.yr[dy + 1];
-            const unsigned own = (unsigned)k * N + st.n;
-            unsigned off;
+            const Off row = (Off)(opp(i) - D0) * N + st.zr[dz + 1] + st.yr[dy + 1];
+            const Off own = (Off)k * N + st.n;
+            Off off;
             bool need;
             if (dx < 0) { need = st.left; off = st.xmo ? row + st.xm : own; }
             else { need = st.right; off = st.xp2o ? row + st.xp2 : own + 1; }
@@ -205,7 +205,7 @@ __device__ __forceinline__ void gather2(const KParams& kp, const S* __restrict__
 // under a predicate (pair stores for the interior lanes, single-element
 // stores for the edge lanes, pair stores into the own slots at a z wall).
 template <int Q, bool ODD, typename S, int D0 = 0, bool R32 = false, bool ZW = true,
-          bool FAST = false>
+          bool FAST = false, typename Off = unsigned>
 __device__ __forceinline__ void scatter2(const KParams& kp, S* __restrict__ a, const Stencil2& st,
                                          const float (&v0)[Q], const float (&v1)[Q]) {
     const unsigned N = kp.N;
@@ -227,15 +227,15 @@ __device__ __forceinline__ void scatter2(const KParams& kp, S* __restrict__ a, c
             if (st.active) PairIO<float>::st(rest_row(a, Q, N) + st.n, v0[k], v1[k]);
             continue;
         }
-        const unsigned own = (unsigned)(opp(i) - D0) * N + st.n;
+        const Off own = (Off)(opp(i) - D0) * N + st.n;
         if (!ODD || i == 0) {
             if (st.active) PairIO<S>::st(a + own, v0[k], v1[k]);
             continue;
         }
         const bool in = !ZWe || st.zo[dz + 1];
-        const unsigned row = (unsigned)k * N + st.zr[dz + 1] + st.yr[dy + 1];
+        const Off row = (Off)k * N + st.zr[dz + 1] + st.yr[dy + 1];
         if (FAST && dx != 0) {
-            const unsigned e = row + st.x + (unsigned)dx;
+            const Off e = row + st.x + (Off)dx;
             Store<S>::st(a + e, v0[k]);
             Store<S>::st(a + e + 1, v1[k]);
             continue;

@@ -53,6 +53,17 @@ __device__ __forceinline__ void axis_inverse_vjp(float s, float v, float d0, flo
     gv += 2.0f * (v * k0 + d1) * (ga - g0) + gb * k0;
 }
 
+// The same, also adding to dot the value of sum_j g_j p(j) over the line's
+// outputs, gm p(-1) + g0 p(0) + gp p(+1), which for this affine stage is
+// gd . (d0, d1, d2) + s ((ga - g0) v^2 + gb v) (d2: the line's third input).
+__device__ __forceinline__ void axis_inverse_vjp(float s, float v, float d0, float d1, float gm,
+                                                 float g0, float gp, float& gd0, float& gd1,
+                                                 float& gd2, float& gv, float d2, float& dot) {
+    axis_inverse_vjp(s, v, d0, d1, gm, g0, gp, gd0, gd1, gd2, gv);
+    const float ga = 0.5f * (gp + gm), gb = 0.5f * (gp - gm);
+    dot += gd0 * d0 + gd1 * d1 + gd2 * d2 + s * ((ga - g0) * (v * v) + gb * v);
+}
+
 // One reverse step: lam_n = C(s_n)^T P^T lam_{n+1} + w_fw dF_w/ds_n, with P^T
 // reading lam_{n+1} where each post-collision population was pushed and C^T
 // the reverse-mode derivative of collide_cumulant<7> written out by hand
@@ -94,19 +105,11 @@ __global__ void __launch_bounds__(128, LBM_CUM_ADJ_MINB) cumulant_adjoint_kernel
     for (int k = 0; k < 7; ++k) chit += p[k];
     const float chi = 1.0f + chit;
     const float Fx = kp.gx * chi, Fy = kp.gy * chi, Fz = kp.gz * chi;
-    float drho = f[0], jx = 0.0f, jy = 0.0f, jz = 0.0f;
-    float mxx = 0.0f, myy = 0.0f, mzz = 0.0f, mxy = 0.0f, mxz = 0.0f, myz = 0.0f;
-#pragma unroll
-    for (int i = 1; i < 27; i += 2) {
-        const float sm = f[i] + f[i + 1], dm = f[i] - f[i + 1];
-        drho += sm;
-        if (cx27(i)) { jx += cx27(i) * dm; mxx += sm; }
-        if (cy27(i)) { jy += cy27(i) * dm; myy += sm; }
-        if (cz27(i)) { jz += cz27(i) * dm; mzz += sm; }
-        if (cx27(i) * cy27(i)) mxy += cx27(i) * cy27(i) * sm;
-        if (cx27(i) * cz27(i)) mxz += cx27(i) * cz27(i) * sm;
-        if (cy27(i) * cz27(i)) myz += cy27(i) * cz27(i) * sm;
-    }
+    // the forward's moments, summed by lines as it sums them
+    const Moments2 mo = moments_by_lines(f);
+    const float drho = mo.drho, jx = mo.jx, jy = mo.jy, jz = mo.jz;
+    const float mxx = mo.mxx, myy = mo.myy, mzz = mo.mzz, mxy = mo.mxy, mxz = mo.mxz,
+                myz = mo.myz;
     const float rho = 1.0f + drho, irho = 1.0f / rho;
     const float vx = jx * irho, vy = jy * irho, vz = jz * irho;
     const float d3 = drho * (1.0f / 3.0f);
@@ -161,21 +164,26 @@ __global__ void __launch_bounds__(128, LBM_CUM_ADJ_MINB) cumulant_adjoint_kernel
     const float omp = 1.0f / kp.taup0;
 
     // ---- reverse ----
-    // f*_i - w_i = drho w_i + rho (P_i - w_i), P from the x-stage
-    float gdrho = 0.0f, gux = 0.0f, guy = 0.0f, guz = 0.0f;
+    // f*_i - w_i = drho w_i + rho P_i with P_i the deviations the x-stage
+    // returns, so d/d drho = sum_i mu_i (w_i + P_i).  The x-stage is affine
+    // in its line (d0, d1, d2) with the rest offset s, so sum over a line of
+    // mu P = (gd . d + s ((ga - g0) v^2 + gb v)) / rho for the adjoints gd the
+    // stage's reverse returns from (rho mu): no forward x-stage is needed.
+    float gux = 0.0f, guy = 0.0f, guz = 0.0f, smuP = 0.0f;
     float gB[3][3][3];
 #pragma unroll
     for (int b = 0; b < 3; ++b)
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            float pm, p0, pp;
-            axis_inverse(W1[b] * W1[c], ux, B[0][b][c], B[1][b][c], B[2][b][c], pm, p0, pp);
             const int im = dir27(-1, b - 1, c - 1), i0 = dir27(0, b - 1, c - 1),
                       ip = dir27(1, b - 1, c - 1);
-            gdrho += mu[im] * (w27(im) + pm) + mu[i0] * (w27(i0) + p0) + mu[ip] * (w27(ip) + pp);
             axis_inverse_vjp(W1[b] * W1[c], ux, B[0][b][c], B[1][b][c], rho * mu[im], rho * mu[i0],
-                             rho * mu[ip], gB[0][b][c], gB[1][b][c], gB[2][b][c], gux);
+                             rho * mu[ip], gB[0][b][c], gB[1][b][c], gB[2][b][c], gux,
+                             B[2][b][c], smuP);
         }
+    float gdrho = smuP * irho;
+#pragma unroll
+    for (int i = 0; i < 27; ++i) gdrho += w27(i) * mu[i];
     float gA[3][3][3];
 #pragma unroll
     for (int a = 0; a < 3; ++a)

@@ -55,8 +55,6 @@ const char* check(const lbm_params* p) {
         return "the D3Q27 scalar runs with the cumulant model";
     if (p->model == LBM_CUMULANT_Q27 && p->scalar == LBM_SCALAR_Q6)
         return "the D3Q6 scalar runs with the BGK model";
-    if ((double)(q_of(p) + ns_of(p)) * p->nx * p->ny * p->nz >= 4294967296.0)
-        return "(Q+NS)*nx*ny*nz must be < 2^32 (32-bit element offsets)";
     if (p->storage != LBM_FP32 && p->storage != LBM_FP16S && p->storage != LBM_BF16S)
         return "unknown storage";
     if (p->flags & ~(LBM_FLAG_NO_COLLIDE | LBM_FLAG_PERIODIC_X | LBM_FLAG_PERIODIC_Z |
@@ -136,6 +134,8 @@ KParams kparams(const lbm_params* p) {
     // the correctly rounded FP32 quotient, bit-identical to 1.0f / taup0 on
     // the device, so that a kernel may take either form
     k.omp0 = 1.0f / k.taup0;
+    // 64-bit element offsets in the step kernels once (Q + NS) N reaches 2^32
+    k.wide = (double)(q_of(p) + ns_of(p)) * k.N >= 4294967296.0 ? 1 : 0;
     k.x_off = p->x_offset;
     k.nxg = p->nx_global ? p->nx_global : p->nx;
     return k;
@@ -150,6 +150,17 @@ lbm_status arg_fail(lbm_ctx* c, const char* what) {
     if (c) snprintf(c->err, sizeof c->err, "%s", what);
     else snprintf(g_err, sizeof g_err, "%s", what);
     return LBM_ERR_ARG;
+}
+
+// The saved steps and the adjoint kernels use 32-bit element offsets of the
+// canonical layout: boxes with (Q + NS) N < 2^32.
+lbm_status narrow_check(lbm_ctx* c) {
+    if (c->kp.wide) {
+        snprintf(c->err, sizeof c->err,
+                 "saved steps and the adjoint need (Q + NS) * nx * ny * nz < 2^32");
+        return LBM_ERR_STATE;
+    }
+    return LBM_OK;
 }
 
 }  // namespace
@@ -259,6 +270,7 @@ lbm_status lbm_step(lbm_ctx* c, int32_t nsteps) {
 lbm_status lbm_step_save(lbm_ctx* c, float* state_out) {
     if (!c) return arg_fail(nullptr, "ctx is NULL");
     if (!state_out) return arg_fail(c, "state_out is NULL");
+    if (lbm_status s = narrow_check(c); s != LBM_OK) return s;
     cudaError_t e = launch_step(c->kp, kind(&c->p), c->odd != 0, c->v.f, c->v.phi,
                                 state_out, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "step launch");
@@ -352,6 +364,7 @@ cudaStream_t stream_or_ctx(lbm_ctx* c, void* stream) {
 }
 
 lbm_status sweep_check(lbm_ctx* c) {
+    if (lbm_status s = narrow_check(c); s != LBM_OK) return s;
     if (c->p.storage != LBM_FP32 || c->p.scalar != LBM_SCALAR_Q7) {
         snprintf(c->err, sizeof c->err,
                  "the adjoint sweep exists for the D3Q7 scalar and FP32 storage");
@@ -361,6 +374,7 @@ lbm_status sweep_check(lbm_ctx* c) {
 }
 
 lbm_status adjoint_model_check(lbm_ctx* c) {
+    if (lbm_status s = narrow_check(c); s != LBM_OK) return s;
     if (c->p.scalar != LBM_SCALAR_Q7) {
         snprintf(c->err, sizeof c->err, "the adjoint exists for the D3Q7 scalar");
         return LBM_ERR_STATE;

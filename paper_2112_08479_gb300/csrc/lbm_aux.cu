@@ -30,8 +30,8 @@ __device__ __forceinline__ void node_macros(const KParams& kp, const S* __restri
     constexpr int NS = ScalarLat<SL>::NS;
     const Stencil st = make_stencil(kp, x, y, z);
     float fv[Q], pv[NS];
-    gather<Q, ODD>(kp, f, st, fv);
-    gather<NS, ODD, S, ScalarLat<SL>::D0, rest32<S, SL>()>(kp, phi, st, pv);
+    gather<Q, ODD, S, 0, false, true, size_t>(kp, f, st, fv);
+    gather<NS, ODD, S, ScalarLat<SL>::D0, rest32<S, SL>(), true, size_t>(kp, phi, st, pv);
     float c = 0.0f;   // chi - 1 (Phi is held as Phi - w)
 #pragma unroll
     for (int k = 0; k < NS; ++k) c += pv[k];
@@ -135,8 +135,8 @@ __global__ void get_state_kernel(KParams kp, const S* __restrict__ f, const S* _
     const Stencil st = make_stencil(kp, x, y, z);
     const unsigned n = st.n;
     float fv[Q], pv[NS];
-    gather<Q, ODD>(kp, f, st, fv);
-    gather<NS, ODD, S, ScalarLat<SL>::D0, rest32<S, SL>()>(kp, phi, st, pv);
+    gather<Q, ODD, S, 0, false, true, size_t>(kp, f, st, fv);
+    gather<NS, ODD, S, ScalarLat<SL>::D0, rest32<S, SL>(), true, size_t>(kp, phi, st, pv);
     const size_t N = kp.N;
 #pragma unroll
     for (int i = 0; i < Q; ++i) dst[(size_t)i * N + n] = is16<S>() ? fv[i] * kp.isf : fv[i];

@@ -27,7 +27,7 @@
 
 namespace lbmgpu {
 
-template <bool ODD, bool SAVE, typename S, int SL>
+template <bool ODD, bool SAVE, typename S, int SL, typename Off = unsigned>
 __global__ void __launch_bounds__(128, LBM_STEP_MINB) bgk_step_kernel(KParams kp, S* __restrict__ f,
                                                        S* __restrict__ phi,
                                                        float* __restrict__ save) {
@@ -39,8 +39,8 @@ __global__ void __launch_bounds__(128, LBM_STEP_MINB) bgk_step_kernel(KParams kp
     constexpr int NS = ScalarLat<SL>::NS, D0 = ScalarLat<SL>::D0;
     constexpr bool R32 = rest32<S, SL>();
     float fv[19], pv[NS];
-    gather<19, ODD>(kp, f, st, fv);
-    gather<NS, ODD, S, D0, R32>(kp, phi, st, pv);
+    gather<19, ODD, S, 0, false, true, Off>(kp, f, st, fv);
+    gather<NS, ODD, S, D0, R32, true, Off>(kp, phi, st, pv);
     constexpr bool s16 = !std::is_same<S, float>::value;   // populations in storage units
     if (SAVE) {
         const size_t N = kp.N;
@@ -51,8 +51,8 @@ __global__ void __launch_bounds__(128, LBM_STEP_MINB) bgk_step_kernel(KParams kp
     }
     if (!(kp.flags & LBM_FLAG_NO_COLLIDE)) collide_bgk<s16, SL>(kp, fv, pv);
     if constexpr (R32) feed_rest<S>(pv);
-    scatter<19, ODD>(kp, f, st, fv);
-    scatter<NS, ODD, S, D0, R32>(kp, phi, st, pv);
+    scatter<19, ODD, S, 0, false, true, Off>(kp, f, st, fv);
+    scatter<NS, ODD, S, D0, R32, true, Off>(kp, phi, st, pv);
 }
 
 
@@ -69,15 +69,15 @@ __global__ void __launch_bounds__(128, LBM_STEP_MINB) bgk_step_kernel(KParams kp
 #define LBM_STEP2_MINB16 LBM_STEP2_MINB
 #endif
 
-template <bool ODD, bool SAVE, typename S, int SL, bool ZW, bool FAST>
+template <bool ODD, bool SAVE, typename S, int SL, bool ZW, bool FAST, typename Off>
 __device__ __forceinline__ void bgk_step2_body(const KParams& kp, S* __restrict__ f,
                                                S* __restrict__ phi, float* __restrict__ save,
                                                const Stencil2& st) {
     constexpr int NS = ScalarLat<SL>::NS, D0 = ScalarLat<SL>::D0;
     constexpr bool R32 = rest32<S, SL>();
     float f0[19], f1[19], p0[NS], p1[NS];
-    gather2<19, ODD, S, 0, false, ZW, FAST>(kp, f, st, f0, f1);
-    gather2<NS, ODD, S, D0, R32, ZW, FAST>(kp, phi, st, p0, p1);
+    gather2<19, ODD, S, 0, false, ZW, FAST, Off>(kp, f, st, f0, f1);
+    gather2<NS, ODD, S, D0, R32, ZW, FAST, Off>(kp, phi, st, p0, p1);
     constexpr bool s16 = !std::is_same<S, float>::value;   // populations in storage units
     if (SAVE && st.active) {
         const unsigned N = kp.N;
@@ -95,15 +95,15 @@ __device__ __forceinline__ void bgk_step2_body(const KParams& kp, S* __restrict_
         collide_bgk<s16, SL>(kp, f1, p1);
     }
     if constexpr (R32) feed_rest2<S>(p0, p1);
-    scatter2<19, ODD, S, 0, false, ZW, FAST>(kp, f, st, f0, f1);
-    scatter2<NS, ODD, S, D0, R32, ZW, FAST>(kp, phi, st, p0, p1);
+    scatter2<19, ODD, S, 0, false, ZW, FAST, Off>(kp, f, st, f0, f1);
+    scatter2<NS, ODD, S, D0, R32, ZW, FAST, Off>(kp, phi, st, p0, p1);
 }
 
 // Two x-adjacent nodes per thread (nx even): paired population accesses, see
 // lbm_aa2.cuh.  Same arithmetic per node as bgk_step_kernel.  On odd steps
 // the rows away from the z walls (uniform per block) take a body without the
 // wall selects.
-template <bool ODD, bool SAVE, typename S, int SL>
+template <bool ODD, bool SAVE, typename S, int SL, typename Off = unsigned>
 __global__ void __launch_bounds__(128, std::is_same<S, float>::value ? LBM_STEP2_MINB : LBM_STEP2_MINB16) bgk_step2_kernel(KParams kp, S* __restrict__ f,
                                                                     S* __restrict__ phi,
                                                                     float* __restrict__ save) {
@@ -112,11 +112,11 @@ __global__ void __launch_bounds__(128, std::is_same<S, float>::value ? LBM_STEP2
     const int z = blockIdx.z;
     const bool zwall = ODD && (!LBM_BGK_ZSPLIT ||
                                (!(kp.flags & LBM_FLAG_PERIODIC_Z) && (z == 0 || z == kp.nz - 1)));
-    if (!ODD) bgk_step2_body<ODD, SAVE, S, SL, false, false>(kp, f, phi, save, st);
+    if (!ODD) bgk_step2_body<ODD, SAVE, S, SL, false, false, Off>(kp, f, phi, save, st);
     else if (LBM_BGK_FAST && block_interior2(kp))
-        bgk_step2_body<ODD, SAVE, S, SL, false, true>(kp, f, phi, save, st);
-    else if (!zwall) bgk_step2_body<ODD, SAVE, S, SL, false, false>(kp, f, phi, save, st);
-    else bgk_step2_body<ODD, SAVE, S, SL, true, false>(kp, f, phi, save, st);
+        bgk_step2_body<ODD, SAVE, S, SL, false, true, Off>(kp, f, phi, save, st);
+    else if (!zwall) bgk_step2_body<ODD, SAVE, S, SL, false, false, Off>(kp, f, phi, save, st);
+    else bgk_step2_body<ODD, SAVE, S, SL, true, false, Off>(kp, f, phi, save, st);
 }
 
 #ifndef LBM_BGK_QUAD
@@ -159,7 +159,7 @@ __device__ __forceinline__ unsigned put16(unsigned w, unsigned b, int hi) {
 // time.  Same arithmetic per node as bgk_step_kernel.  Odd steps stay with
 // bgk_step2_kernel: there the x-shifted rows of a packed quad need shuffles
 // and byte permutes and measured slower than the paired form.
-template <typename S, int SL>
+template <typename S, int SL, typename Off = unsigned>
 __global__ void __launch_bounds__(128, LBM_STEP4_MINB) bgk_even4_kernel(KParams kp, S* __restrict__ f,
                                                                        S* __restrict__ phi) {
     const unsigned x = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
@@ -174,11 +174,11 @@ __global__ void __launch_bounds__(128, LBM_STEP4_MINB) bgk_even4_kernel(KParams 
     uint2 wf[19], wp[NS];
     float4 r = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 #pragma unroll
-    for (int i = 0; i < 19; ++i) wf[i] = ld_pop(fw + (((unsigned)i * N + n) >> 2));
+    for (int i = 0; i < 19; ++i) wf[i] = ld_pop(fw + (((Off)i * N + n) >> 2));
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
         if (R32 && k == 0) r = ld_pop(rest);
-        else wp[k] = ld_pop(pw + (((unsigned)k * N + n) >> 2));
+        else wp[k] = ld_pop(pw + (((Off)k * N + n) >> 2));
     }
     const bool collide = !(kp.flags & LBM_FLAG_NO_COLLIDE);
 #pragma unroll
@@ -209,44 +209,60 @@ __global__ void __launch_bounds__(128, LBM_STEP4_MINB) bgk_even4_kernel(KParams 
         }
     }
 #pragma unroll
-    for (int i = 0; i < 19; ++i) st_pop(fw + (((unsigned)opp(i) * N + n) >> 2), wf[i]);
+    for (int i = 0; i < 19; ++i) st_pop(fw + (((Off)opp(i) * N + n) >> 2), wf[i]);
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
         if (R32 && k == 0) st_pop(rest, r);
-        else st_pop(pw + (((unsigned)(opp(k + D0) - D0) * N + n) >> 2), wp[k]);
+        else st_pop(pw + (((Off)(opp(k + D0) - D0) * N + n) >> 2), wp[k]);
     }
 }
 
-template <typename S, int SL>
-static cudaError_t launch_bgk_typed(const KParams& kp, bool odd, S* f, S* phi, float* save,
-                                   cudaStream_t st) {
+template <typename S, int SL, typename Off>
+static cudaError_t launch_bgk_off(const KParams& kp, bool odd, S* f, S* phi, float* save,
+                                  cudaStream_t st) {
     if constexpr (LBM_BGK_QUAD && !std::is_same<S, float>::value) {
         if (!odd && !save && kp.nx % 4 == 0 && !(kp.flags & LBM_FLAG_ONE_NODE)) {
             dim3 block(128), grid((kp.nx / 4 + 127) / 128, kp.ny, kp.nz);
-            bgk_even4_kernel<S, SL><<<grid, block, 0, st>>>(kp, f, phi);
+            bgk_even4_kernel<S, SL, Off><<<grid, block, 0, st>>>(kp, f, phi);
             return cudaGetLastError();
         }
     }
     if constexpr (LBM_BGK_PAIR) if (kp.nx % 2 == 0 && !(kp.flags & LBM_FLAG_ONE_NODE)) {
         dim3 block(128), grid((kp.nx / 2 + 127) / 128, kp.ny, kp.nz);
         if (save) {
-            if (odd) bgk_step2_kernel<true, true, S, SL><<<grid, block, 0, st>>>(kp, f, phi, save);
-            else bgk_step2_kernel<false, true, S, SL><<<grid, block, 0, st>>>(kp, f, phi, save);
+            if constexpr (std::is_same<Off, unsigned>::value) {
+                if (odd) bgk_step2_kernel<true, true, S, SL><<<grid, block, 0, st>>>(kp, f, phi, save);
+                else bgk_step2_kernel<false, true, S, SL><<<grid, block, 0, st>>>(kp, f, phi, save);
+            } else {
+                return cudaErrorInvalidValue;   // saved steps need (Q + NS) N < 2^32
+            }
         } else {
-            if (odd) bgk_step2_kernel<true, false, S, SL><<<grid, block, 0, st>>>(kp, f, phi, nullptr);
-            else bgk_step2_kernel<false, false, S, SL><<<grid, block, 0, st>>>(kp, f, phi, nullptr);
+            if (odd) bgk_step2_kernel<true, false, S, SL, Off><<<grid, block, 0, st>>>(kp, f, phi, nullptr);
+            else bgk_step2_kernel<false, false, S, SL, Off><<<grid, block, 0, st>>>(kp, f, phi, nullptr);
         }
         return cudaGetLastError();
     }
     dim3 block(128), grid((kp.nx + 127) / 128, kp.ny, kp.nz);
     if (save) {
-        if (odd) bgk_step_kernel<true, true, S, SL><<<grid, block, 0, st>>>(kp, f, phi, save);
-        else bgk_step_kernel<false, true, S, SL><<<grid, block, 0, st>>>(kp, f, phi, save);
+        if constexpr (std::is_same<Off, unsigned>::value) {
+            if (odd) bgk_step_kernel<true, true, S, SL><<<grid, block, 0, st>>>(kp, f, phi, save);
+            else bgk_step_kernel<false, true, S, SL><<<grid, block, 0, st>>>(kp, f, phi, save);
+        } else {
+            return cudaErrorInvalidValue;
+        }
     } else {
-        if (odd) bgk_step_kernel<true, false, S, SL><<<grid, block, 0, st>>>(kp, f, phi, nullptr);
-        else bgk_step_kernel<false, false, S, SL><<<grid, block, 0, st>>>(kp, f, phi, nullptr);
+        if (odd) bgk_step_kernel<true, false, S, SL, Off><<<grid, block, 0, st>>>(kp, f, phi, nullptr);
+        else bgk_step_kernel<false, false, S, SL, Off><<<grid, block, 0, st>>>(kp, f, phi, nullptr);
     }
     return cudaGetLastError();
+}
+
+// 32-bit element offsets unless (Q + NS) N >= 2^32 (KParams::wide).
+template <typename S, int SL>
+static cudaError_t launch_bgk_typed(const KParams& kp, bool odd, S* f, S* phi, float* save,
+                                   cudaStream_t st) {
+    if (kp.wide) return launch_bgk_off<S, SL, size_t>(kp, odd, f, phi, save, st);
+    return launch_bgk_off<S, SL, unsigned>(kp, odd, f, phi, save, st);
 }
 
 template <int SL>

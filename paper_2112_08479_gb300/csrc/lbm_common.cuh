@@ -92,6 +92,7 @@ struct KParams {
     float omp0;          // 1 / taup0: the scalar rate of the cumulant model (molecular D)
     int* devflags;       // sticky device flags (LBM_DEVFLAG_*) of the context
     int x_off, nxg;      // x-slab: global x of local column 0, nx of the whole box
+    int wide;            // (Q + NS) N >= 2^32: 64-bit element offsets in the step kernels
 };
 
 // ---------------------------------------------------------------------------
@@ -200,8 +201,10 @@ __device__ __forceinline__ void feed_rest(float (&p)[NS]) {
 // Neighbourhood of one node, computed once per thread: the node indices of
 // the rows (y + dy, z + dz) and the columns x + dx, with y always periodic
 // and x, z bounded by half-way bounce-back walls unless the periodic flags
-// are set.  Element offsets are 32-bit: the library accepts only sizes with
-// (Q + 7) * N < 2^32.
+// are set.  Node indices are 32-bit (N < 2^31); element offsets row * N + n
+// are computed in the type Off of the gather / scatter: 32-bit in the step
+// kernels where (Q + NS) N < 2^32 (KParams::wide false), 64-bit otherwise and
+// in the auxiliary kernels.
 struct Stencil {
     unsigned n;        // this node
     unsigned zr[3];    // (z + dz) * nx * ny for dz = -1, 0, 1
@@ -251,7 +254,8 @@ __device__ __forceinline__ unsigned nbr(const Stencil& s, int dx, int dy, int dz
 // R32: population 0 (direction 0) lives in the FP32 rest row (rest_row).
 // W: the node may have a wall neighbour; false when every neighbour is known
 // to be in the fluid (the wall selects are then skipped).
-template <int Q, bool ODD, typename S, int D0 = 0, bool R32 = false, bool W = true>
+template <int Q, bool ODD, typename S, int D0 = 0, bool R32 = false, bool W = true,
+          typename Off = unsigned>
 __device__ __forceinline__ void gather(const KParams& kp, const S* __restrict__ a,
                                        const Stencil& st, float (&v)[Q]) {
     const unsigned N = kp.N;
@@ -262,17 +266,18 @@ __device__ __forceinline__ void gather(const KParams& kp, const S* __restrict__ 
             v[k] = ld_pop(rest_row(a, Q, N) + st.n);
             continue;
         }
-        unsigned off = (unsigned)k * N + st.n;
+        Off off = (Off)k * N + st.n;
         if (ODD && d != 0) {
             bool in;
             const unsigned s = nbr(st, -cx27(d), -cy27(d), -cz27(d), in);
-            off = (!W || in) ? (unsigned)(opp(d) - D0) * N + s : off;
+            off = (!W || in) ? (Off)(opp(d) - D0) * N + s : off;
         }
         v[k] = Store<S>::ld(a + off);
     }
 }
 
-template <int Q, bool ODD, typename S, int D0 = 0, bool R32 = false, bool W = true>
+template <int Q, bool ODD, typename S, int D0 = 0, bool R32 = false, bool W = true,
+          typename Off = unsigned>
 __device__ __forceinline__ void scatter(const KParams& kp, S* __restrict__ a, const Stencil& st,
                                         const float (&v)[Q]) {
     const unsigned N = kp.N;
@@ -283,11 +288,11 @@ __device__ __forceinline__ void scatter(const KParams& kp, S* __restrict__ a, co
             st_pop(rest_row(a, Q, N) + st.n, v[k]);
             continue;
         }
-        unsigned off = (unsigned)(opp(d) - D0) * N + st.n;
+        Off off = (Off)(opp(d) - D0) * N + st.n;
         if (ODD && d != 0) {
             bool in;
             const unsigned t = nbr(st, cx27(d), cy27(d), cz27(d), in);
-            off = (!W || in) ? (unsigned)k * N + t : off;
+            off = (!W || in) ? (Off)k * N + t : off;
         }
         Store<S>::st(a + off, v[k]);
     }

@@ -25,7 +25,7 @@ namespace lbmgpu {
 #ifndef LBM_CUM_WSPLIT
 #define LBM_CUM_WSPLIT 1
 #endif
-template <bool ODD, bool SAVE, typename S, int SL, bool W>
+template <bool ODD, bool SAVE, typename S, int SL, bool W, typename Off>
 __device__ __forceinline__ void cumulant_step_body(const KParams& kp, S* __restrict__ f,
                                                    S* __restrict__ phi, float* __restrict__ save,
                                                    const Stencil& st) {
@@ -33,8 +33,8 @@ __device__ __forceinline__ void cumulant_step_body(const KParams& kp, S* __restr
     constexpr int NS = ScalarLat<SL>::NS;
     constexpr bool R32 = rest32<S, SL>();
     float fv[27], pv[NS];
-    gather<27, ODD, S, 0, false, W>(kp, f, st, fv);
-    gather<NS, ODD, S, 0, R32, W>(kp, phi, st, pv);
+    gather<27, ODD, S, 0, false, W, Off>(kp, f, st, fv);
+    gather<NS, ODD, S, 0, R32, W, Off>(kp, phi, st, pv);
     constexpr bool s16 = !std::is_same<S, float>::value;   // populations in storage units
     constexpr bool fold = s16 && SL == 7;                  // the collision applies the scales
     if (SAVE) {
@@ -58,15 +58,15 @@ __device__ __forceinline__ void cumulant_step_body(const KParams& kp, S* __restr
         for (int k = 0; k < NS; ++k) pv[k] *= kp.sp;
     }
     if constexpr (R32) feed_rest<S>(pv);
-    scatter<27, ODD, S, 0, false, W>(kp, f, st, fv);
-    scatter<NS, ODD, S, 0, R32, W>(kp, phi, st, pv);
+    scatter<27, ODD, S, 0, false, W, Off>(kp, f, st, fv);
+    scatter<NS, ODD, S, 0, R32, W, Off>(kp, phi, st, pv);
 }
 
 // One node per thread.  On odd steps the blocks with no wall neighbour
 // (uniform per block) take a body without the wall selects (D3Q7 scalar:
 // measured 0.6-0.9 % faster; with the D3Q27 scalar the second body costs
 // registers and was 4 % slower, so that instantiation keeps one body).
-template <bool ODD, bool SAVE, typename S, int SL>
+template <bool ODD, bool SAVE, typename S, int SL, typename Off = unsigned>
 __global__ void __launch_bounds__(128, SL == 27 ? LBM_Q27_MINB : LBM_CUM_MINB) cumulant_step_kernel(KParams kp, S* __restrict__ f,
                                                             S* __restrict__ phi,
                                                             float* __restrict__ save) {
@@ -74,12 +74,12 @@ __global__ void __launch_bounds__(128, SL == 27 ? LBM_Q27_MINB : LBM_CUM_MINB) c
     if (x >= kp.nx) return;
     const Stencil st = make_stencil(kp, x, blockIdx.y, blockIdx.z);
     if constexpr (SL == 27) {
-        cumulant_step_body<ODD, SAVE, S, SL, true>(kp, f, phi, save, st);
+        cumulant_step_body<ODD, SAVE, S, SL, true, Off>(kp, f, phi, save, st);
     } else {
         if (!ODD || (LBM_CUM_WSPLIT && block_interior(kp)))
-            cumulant_step_body<ODD, SAVE, S, SL, false>(kp, f, phi, save, st);
+            cumulant_step_body<ODD, SAVE, S, SL, false, Off>(kp, f, phi, save, st);
         else
-            cumulant_step_body<ODD, SAVE, S, SL, true>(kp, f, phi, save, st);
+            cumulant_step_body<ODD, SAVE, S, SL, true, Off>(kp, f, phi, save, st);
     }
 }
 
@@ -87,6 +87,12 @@ template <typename S, int SL>
 static cudaError_t launch_cumulant_typed(const KParams& kp, bool odd, S* f, S* phi, float* save,
                                         cudaStream_t st) {
     dim3 block(128), grid((kp.nx + 127) / 128, kp.ny, kp.nz);
+    if (kp.wide) {   // (Q + NS) N >= 2^32: 64-bit element offsets; no saved steps
+        if (save) return cudaErrorInvalidValue;
+        if (odd) cumulant_step_kernel<true, false, S, SL, size_t><<<grid, block, 0, st>>>(kp, f, phi, nullptr);
+        else cumulant_step_kernel<false, false, S, SL, size_t><<<grid, block, 0, st>>>(kp, f, phi, nullptr);
+        return cudaGetLastError();
+    }
     if (save) {
         if (odd) cumulant_step_kernel<true, true, S, SL><<<grid, block, 0, st>>>(kp, f, phi, save);
         else cumulant_step_kernel<false, true, S, SL><<<grid, block, 0, st>>>(kp, f, phi, save);

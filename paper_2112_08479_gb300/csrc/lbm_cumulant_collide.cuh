@@ -52,26 +52,14 @@ __host__ __device__ constexpr int dir27(int x, int y, int z) {
     return t[(x + 1) * 9 + (y + 1) * 3 + (z + 1)];
 }
 
-// SL: scalar lattice, D3Q7 BGK or D3Q27 factorized central moments.
-// SCALED (16-bit storage, D3Q7 scalar): f and p hold the storage units
-// scale_f (f - w) and scale_phi (Phi - w); the scales are applied to the few
-// moments and output coefficients instead of to every population.
-template <int SL = 7, bool SCALED = false>
-__device__ __forceinline__ void collide_cumulant(const KParams& kp, float (&f)[27],
-                                                 float (&p)[ScalarLat<SL>::NS]) {
-    static_assert(SL == 7 || SL == 27, "the cumulant model runs with the D3Q7 or D3Q27 scalar");
-    static_assert(!(SCALED && SL == 27), "the D3Q27 scalar takes unscaled populations");
-    constexpr int NS = ScalarLat<SL>::NS;
-    float chs = 0.0f;  // chi - 1 in storage units (Phi is held as Phi - w)
-#pragma unroll
-    for (int k = 0; k < NS; ++k) chs += p[k];
-    const float chit = SCALED ? chs * kp.isp : chs;
-    const float chi = 1.0f + chit;
-    const float Fx = kp.gx * chi, Fy = kp.gy * chi, Fz = kp.gz * chi;
-
-    // moments of order <= 2, summed by lines: along x for each (cy, cz), then
-    // along y for each cz, then along z (66 additions; term by term the ten
-    // sums take 170)
+// Moments of order <= 2 of the 27 populations (held as f - w), summed by
+// lines: along x for each (c_y, c_z), then along y for each c_z, then along
+// z (66 additions; term by term the ten sums take 170).  drho = sum f,
+// j = sum c f, m_ab = sum c_a c_b f.
+struct Moments2 {
+    float drho, jx, jy, jz, mxx, myy, mzz, mxy, mxz, myz;
+};
+__device__ __forceinline__ Moments2 moments_by_lines(const float (&f)[27]) {
     float L0[3][3], L1[3][3], L2[3][3];   // x-moments 0, 1, 2 of the line [cy + 1][cz + 1]
 #pragma unroll
     for (int b = 0; b < 3; ++b)
@@ -93,11 +81,41 @@ __device__ __forceinline__ void collide_cumulant(const KParams& kp, float (&f)[2
         m11[c] = L1[2][c] - L1[0][c];
         m20[c] = (L2[0][c] + L2[2][c]) + L2[1][c];
     }
-    float mzz = m00[2] + m00[0];
-    float drho = mzz + m00[1];
-    float jx = (m10[0] + m10[2]) + m10[1], jy = (m01[0] + m01[2]) + m01[1], jz = m00[2] - m00[0];
-    float mxx = (m20[0] + m20[2]) + m20[1], myy = (m02[0] + m02[2]) + m02[1];
-    float mxy = (m11[0] + m11[2]) + m11[1], mxz = m10[2] - m10[0], myz = m01[2] - m01[0];
+    Moments2 m;
+    m.mzz = m00[2] + m00[0];
+    m.drho = m.mzz + m00[1];
+    m.jx = (m10[0] + m10[2]) + m10[1];
+    m.jy = (m01[0] + m01[2]) + m01[1];
+    m.jz = m00[2] - m00[0];
+    m.mxx = (m20[0] + m20[2]) + m20[1];
+    m.myy = (m02[0] + m02[2]) + m02[1];
+    m.mxy = (m11[0] + m11[2]) + m11[1];
+    m.mxz = m10[2] - m10[0];
+    m.myz = m01[2] - m01[0];
+    return m;
+}
+
+// SL: scalar lattice, D3Q7 BGK or D3Q27 factorized central moments.
+// SCALED (16-bit storage, D3Q7 scalar): f and p hold the storage units
+// scale_f (f - w) and scale_phi (Phi - w); the scales are applied to the few
+// moments and output coefficients instead of to every population.
+template <int SL = 7, bool SCALED = false>
+__device__ __forceinline__ void collide_cumulant(const KParams& kp, float (&f)[27],
+                                                 float (&p)[ScalarLat<SL>::NS]) {
+    static_assert(SL == 7 || SL == 27, "the cumulant model runs with the D3Q7 or D3Q27 scalar");
+    static_assert(!(SCALED && SL == 27), "the D3Q27 scalar takes unscaled populations");
+    constexpr int NS = ScalarLat<SL>::NS;
+    float chs = 0.0f;  // chi - 1 in storage units (Phi is held as Phi - w)
+#pragma unroll
+    for (int k = 0; k < NS; ++k) chs += p[k];
+    const float chit = SCALED ? chs * kp.isp : chs;
+    const float chi = 1.0f + chit;
+    const float Fx = kp.gx * chi, Fy = kp.gy * chi, Fz = kp.gz * chi;
+
+    // moments of order <= 2, summed by lines
+    const Moments2 mo = moments_by_lines(f);
+    float drho = mo.drho, jx = mo.jx, jy = mo.jy, jz = mo.jz;
+    float mxx = mo.mxx, myy = mo.myy, mzz = mo.mzz, mxy = mo.mxy, mxz = mo.mxz, myz = mo.myz;
     if (SCALED) {
         drho *= kp.isf; jx *= kp.isf; jy *= kp.isf; jz *= kp.isf;
         mxx *= kp.isf; myy *= kp.isf; mzz *= kp.isf; mxy *= kp.isf; mxz *= kp.isf; myz *= kp.isf;

@@ -547,7 +547,8 @@ cudaError_t launch_parity(const KParams& kp, bool odd, void* f, void* phi, cudaS
 
 bool staged_step_applies(const KParams& kp, Kind k) {
     // opt-in; 16-bit storage, tiles of LBM_STAGED_ROWBYTES / 2 nodes
-    if (!(kp.flags & LBM_FLAG_TMA_STAGED) || (kp.flags & LBM_FLAG_ONE_NODE) || !kp.devflags)
+    if (!(kp.flags & LBM_FLAG_TMA_STAGED) || (kp.flags & LBM_FLAG_ONE_NODE) || !kp.devflags ||
+        kp.wide)
         return false;
     if (k.storage == LBM_FP32 || kp.nx % (LBM_STAGED_ROWBYTES / 2) != 0) return false;
     return k.model == LBM_CUMULANT_Q27 && k.scalar == LBM_SCALAR_Q7;

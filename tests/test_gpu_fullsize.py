@@ -81,3 +81,48 @@ def test_full_size_budgets_conserved():
     assert abs(d1["mass_delta"] - d0["mass_delta"]) < 1e-7 * p.N
     # the gate column starts at x0 - 1 = 255: the front has moved forward
     assert d1["front"] > d0["front"]
+
+
+@pytest.mark.parametrize("model,storage", [("cumulant", "fp16s"), ("bgk", "bf16s")])
+def test_wide_box_sampled_nodes(model, storage):
+    """A box past 32-bit element offsets: 2048 x 256 x 320 = 167.8 M nodes,
+    (Q + 7) N >= 2^32 (the cumulant's fluid rows alone reach 27 N = 4.5e9), so
+    the step kernels run with 64-bit offsets and the canonical state (22.8 GB
+    for the cumulant) is read and written with them too.  One even and one odd
+    step, sampled nodes against the oracle as above."""
+    nx, ny, nz = 2048, 256, 320
+    p = lbm.lock_exchange(nx, ny, nz, H=nz, x0=nz, u_b=0.03, Re=30000.0, model=model,
+                          storage=storage)
+    p.gprime = 1e-3
+    assert (p.Q + p.NS) * p.N >= 2**32
+    lat = lbm.Lattice(p, device="cuda")
+    lat.set_state(_random_full_state(p, 23))
+    rel = {"fp16s": 2.0**-11, "bf16s": 2.0**-8}[storage]
+    rng = np.random.default_rng(7)
+    nodes = [(0, 0, 0), (nx - 1, ny - 1, nz - 1), (nx - 1, 0, nz - 1), (1000, 200, 300)]
+    nodes += [(int(rng.integers(nx)), int(rng.integers(ny)), int(rng.integers(nz)))
+              for _ in range(8)]
+    for parity in ("even", "odd"):
+        s0 = lat.get_state()
+        lat.step(1)
+        s1 = lat.get_state()
+        s0v = s0.view(p.Q + 7, nz, ny, nx)
+        s1v = s1.view(p.Q + 7, nz, ny, nx)
+        scale = float(s0[: p.Q, :: 997].abs().max())
+        for node in nodes:
+            x, y, z = node
+            f_o, phi_o = window_oracle(p, s0v, node, 1)
+            got = s1v[:, z, y, x].cpu().numpy().astype(np.float64)
+            tol_f = rel * np.abs(f_o) * 1.001 + 1e-5 * scale
+            tol_p = rel * np.abs(phi_o) * 1.001 + 1e-6
+            col = s0v[:, z, y, x].cpu().numpy().astype(np.float64)[:, None]
+            tol_p[0] = rest_row_tol(p, col, rel)[0] + 1e-6
+            assert np.all(np.abs(got[: p.Q] - f_o) <= tol_f), (parity, node)
+            assert np.all(np.abs(got[p.Q:] - phi_o) <= tol_p), (parity, node)
+        del s0, s1, s0v, s1v
+        torch.cuda.empty_cache()
+    assert lat.diag()["flags"] == 0
+    # saved steps and the adjoint keep 32-bit canonical offsets
+    with pytest.raises(lbm.LBMError) as e:
+        lat.step_save(torch.empty(1, device="cuda"))
+    assert e.value.status == lbm.LBM_ERR_STATE

@@ -254,48 +254,56 @@ __device__ __forceinline__ unsigned nbr(const Stencil& s, int dx, int dy, int dz
 // R32: population 0 (direction 0) lives in the FP32 rest row (rest_row).
 // W: the node may have a wall neighbour; false when every neighbour is known
 // to be in the fluid (the wall selects are then skipped).
+// One population k (of Q): the read of the gather, the write of the scatter.
+template <int Q, bool ODD, typename S, int D0 = 0, bool R32 = false, bool W = true,
+          typename Off = unsigned>
+__device__ __forceinline__ float gather_one(const KParams& kp, const S* __restrict__ a,
+                                            const Stencil& st, int k) {
+    const unsigned N = kp.N;
+    const int d = k + D0;
+    if (R32 && d == 0) return ld_pop(rest_row(a, Q, N) + st.n);
+    Off off = (Off)k * N + st.n;
+    if (ODD && d != 0) {
+        bool in;
+        const unsigned s = nbr(st, -cx27(d), -cy27(d), -cz27(d), in);
+        off = (!W || in) ? (Off)(opp(d) - D0) * N + s : off;
+    }
+    return Store<S>::ld(a + off);
+}
+
+template <int Q, bool ODD, typename S, int D0 = 0, bool R32 = false, bool W = true,
+          typename Off = unsigned>
+__device__ __forceinline__ void scatter_one(const KParams& kp, S* __restrict__ a,
+                                            const Stencil& st, int k, float v) {
+    const unsigned N = kp.N;
+    const int d = k + D0;
+    if (R32 && d == 0) {
+        st_pop(rest_row(a, Q, N) + st.n, v);
+        return;
+    }
+    Off off = (Off)(opp(d) - D0) * N + st.n;
+    if (ODD && d != 0) {
+        bool in;
+        const unsigned t = nbr(st, cx27(d), cy27(d), cz27(d), in);
+        off = (!W || in) ? (Off)k * N + t : off;
+    }
+    Store<S>::st(a + off, v);
+}
+
 template <int Q, bool ODD, typename S, int D0 = 0, bool R32 = false, bool W = true,
           typename Off = unsigned>
 __device__ __forceinline__ void gather(const KParams& kp, const S* __restrict__ a,
                                        const Stencil& st, float (&v)[Q]) {
-    const unsigned N = kp.N;
 #pragma unroll
-    for (int k = 0; k < Q; ++k) {
-        const int d = k + D0;
-        if (R32 && d == 0) {
-            v[k] = ld_pop(rest_row(a, Q, N) + st.n);
-            continue;
-        }
-        Off off = (Off)k * N + st.n;
-        if (ODD && d != 0) {
-            bool in;
-            const unsigned s = nbr(st, -cx27(d), -cy27(d), -cz27(d), in);
-            off = (!W || in) ? (Off)(opp(d) - D0) * N + s : off;
-        }
-        v[k] = Store<S>::ld(a + off);
-    }
+    for (int k = 0; k < Q; ++k) v[k] = gather_one<Q, ODD, S, D0, R32, W, Off>(kp, a, st, k);
 }
 
 template <int Q, bool ODD, typename S, int D0 = 0, bool R32 = false, bool W = true,
           typename Off = unsigned>
 __device__ __forceinline__ void scatter(const KParams& kp, S* __restrict__ a, const Stencil& st,
                                         const float (&v)[Q]) {
-    const unsigned N = kp.N;
 #pragma unroll
-    for (int k = 0; k < Q; ++k) {
-        const int d = k + D0;
-        if (R32 && d == 0) {
-            st_pop(rest_row(a, Q, N) + st.n, v[k]);
-            continue;
-        }
-        Off off = (Off)(opp(d) - D0) * N + st.n;
-        if (ODD && d != 0) {
-            bool in;
-            const unsigned t = nbr(st, cx27(d), cy27(d), cz27(d), in);
-            off = (!W || in) ? (Off)k * N + t : off;
-        }
-        Store<S>::st(a + off, v[k]);
-    }
+    for (int k = 0; k < Q; ++k) scatter_one<Q, ODD, S, D0, R32, W, Off>(kp, a, st, k, v[k]);
 }
 
 // Columns searched for the front (Sec. 3.1 with reading R11): all of them

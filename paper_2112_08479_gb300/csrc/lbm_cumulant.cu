@@ -13,9 +13,9 @@
 namespace lbmgpu {
 
 // Minimum resident blocks per SM for the register allocator: the D3Q27 FCM
-// scalar doubles the live populations, so its instantiation gets its own
-// setting; 3 (168 registers, ~150 bytes of spills) measured 12.2 G node
-// updates/s against 11.0 for 2 (239 registers) and 10.0 for 4 (128).
+// scalar holds more live values, so its instantiation gets its own setting;
+// 3 (168 registers, 36-56 bytes of spills) measured 14.1 G node updates/s
+// against 11.9 for 2 and 11.3 for 4 (128 registers, ~200 bytes of spills).
 #ifndef LBM_Q27_MINB
 #define LBM_Q27_MINB 3
 #endif
@@ -25,6 +25,81 @@ namespace lbmgpu {
 #ifndef LBM_CUM_WSPLIT
 #define LBM_CUM_WSPLIT 1
 #endif
+
+// With the D3Q27 scalar the factorized-central-moment collision needs, of
+// the 27 pre-collision scalar populations, only chi, their first moments and
+// (for the closing sum of the rest population) the populations themselves
+// at the very end.  So the scalar is read, reduced to those four numbers and
+// dropped; the fluid collides and is stored; then the scalar is read again
+// (the same elements, which no other thread writes within the step) and
+// collided: 27 values fewer live across the fluid collision.  Same arithmetic
+// as collide_cumulant<27>.
+template <bool ODD, bool SAVE, typename S, bool W, typename Off>
+__device__ __forceinline__ void cumulant_fcm_step_body(const KParams& kp, S* __restrict__ f,
+                                                       S* __restrict__ phi,
+                                                       float* __restrict__ save,
+                                                       const Stencil& st) {
+    const unsigned n = st.n;
+    constexpr bool R32 = rest32<S, 27>();
+    constexpr bool s16 = !std::is_same<S, float>::value;
+    float chs = 0.0f, jpx, jpy, jpz;
+    {
+        float pv[27];
+        gather<27, ODD, S, 0, R32, W, Off>(kp, phi, st, pv);
+        if (SAVE) {
+            const size_t N = kp.N;
+#pragma unroll
+            for (int k = 0; k < 27; ++k)
+                save[(size_t)(27 + k) * N + n] = s16 ? pv[k] * kp.isp : pv[k];
+        }
+        if (s16) {
+#pragma unroll
+            for (int k = 0; k < 27; ++k) pv[k] *= kp.isp;
+        }
+#pragma unroll
+        for (int k = 0; k < 27; ++k) chs += pv[k];
+        scalar_first_moments27(pv, jpx, jpy, jpz);
+    }
+    float fv[27];
+    gather<27, ODD, S, 0, false, W, Off>(kp, f, st, fv);
+    if (SAVE) {
+        const size_t N = kp.N;
+#pragma unroll
+        for (int i = 0; i < 27; ++i) save[(size_t)i * N + n] = s16 ? fv[i] * kp.isf : fv[i];
+    }
+    const bool collide = !(kp.flags & LBM_FLAG_NO_COLLIDE);
+    float chit = 0.0f, chi = 1.0f, hx = 0.0f, hy = 0.0f, hz = 0.0f;
+    if (s16) {
+#pragma unroll
+        for (int i = 0; i < 27; ++i) fv[i] *= kp.isf;
+    }
+    if (collide) cumulant_fluid<false>(kp, fv, chs, chit, chi, hx, hy, hz);
+    if (s16) {
+#pragma unroll
+        for (int i = 0; i < 27; ++i) fv[i] *= kp.sf;
+    }
+    scatter<27, ODD, S, 0, false, W, Off>(kp, f, st, fv);
+    // keep the second read of the scalar after the fluid's collision (the
+    // compiler would otherwise issue it early and hold its values live again)
+    asm volatile("" ::: "memory");
+    // (held in registers all at once: reading, relaxing and storing the
+    // scalar in groups of opposite pairs spills nothing but measured 7-17 %
+    // slower, the loads of each group waiting behind the stores of the last)
+    float pv[27];
+    gather<27, ODD, S, 0, R32, W, Off>(kp, phi, st, pv);
+    if (s16) {
+#pragma unroll
+        for (int k = 0; k < 27; ++k) pv[k] *= kp.isp;
+    }
+    if (collide) collide_fcm27(kp, pv, chit, chi, hx, hy, hz, jpx, jpy, jpz);
+    if (s16) {
+#pragma unroll
+        for (int k = 0; k < 27; ++k) pv[k] *= kp.sp;
+    }
+    if constexpr (R32) feed_rest<S>(pv);
+    scatter<27, ODD, S, 0, R32, W, Off>(kp, phi, st, pv);
+}
+
 template <bool ODD, bool SAVE, typename S, int SL, bool W, typename Off>
 __device__ __forceinline__ void cumulant_step_body(const KParams& kp, S* __restrict__ f,
                                                    S* __restrict__ phi, float* __restrict__ save,
@@ -74,7 +149,7 @@ __global__ void __launch_bounds__(128, SL == 27 ? LBM_Q27_MINB : LBM_CUM_MINB) c
     if (x >= kp.nx) return;
     const Stencil st = make_stencil(kp, x, blockIdx.y, blockIdx.z);
     if constexpr (SL == 27) {
-        cumulant_step_body<ODD, SAVE, S, SL, true, Off>(kp, f, phi, save, st);
+        cumulant_fcm_step_body<ODD, SAVE, S, true, Off>(kp, f, phi, save, st);
     } else {
         if (!ODD || (LBM_CUM_WSPLIT && block_interior(kp)))
             cumulant_step_body<ODD, SAVE, S, SL, false, Off>(kp, f, phi, save, st);

@@ -95,19 +95,13 @@ __device__ __forceinline__ Moments2 moments_by_lines(const float (&f)[27]) {
     return m;
 }
 
-// SL: scalar lattice, D3Q7 BGK or D3Q27 factorized central moments.
-// SCALED (16-bit storage, D3Q7 scalar): f and p hold the storage units
-// scale_f (f - w) and scale_phi (Phi - w); the scales are applied to the few
-// moments and output coefficients instead of to every population.
-template <int SL = 7, bool SCALED = false>
-__device__ __forceinline__ void collide_cumulant(const KParams& kp, float (&f)[27],
-                                                 float (&p)[ScalarLat<SL>::NS]) {
-    static_assert(SL == 7 || SL == 27, "the cumulant model runs with the D3Q7 or D3Q27 scalar");
-    static_assert(!(SCALED && SL == 27), "the D3Q27 scalar takes unscaled populations");
-    constexpr int NS = ScalarLat<SL>::NS;
-    float chs = 0.0f;  // chi - 1 in storage units (Phi is held as Phi - w)
-#pragma unroll
-    for (int k = 0; k < NS; ++k) chs += p[k];
+// The fluid part: replaces f by its post-collision populations, given
+// chs = sum_k (Phi_k - w_k) (storage units when SCALED); returns chi - 1,
+// chi and the half-force velocity h = (j + F/2) / rho the scalar takes.
+template <bool SCALED>
+__device__ __forceinline__ void cumulant_fluid(const KParams& kp, float (&f)[27], float chs,
+                                               float& chit_out, float& chi_out, float& hx,
+                                               float& hy, float& hz) {
     const float chit = SCALED ? chs * kp.isp : chs;
     const float chi = 1.0f + chit;
     const float Fx = kp.gx * chi, Fy = kp.gy * chi, Fz = kp.gz * chi;
@@ -193,9 +187,120 @@ __device__ __forceinline__ void collide_cumulant(const KParams& kp, float (&f)[2
             f[ip] = ds * w27(ip) + rs * pp;
         }
 
-    const float hx = (jx + 0.5f * Fx) * irho, hy = (jy + 0.5f * Fy) * irho,
-                hz = (jz + 0.5f * Fz) * irho;
-    if constexpr (SL == 7) {
+    hx = (jx + 0.5f * Fx) * irho;
+    hy = (jy + 0.5f * Fy) * irho;
+    hz = (jz + 0.5f * Fz) * irho;
+    chit_out = chit;
+    chi_out = chi;
+}
+
+// Post-collision value of moving population i (1 .. 26) of the D3Q27
+// factorized-central-moment scalar (collide_fcm27 below, one population):
+// chi - 1, chi, the half-force velocity h and the relaxed first moments v.
+struct Fcm27 {
+    float chit, chi;
+    float W[3][3], dE[3][3], G[3][3];   // [axis][c + 1]
+    float v[3];
+};
+__device__ __forceinline__ Fcm27 fcm27_setup(const KParams& kp, float chit, float chi, float hx,
+                                             float hy, float hz, float jpx, float jpy, float jpz) {
+    Fcm27 c;
+    c.chit = chit;
+    c.chi = chi;
+    const float r1 = 1.0f - kp.omD;
+    c.v[0] = r1 * (jpx - chi * hx);
+    c.v[1] = r1 * (jpy - chi * hy);
+    c.v[2] = r1 * (jpz - chi * hz);
+    const float u[3] = {hx, hy, hz};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float uu = u[a] * u[a];
+        c.W[a][0] = 1.0f / 6.0f; c.W[a][1] = 2.0f / 3.0f; c.W[a][2] = 1.0f / 6.0f;
+        c.dE[a][1] = -uu;
+        c.dE[a][0] = 0.5f * (uu - u[a]);
+        c.dE[a][2] = 0.5f * (uu + u[a]);
+        c.G[a][1] = -2.0f * u[a];
+        c.G[a][0] = u[a] - 0.5f;
+        c.G[a][2] = u[a] + 0.5f;
+    }
+    return c;
+}
+__device__ __forceinline__ float fcm27_value(const Fcm27& c, int i) {
+    const int cx = cx27(i) + 1, cy = cy27(i) + 1, cz = cz27(i) + 1;
+    const float Ex = c.W[0][cx] + c.dE[0][cx], Ey = c.W[1][cy] + c.dE[1][cy],
+                Ez = c.W[2][cz] + c.dE[2][cz];
+    // Ex Ey Ez - Wx Wy Wz without cancellation
+    const float dprod = c.dE[0][cx] * Ey * Ez + c.W[0][cx] * c.dE[1][cy] * Ez +
+                        c.W[0][cx] * c.W[1][cy] * c.dE[2][cz];
+    const float vt = c.v[0] * c.G[0][cx] * Ey * Ez + c.v[1] * Ex * c.G[1][cy] * Ez +
+                     c.v[2] * Ex * Ey * c.G[2][cz];
+    return c.chit * w27(i) + c.chi * dprod + vt;
+}
+
+// First moments sum_i c_i (Phi_i - w_i) = sum_i c_i Phi_i of the D3Q27 scalar.
+__device__ __forceinline__ void scalar_first_moments27(const float (&p)[27], float& jpx,
+                                                       float& jpy, float& jpz) {
+    jpx = 0.0f; jpy = 0.0f; jpz = 0.0f;
+#pragma unroll
+    for (int i = 1; i < 27; i += 2) {
+        const float dm = p[i] - p[i + 1];
+        if (cx27(i)) jpx += cx27(i) * dm;
+        if (cy27(i)) jpy += cy27(i) * dm;
+        if (cz27(i)) jpz += cz27(i) * dm;
+    }
+}
+
+// D3Q27 factorized central moments (Eq. 37-51) with every rate of order >= 2
+// equal to 1: the moments in the frame of u relax to their lattice
+// equilibria chi (1, 0, 1/3)^(x) per axis, except the first-order ones,
+// v = (1 - omega_D) (sum c Phi - chi u) with omega_D from Eq. 51.  The
+// post-collision populations are therefore
+//   chi Ex Ey Ez + vx Gx Ey Ez + vy Ex Gy Ez + vz Ex Ey Gz,
+// E(0) = 2/3 - u^2, E(+-1) = (1/3 + u^2 +- u)/2 (moments (1, 0, 1/3)),
+// G(0) = -2u, G(+-1) = (2u +- 1)/2 (moments (0, 1, 0)), both inverted in the
+// frame of u.  Held as deviations: Phi* - w = (chi - 1) w + chi (Ex Ey Ez -
+// w) + v-terms, with Ex Ey Ez - w expanded in the small parts dE = E - w1.
+// p holds the pre-collision populations on entry (only the closing sum of
+// the rest population reads them) and the post-collision ones on return;
+// jp: their first moments, computed before.
+__device__ __forceinline__ void collide_fcm27(const KParams& kp, float (&p)[27], float chit,
+                                              float chi, float hx, float hy, float hz, float jpx,
+                                              float jpy, float jpz) {
+    const Fcm27 c = fcm27_setup(kp, chit, chi, hx, hy, hz, jpx, jpy, jpz);
+    float psum = 0.0f;
+#pragma unroll
+    for (int i = 1; i < 27; ++i) {
+        const float nv = fcm27_value(c, i);
+        psum += nv - p[i];
+        p[i] = nv;
+    }
+    // the rest population closes the sum (its reconstruction
+    // chit w_0 + chi dprod_0 + vt_0 in exact arithmetic): sum Phi changes
+    // only by the rounding of Phi_0, not by that of the 27-term chi
+    p[0] -= psum;
+}
+
+// SL: scalar lattice, D3Q7 BGK or D3Q27 factorized central moments.
+// SCALED (16-bit storage, D3Q7 scalar): f and p hold the storage units
+// scale_f (f - w) and scale_phi (Phi - w); the scales are applied to the few
+// moments and output coefficients instead of to every population.
+template <int SL = 7, bool SCALED = false>
+__device__ __forceinline__ void collide_cumulant(const KParams& kp, float (&f)[27],
+                                                 float (&p)[ScalarLat<SL>::NS]) {
+    static_assert(SL == 7 || SL == 27, "the cumulant model runs with the D3Q7 or D3Q27 scalar");
+    static_assert(!(SCALED && SL == 27), "the D3Q27 scalar takes unscaled populations");
+    constexpr int NS = ScalarLat<SL>::NS;
+    float chs = 0.0f;  // chi - 1 in storage units (Phi is held as Phi - w)
+#pragma unroll
+    for (int k = 0; k < NS; ++k) chs += p[k];
+    float chit, chi, hx, hy, hz;
+    if constexpr (SL == 27) {
+        float jpx, jpy, jpz;
+        scalar_first_moments27(p, jpx, jpy, jpz);
+        cumulant_fluid<SCALED>(kp, f, chs, chit, chi, hx, hy, hz);
+        collide_fcm27(kp, p, chit, chi, hx, hy, hz, jpx, jpy, jpz);
+    } else {
+        cumulant_fluid<SCALED>(kp, f, chs, chit, chi, hx, hy, hz);
         // scalar (Eq. 28-30) with the half-force velocity and the molecular D;
         // non-equilibrium form whose parts sum to zero, so sum Phi is conserved
         // up to the rounding of the stored results (see collide_bgk)
@@ -211,60 +316,6 @@ __device__ __forceinline__ void collide_cumulant(const KParams& kp, float (&f)[2
         nq[0] = -(((nq[1] + nq[2]) + (nq[3] + nq[4])) + (nq[5] + nq[6]));
 #pragma unroll
         for (int k = 0; k < 7; ++k) p[k] -= omp * nq[k];
-    } else {
-        // D3Q27 factorized central moments (Eq. 37-51) with every rate of order
-        // >= 2 equal to 1: the moments in the frame of u relax to their lattice
-        // equilibria chi (1, 0, 1/3)^(x) per axis, except the first-order ones,
-        // v = (1 - omega_D) (sum c Phi - chi u) with omega_D from Eq. 51.  The
-        // post-collision populations are therefore
-        //   chi Ex Ey Ez + vx Gx Ey Ez + vy Ex Gy Ez + vz Ex Ey Gz,
-        // E(0) = 2/3 - u^2, E(+-1) = (1/3 + u^2 +- u)/2 (moments (1, 0, 1/3)),
-        // G(0) = -2u, G(+-1) = (2u +- 1)/2 (moments (0, 1, 0)), both inverted in
-        // the frame of u.  Held as deviations: Phi* - w = (chi - 1) w +
-        // chi (Ex Ey Ez - w) + v-terms, with Ex Ey Ez - w expanded in the small
-        // parts dE = E - w1.
-        float jpx = 0.0f, jpy = 0.0f, jpz = 0.0f;   // sum c (Phi - w) = sum c Phi
-#pragma unroll
-        for (int i = 1; i < 27; i += 2) {
-            const float dm = p[i] - p[i + 1];
-            if (cx27(i)) jpx += cx27(i) * dm;
-            if (cy27(i)) jpy += cy27(i) * dm;
-            if (cz27(i)) jpz += cz27(i) * dm;
-        }
-        const float r1 = 1.0f - kp.omD;
-        const float vx = r1 * (jpx - chi * hx), vy = r1 * (jpy - chi * hy), vz = r1 * (jpz - chi * hz);
-        const float u[3] = {hx, hy, hz};
-        const float v[3] = {vx, vy, vz};
-        float W[3][3], dE[3][3], G[3][3];   // [axis][c + 1]
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const float uu = u[a] * u[a];
-            W[a][0] = 1.0f / 6.0f; W[a][1] = 2.0f / 3.0f; W[a][2] = 1.0f / 6.0f;
-            dE[a][1] = -uu;
-            dE[a][0] = 0.5f * (uu - u[a]);
-            dE[a][2] = 0.5f * (uu + u[a]);
-            G[a][1] = -2.0f * u[a];
-            G[a][0] = u[a] - 0.5f;
-            G[a][2] = u[a] + 0.5f;
-        }
-        float psum = 0.0f;
-#pragma unroll
-        for (int i = 1; i < 27; ++i) {
-            const int cx = cx27(i) + 1, cy = cy27(i) + 1, cz = cz27(i) + 1;
-            const float Ex = W[0][cx] + dE[0][cx], Ey = W[1][cy] + dE[1][cy], Ez = W[2][cz] + dE[2][cz];
-            // Ex Ey Ez - Wx Wy Wz without cancellation
-            const float dprod = dE[0][cx] * Ey * Ez + W[0][cx] * dE[1][cy] * Ez +
-                                W[0][cx] * W[1][cy] * dE[2][cz];
-            const float vt = v[0] * G[0][cx] * Ey * Ez + v[1] * Ex * G[1][cy] * Ez +
-                             v[2] * Ex * Ey * G[2][cz];
-            const float nv = chit * w27(i) + chi * dprod + vt;
-            psum += nv - p[i];
-            p[i] = nv;
-        }
-        // the rest population closes the sum (its reconstruction
-        // chit w_0 + chi dprod_0 + vt_0 in exact arithmetic): sum Phi changes
-        // only by the rounding of Phi_0, not by that of the 27-term chi
-        p[0] -= psum;
     }
 }
 

@@ -95,6 +95,11 @@ typedef enum lbm_storage {
                                   segments moved by bulk copies through shared memory by a
                                   producer warp); same results bit for bit, measured slower
                                   than the default kernel on GB300; ignored elsewhere */
+#define LBM_FLAG_TEST_STALL 32 /* test hook of the failure path of LBM_FLAG_TMA_STAGED: each
+                                  block's first tile is announced on its barrier but never
+                                  copied, so its wait cannot end; every wait gives up after 0.1 s, the kernel
+                                  sets LBM_DEVFLAG_TIMEOUT and returns (lbm_diag then
+                                  reports LBM_ERR_TIMEOUT); no fault, no hang */
 
 /* sticky device flags reported in lbm_diagnostics.flags */
 #define LBM_DEVFLAG_NONFINITE 1   /* a macroscopic value was NaN or Inf */

@@ -58,7 +58,7 @@ const char* check(const lbm_params* p) {
     if (p->storage != LBM_FP32 && p->storage != LBM_FP16S && p->storage != LBM_BF16S)
         return "unknown storage";
     if (p->flags & ~(LBM_FLAG_NO_COLLIDE | LBM_FLAG_PERIODIC_X | LBM_FLAG_PERIODIC_Z |
-                     LBM_FLAG_ONE_NODE | LBM_FLAG_TMA_STAGED))
+                     LBM_FLAG_ONE_NODE | LBM_FLAG_TMA_STAGED | LBM_FLAG_TEST_STALL))
         return "unknown flag bits";
     if (!finite(p->nu) || p->nu <= 0.0) return "nu must be finite and > 0";
     if (!finite(p->D) || p->D <= 0.0) return "D must be finite and > 0";

@@ -336,13 +336,19 @@ __global__ void __launch_bounds__(Geom<Q, SL, S>::TX + 32, LBM_STAGED_BLOCKS)
     }
     __syncthreads();
 
+    // the test hook of the failure path: a short limit, and each block's
+    // first tile announced on its barrier but never copied (the phase never
+    // completes, and no copy is in flight on it)
+    const bool stall = (kp.flags & LBM_FLAG_TEST_STALL) != 0;
+    const uint64_t limit = stall ? 100000000ull : WAIT_LIMIT_NS;
+
     // bounded wait that also gives up once another warp has given up
     auto wait = [&](uint64_t* bar, uint32_t parity) -> bool {
         if (mbar_try_wait(bar, parity)) return true;
         const uint64_t t0 = global_ns();
         while (!mbar_try_wait(bar, parity)) {
             if (*(volatile int*)&abort_flag) return false;
-            if (global_ns() - t0 > WAIT_LIMIT_NS) {
+            if (global_ns() - t0 > limit) {
                 atomicExch(&abort_flag, 1);
                 return false;
             }
@@ -401,6 +407,7 @@ __global__ void __launch_bounds__(Geom<Q, SL, S>::TX + 32, LBM_STAGED_BLOCKS)
             total = __reduce_add_sync(0xffffffffu, total);
             if (lane == 0) mbar_arrive_expect_tx(&full[s], total);
             __syncwarp();
+            if (stall && k == 0) return;
 #pragma unroll
             for (int h = 0; h < 2; ++h)
                 if (nbytes[h]) bulk_load(sb + dst[h], src[h], nbytes[h], &full[s]);
@@ -471,7 +478,7 @@ __global__ void __launch_bounds__(Geom<Q, SL, S>::TX + 32, LBM_STAGED_BLOCKS)
             // loads still in flight land in this block's shared memory: let
             // them complete (bounded) before the block exits
             for (unsigned k = issued > (unsigned)NIN ? issued - NIN : 0u; k < issued; ++k)
-                mbar_wait_bounded(&full[k % NIN], (k / NIN) & 1u, WAIT_LIMIT_NS);
+                mbar_wait_bounded(&full[k % NIN], (k / NIN) & 1u, limit);
         }
         return;
     }

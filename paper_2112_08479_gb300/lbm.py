@@ -18,7 +18,7 @@ LBM_OK, LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_NOMEM, LBM_ERR_UNSTABLE, LBM_ERR_STAT
 LBM_BGK_SMAG_Q19, LBM_CUMULANT_Q27 = 0, 1
 LBM_FP32, LBM_FP16S, LBM_BF16S = 0, 1, 2
 LBM_FLAG_NO_COLLIDE, LBM_FLAG_PERIODIC_X, LBM_FLAG_PERIODIC_Z, LBM_FLAG_ONE_NODE = 1, 2, 4, 8
-LBM_FLAG_TMA_STAGED = 16
+LBM_FLAG_TMA_STAGED, LBM_FLAG_TEST_STALL = 16, 32
 LBM_DEVFLAG_NONFINITE, LBM_DEVFLAG_RHO_NONPOS, LBM_DEVFLAG_TIMEOUT = 1, 2, 4
 
 LBM_SCALAR_Q7, LBM_SCALAR_Q6, LBM_SCALAR_Q27 = 0, 1, 2

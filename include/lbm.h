@@ -60,7 +60,8 @@ typedef enum lbm_status {
     LBM_ERR_NOMEM = 3,     /* workspace smaller than lbm_workspace_bytes */
     LBM_ERR_UNSTABLE = 4,  /* sticky device flag: non-finite value or rho <= 0 */
     LBM_ERR_STATE = 5,     /* call not valid in the context's current state */
-    LBM_ERR_TIMEOUT = 6    /* a bounded wait gave up */
+    LBM_ERR_TIMEOUT = 6,   /* a bounded wait gave up */
+    LBM_ERR_BOUNDS = 7     /* debug build only: an index check failed (lbm_debug_record) */
 } lbm_status;
 
 typedef enum lbm_model {
@@ -100,6 +101,11 @@ typedef enum lbm_storage {
                                   copied, so its wait cannot end; every wait gives up after 0.1 s, the kernel
                                   sets LBM_DEVFLAG_TIMEOUT and returns (lbm_diag then
                                   reports LBM_ERR_TIMEOUT); no fault, no hang */
+#define LBM_FLAG_TEST_BOUNDS 64 /* test hook of the index checks of the debug build (rejected
+                                   with LBM_ERR_ARG by the release build): every check uses
+                                   half of its array's true extent, so the in-bounds accesses
+                                   to the upper half of each array fail the check, are
+                                   recorded and skipped; no access leaves its array */
 
 /* sticky device flags reported in lbm_diagnostics.flags */
 #define LBM_DEVFLAG_NONFINITE 1   /* a macroscopic value was NaN or Inf */
@@ -108,6 +114,8 @@ typedef enum lbm_storage {
                                      through shared memory (a bounded wait for its
                                      own bulk copies gave up, or the shared memory
                                      was misaligned): the step is incomplete */
+#define LBM_DEVFLAG_BOUNDS 8      /* debug build: an index check failed and its access
+                                     was skipped (lbm_debug_record) */
 
 typedef struct lbm_params {
     int32_t nx, ny, nz;       /* nodes; 1 <= nx, ny, nz; nx*ny*nz < 2^31; ny, nz <= 65535.
@@ -401,6 +409,36 @@ LBM_API lbm_status lbm_sync(lbm_ctx* ctx);
 
 /* Frees the host context (not the caller's workspace).  NULL is a no-op. */
 LBM_API void lbm_destroy(lbm_ctx* ctx);
+
+/* ---- index checks of the debug build -----------------------------------
+ * The debug build of this library (liblbm_debug.so, compiled with
+ * LBM_DEBUG) checks, before every population access of the step, halo,
+ * adjoint and state-transfer kernels, that the accessed elements lie inside
+ * their array (a population array of rows x N elements, the FP32 rest row,
+ * a halo buffer, an adjoint or state buffer).  A failed check counts
+ * itself, records the first failure, sets LBM_DEVFLAG_BOUNDS and skips the
+ * access (a skipped load gives 0): an indexing error becomes a status the
+ * host reads, never a memory fault.  lbm_diag returns LBM_ERR_BOUNDS once
+ * the flag is set.  The release build compiles the checks to nothing.
+ *
+ * lbm_debug_build: 1 in the debug build, 0 in the release build.
+ * lbm_debug_record: the context's record, out[0] = failed checks, out[1] =
+ * site of the first failure (LBM_SITE_*), out[2] = its element offset in
+ * its array, out[3] = the extent (elements) it was checked against; all 0
+ * when no check failed, and always in the release build.  Synchronises the
+ * context's stream; the workspace must still be allocated.  LBM_ERR_ARG for
+ * NULL arguments.  (lbm_diag_static reads its state without these checks.) */
+#define LBM_SITE_GATHER 1      /* one-node gather (step, diagnostics, state export) */
+#define LBM_SITE_SCATTER 2     /* one-node scatter */
+#define LBM_SITE_PAIR_LOAD 3   /* two-node gather */
+#define LBM_SITE_PAIR_STORE 4  /* two-node scatter */
+#define LBM_SITE_QUAD 5        /* four-node even step of 16-bit storage */
+#define LBM_SITE_STAGED 6      /* TMA-staged step: bulk copies and direct accesses */
+#define LBM_SITE_HALO 7        /* halo pack / unpack (state and face buffer) */
+#define LBM_SITE_ADJOINT 8     /* adjoint kernels: saved states and adjoint fields */
+#define LBM_SITE_STATE 9       /* initial condition, state import, saved steps */
+LBM_API int32_t lbm_debug_build(void);
+LBM_API lbm_status lbm_debug_record(lbm_ctx* ctx, int64_t out[4]);
 
 #ifdef __cplusplus
 }

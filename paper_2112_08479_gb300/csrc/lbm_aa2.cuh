@@ -145,7 +145,9 @@ __device__ __forceinline__ void gather2(const KParams& kp, const S* __restrict__
         const int i = k + D0;       // direction; population k lives in row k
         if (R32 && i == 0) {
             P0[k] = 0.0f; P1[k] = 0.0f;
-            if (st.active) PairIO<float>::ld(rest_row(a, Q, N) + st.n, P0[k], P1[k]);
+            const float* r = rest_row(a, Q, N);
+            if (st.active && LBM_IN(kp, LBM_SITE_PAIR_LOAD, r, r + st.n, 2, N))
+                PairIO<float>::ld(r + st.n, P0[k], P1[k]);
             continue;
         }
         Off off = (Off)k * N + st.n;
@@ -154,14 +156,19 @@ __device__ __forceinline__ void gather2(const KParams& kp, const S* __restrict__
             const Off row = (Off)(opp(i) - D0) * N + st.zr[dz + 1] + st.yr[dy + 1];
             if (FAST && dx != 0) {
                 const Off e = row + st.x + (Off)dx;
-                P0[k] = Store<S>::ld(a + e);
-                P1[k] = Store<S>::ld(a + e + 1);
+                if (LBM_IN(kp, LBM_SITE_PAIR_LOAD, a, a + e, 2, (size_t)Q * N)) {
+                    P0[k] = Store<S>::ld(a + e);
+                    P1[k] = Store<S>::ld(a + e + 1);
+                } else {
+                    P0[k] = 0.0f; P1[k] = 0.0f;
+                }
                 continue;
             }
             off = (!ZWe || st.zo[dz + 1]) ? row + st.x : off;
         }
         P0[k] = 0.0f; P1[k] = 0.0f;
-        if (st.active) PairIO<S>::ld(a + off, P0[k], P1[k]);
+        if (st.active && LBM_IN(kp, LBM_SITE_PAIR_LOAD, a, a + off, 2, (size_t)Q * N))
+            PairIO<S>::ld(a + off, P0[k], P1[k]);
     }
 #pragma unroll
     for (int k = 0; k < Q; ++k) {
@@ -176,7 +183,8 @@ __device__ __forceinline__ void gather2(const KParams& kp, const S* __restrict__
             if (dx < 0) { need = st.left; off = st.xmo ? row + st.xm : own; }
             else { need = st.right; off = st.xp2o ? row + st.xp2 : own + 1; }
             need = need && st.active && (!ZWe || st.zo[dz + 1]);
-            if (need) E[k] = Store<S>::ld(a + off);
+            if (need && LBM_IN(kp, LBM_SITE_PAIR_LOAD, a, a + off, 1, (size_t)Q * N))
+                E[k] = Store<S>::ld(a + off);
         }
     }
 #pragma unroll
@@ -224,39 +232,51 @@ __device__ __forceinline__ void scatter2(const KParams& kp, S* __restrict__ a, c
         const int i = k + D0;
         const int dx = cx27(i), dy = cy27(i), dz = cz27(i);
         if (R32 && i == 0) {
-            if (st.active) PairIO<float>::st(rest_row(a, Q, N) + st.n, v0[k], v1[k]);
+            float* r = rest_row(a, Q, N);
+            if (st.active && LBM_IN(kp, LBM_SITE_PAIR_STORE, r, r + st.n, 2, N))
+                PairIO<float>::st(r + st.n, v0[k], v1[k]);
             continue;
         }
         const Off own = (Off)(opp(i) - D0) * N + st.n;
+        // element offset and count of every store below, checked in the debug build
+        auto ok = [&](Off o, int n) {
+            return LBM_IN(kp, LBM_SITE_PAIR_STORE, a, a + o, n, (size_t)Q * N);
+        };
         if (!ODD || i == 0) {
-            if (st.active) PairIO<S>::st(a + own, v0[k], v1[k]);
+            if (st.active && ok(own, 2)) PairIO<S>::st(a + own, v0[k], v1[k]);
             continue;
         }
         const bool in = !ZWe || st.zo[dz + 1];
         const Off row = (Off)k * N + st.zr[dz + 1] + st.yr[dy + 1];
         if (FAST && dx != 0) {
             const Off e = row + st.x + (Off)dx;
-            Store<S>::st(a + e, v0[k]);
-            Store<S>::st(a + e + 1, v1[k]);
+            if (ok(e, 2)) {
+                Store<S>::st(a + e, v0[k]);
+                Store<S>::st(a + e + 1, v1[k]);
+            }
             continue;
         }
-        if (st.active && !in) PairIO<S>::st(a + own, v0[k], v1[k]);
+        if (st.active && !in && ok(own, 2)) PairIO<S>::st(a + own, v0[k], v1[k]);
         if (dx == 0) {
-            if (st.active && in) PairIO<S>::st(a + row + st.x, v0[k], v1[k]);
+            if (st.active && in && ok(row + st.x, 2)) PairIO<S>::st(a + row + st.x, v0[k], v1[k]);
         } else if (dx > 0) {
             // element x receives node x - 1, element x + 1 receives node x
-            if (st.active && in && !st.left) PairIO<S>::st(a + row + st.x, X[k], v0[k]);
-            if (st.active && in && st.left) Store<S>::st(a + row + st.x + 1, v0[k]);
+            if (st.active && in && !st.left && ok(row + st.x, 2))
+                PairIO<S>::st(a + row + st.x, X[k], v0[k]);
+            if (st.active && in && st.left && ok(row + st.x + 1, 1))
+                Store<S>::st(a + row + st.x + 1, v0[k]);
             // node x + 1 -> x + 2 across the warp edge, or back from an x wall
-            if (st.active && in && st.right)
-                Store<S>::st(a + (st.xp2o ? row + st.xp2 : own + 1), v1[k]);
+            const Off o = st.xp2o ? row + st.xp2 : own + 1;
+            if (st.active && in && st.right && ok(o, 1)) Store<S>::st(a + o, v1[k]);
         } else {
             // element x receives node x + 1, element x + 1 receives node x + 2
-            if (st.active && in && !st.right) PairIO<S>::st(a + row + st.x, v1[k], X[k]);
-            if (st.active && in && st.right) Store<S>::st(a + row + st.x, v1[k]);
+            if (st.active && in && !st.right && ok(row + st.x, 2))
+                PairIO<S>::st(a + row + st.x, v1[k], X[k]);
+            if (st.active && in && st.right && ok(row + st.x, 1))
+                Store<S>::st(a + row + st.x, v1[k]);
             // node x -> x - 1 across the warp edge, or back from an x wall
-            if (st.active && in && st.left)
-                Store<S>::st(a + (st.xmo ? row + st.xm : own), v0[k]);
+            const Off o = st.xmo ? row + st.xm : own;
+            if (st.active && in && st.left && ok(o, 1)) Store<S>::st(a + o, v0[k]);
         }
     }
 }

@@ -24,21 +24,24 @@ __global__ void __launch_bounds__(128, LBM_STEP_MINB) bgk_push_kernel(KParams kp
     const unsigned n = st.n, N = kp.N;
     float f[19], p[7];
 #pragma unroll
-    for (int i = 0; i < 19; ++i) f[i] = src[(unsigned)i * N + n];
+    for (int i = 0; i < 19; ++i) f[i] = ld_chk(kp, LBM_SITE_ADJOINT, src, (unsigned)i * N + n, (size_t)26 * N);
 #pragma unroll
-    for (int k = 0; k < 7; ++k) p[k] = src[(unsigned)(19 + k) * N + n];
+    for (int k = 0; k < 7; ++k) p[k] = ld_chk(kp, LBM_SITE_ADJOINT, src, (unsigned)(19 + k) * N + n, (size_t)26 * N);
     if (!(kp.flags & LBM_FLAG_NO_COLLIDE)) collide_bgk(kp, f, p);
 #pragma unroll
     for (int i = 0; i < 19; ++i) {
         bool in = false;
         const unsigned d = i == 0 ? n : nbr(st, cx27(i), cy27(i), cz27(i), in);
-        dst[(i != 0 && in) ? (unsigned)i * N + d : (unsigned)opp(i) * N + n] = f[i];
+        st_chk(kp, LBM_SITE_ADJOINT, dst, (i != 0 && in) ? (unsigned)i * N + d : (unsigned)opp(i) * N + n,
+               (size_t)26 * N, f[i]);
     }
 #pragma unroll
     for (int k = 0; k < 7; ++k) {
         bool in = false;
         const unsigned d = k == 0 ? n : nbr(st, cx27(k), cy27(k), cz27(k), in);
-        dst[(k != 0 && in) ? (unsigned)(19 + k) * N + d : (unsigned)(19 + opp(k)) * N + n] = p[k];
+        st_chk(kp, LBM_SITE_ADJOINT, dst,
+               (k != 0 && in) ? (unsigned)(19 + k) * N + d : (unsigned)(19 + opp(k)) * N + n,
+               (size_t)26 * N, p[k]);
     }
 }
 
@@ -124,7 +127,7 @@ __global__ void __launch_bounds__(128, LBM_ADJ_MINB) bgk_adjoint_kernel(KParams 
             bool in = false;
             const unsigned d = i == 0 ? n : nbr(sn, cx27(i), cy27(i), cz27(i), in);
             const unsigned off = (i != 0 && in) ? (unsigned)i * N32 + d : (unsigned)opp(i) * N32 + n;
-            mu[i] = lamn ? lamn[off] : 0.0f;
+            mu[i] = lamn ? ld_chk(kp, LBM_SITE_ADJOINT, lamn, off, (size_t)26 * N) : 0.0f;
         }
 #pragma unroll
         for (int k = 0; k < 7; ++k) {
@@ -132,13 +135,13 @@ __global__ void __launch_bounds__(128, LBM_ADJ_MINB) bgk_adjoint_kernel(KParams 
             const unsigned d = k == 0 ? n : nbr(sn, cx27(k), cy27(k), cz27(k), in);
             const unsigned off = (k != 0 && in) ? (unsigned)(19 + k) * N32 + d
                                                 : (unsigned)(19 + opp(k)) * N32 + n;
-            mup[k] = lamn ? lamn[off] : 0.0f;
+            mup[k] = lamn ? ld_chk(kp, LBM_SITE_ADJOINT, lamn, off, (size_t)26 * N) : 0.0f;
         }
         float f[19], p[7];
 #pragma unroll
-        for (int i = 0; i < 19; ++i) f[i] = st[(size_t)i * N + n];
+        for (int i = 0; i < 19; ++i) f[i] = ld_chk(kp, LBM_SITE_ADJOINT, st, (size_t)i * N + n, (size_t)26 * N);
 #pragma unroll
-        for (int k = 0; k < 7; ++k) p[k] = st[(size_t)(19 + k) * N + n];
+        for (int k = 0; k < 7; ++k) p[k] = ld_chk(kp, LBM_SITE_ADJOINT, st, (size_t)(19 + k) * N + n, (size_t)26 * N);
 
         // ---- forward recompute (as collide_bgk) ----
         float chit = 0.0f;
@@ -295,9 +298,9 @@ __global__ void __launch_bounds__(128, LBM_ADJ_MINB) bgk_adjoint_kernel(KParams 
 #pragma unroll
         for (int k = 0; k < 7; ++k) gp[k] += gchi;
 #pragma unroll
-        for (int i = 0; i < 19; ++i) lam[(size_t)i * N + n] = gf[i];
+        for (int i = 0; i < 19; ++i) st_chk(kp, LBM_SITE_ADJOINT, lam, (size_t)i * N + n, (size_t)26 * N, gf[i]);
 #pragma unroll
-        for (int k = 0; k < 7; ++k) lam[(size_t)(19 + k) * N + n] = gp[k];
+        for (int k = 0; k < 7; ++k) st_chk(kp, LBM_SITE_ADJOINT, lam, (size_t)(19 + k) * N + n, (size_t)26 * N, gp[k]);
     }
     // dJ/dC_s: block reduction in FP64, one atomic per block
     if (dcs) {

@@ -84,20 +84,20 @@ __global__ void __launch_bounds__(128, LBM_CUM_ADJ_MINB) cumulant_adjoint_kernel
         bool in = false;
         const unsigned d = i == 0 ? n : nbr(sn, cx27(i), cy27(i), cz27(i), in);
         const unsigned off = (i != 0 && in) ? (unsigned)i * N + d : (unsigned)opp(i) * N + n;
-        mu[i] = lamn ? lamn[off] : 0.0f;
+        mu[i] = lamn ? ld_chk(kp, LBM_SITE_ADJOINT, lamn, off, (size_t)34 * N) : 0.0f;
     }
 #pragma unroll
     for (int k = 0; k < 7; ++k) {
         bool in = false;
         const unsigned d = k == 0 ? n : nbr(sn, cx27(k), cy27(k), cz27(k), in);
         const unsigned off = (k != 0 && in) ? (unsigned)(27 + k) * N + d : (unsigned)(27 + opp(k)) * N + n;
-        mup[k] = lamn ? lamn[off] : 0.0f;
+        mup[k] = lamn ? ld_chk(kp, LBM_SITE_ADJOINT, lamn, off, (size_t)34 * N) : 0.0f;
     }
     float f[27], p[7];
 #pragma unroll
-    for (int i = 0; i < 27; ++i) f[i] = st[(size_t)i * N + n];
+    for (int i = 0; i < 27; ++i) f[i] = ld_chk(kp, LBM_SITE_ADJOINT, st, (size_t)i * N + n, (size_t)34 * N);
 #pragma unroll
-    for (int k = 0; k < 7; ++k) p[k] = st[(size_t)(27 + k) * N + n];
+    for (int k = 0; k < 7; ++k) p[k] = ld_chk(kp, LBM_SITE_ADJOINT, st, (size_t)(27 + k) * N + n, (size_t)34 * N);
 
     // ---- forward recompute (as collide_cumulant<7>) ----
     float chit = 0.0f;
@@ -276,13 +276,13 @@ __global__ void __launch_bounds__(128, LBM_CUM_ADJ_MINB) cumulant_adjoint_kernel
             const float E = b == 1 ? Ez : (b == 2 ? t + Yz : t - Yz);
             const float X = b == 1 ? Xz : (b == 2 ? Xz + gmxy : Xz - gmxy);
             const float gx = E + gmxx;
-            lam[(size_t)dir27(-1, b - 1, c - 1) * N + n] = gx - X;
-            lam[(size_t)dir27(0, b - 1, c - 1) * N + n] = E;
-            lam[(size_t)dir27(1, b - 1, c - 1) * N + n] = gx + X;
+            st_chk(kp, LBM_SITE_ADJOINT, lam, (size_t)dir27(-1, b - 1, c - 1) * N + n, (size_t)34 * N, gx - X);
+            st_chk(kp, LBM_SITE_ADJOINT, lam, (size_t)dir27(0, b - 1, c - 1) * N + n, (size_t)34 * N, E);
+            st_chk(kp, LBM_SITE_ADJOINT, lam, (size_t)dir27(1, b - 1, c - 1) * N + n, (size_t)34 * N, gx + X);
         }
     }
 #pragma unroll
-    for (int k = 0; k < 7; ++k) lam[(size_t)(27 + k) * N + n] = gp[k] + gchit;
+    for (int k = 0; k < 7; ++k) st_chk(kp, LBM_SITE_ADJOINT, lam, (size_t)(27 + k) * N + n, (size_t)34 * N, gp[k] + gchit);
 }
 
 cudaError_t launch_cumulant_adjoint_step(const KParams& kp, const float* state,

@@ -8,9 +8,22 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "lbm_internal.h"
 
 using namespace lbmgpu;
+
+namespace {
+// A named NVTX range over an entry point, for profilers (ncu --nvtx); inert
+// when no tool is attached.
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range&) = delete;
+    Range& operator=(const Range&) = delete;
+};
+}  // namespace
 
 struct lbm_ctx {
     lbm_params p;
@@ -58,8 +71,11 @@ const char* check(const lbm_params* p) {
     if (p->storage != LBM_FP32 && p->storage != LBM_FP16S && p->storage != LBM_BF16S)
         return "unknown storage";
     if (p->flags & ~(LBM_FLAG_NO_COLLIDE | LBM_FLAG_PERIODIC_X | LBM_FLAG_PERIODIC_Z |
-                     LBM_FLAG_ONE_NODE | LBM_FLAG_TMA_STAGED | LBM_FLAG_TEST_STALL))
+                     LBM_FLAG_ONE_NODE | LBM_FLAG_TMA_STAGED | LBM_FLAG_TEST_STALL |
+                     LBM_FLAG_TEST_BOUNDS))
         return "unknown flag bits";
+    if ((p->flags & LBM_FLAG_TEST_BOUNDS) && !lbm_debug_build())
+        return "LBM_FLAG_TEST_BOUNDS needs the debug build (liblbm_debug.so)";
     if (!finite(p->nu) || p->nu <= 0.0) return "nu must be finite and > 0";
     if (!finite(p->D) || p->D <= 0.0) return "D must be finite and > 0";
     if (!finite(p->cs_smag) || p->cs_smag < 0.0) return "cs_smag must be finite and >= 0";
@@ -99,7 +115,9 @@ Layout layout(const lbm_params* p) {
     L.colmax = o; o = up(o + (size_t)p->nx * sizeof(unsigned));
     L.part = o;   o = up(o + (size_t)L.nblocks * 2 * sizeof(double));
     L.fwpart = o; o = up(o + (size_t)L.nblocks * 2 * sizeof(float));
-    L.ddiag = o;  o = up(o + sizeof(DevDiag) + 2 * sizeof(int));
+    // the diagnostics record, the two device flag words and the debug
+    // build's index-check record (DbgRecord, lbm_common.cuh)
+    L.ddiag = o;  o = up(o + sizeof(DevDiag) + 2 * sizeof(int) + sizeof(DbgRecord));
     L.fgrad = o;  o = up(o + sizeof(FrontGrad));
     L.total = o;
     return L;
@@ -181,6 +199,7 @@ const char* lbm_status_string(lbm_status s) {
         case LBM_ERR_UNSTABLE: return "unstable: non-finite value or rho <= 0";
         case LBM_ERR_STATE: return "call not valid in this state";
         case LBM_ERR_TIMEOUT: return "timeout";
+        case LBM_ERR_BOUNDS: return "index check failed (debug build)";
     }
     return "unknown status";
 }
@@ -200,6 +219,7 @@ size_t lbm_workspace_bytes(const lbm_params* p) {
 
 lbm_status lbm_init(const lbm_params* p, void* workspace, size_t bytes, void* cuda_stream,
                     lbm_ctx** out) {
+    const Range range("lbm_init");
     if (!out) return arg_fail(nullptr, "out is NULL");
     const char* m = check(p);
     if (m) return arg_fail(nullptr, m);
@@ -242,6 +262,7 @@ lbm_status lbm_init(const lbm_params* p, void* workspace, size_t bytes, void* cu
 }
 
 lbm_status lbm_set_scalar(lbm_ctx* c, const float* chi0) {
+    const Range range("lbm_set_scalar");
     if (!c) return arg_fail(nullptr, "ctx is NULL");
     if (!chi0) return arg_fail(c, "chi0 is NULL");
     cudaError_t e = cudaMemcpyAsync(c->v.stage, chi0, (size_t)c->kp.N * sizeof(float),
@@ -255,6 +276,7 @@ lbm_status lbm_set_scalar(lbm_ctx* c, const float* chi0) {
 }
 
 lbm_status lbm_step(lbm_ctx* c, int32_t nsteps) {
+    const Range range("lbm_step");
     if (!c) return arg_fail(nullptr, "ctx is NULL");
     if (nsteps < 0) return arg_fail(c, "nsteps must be >= 0");
     for (int32_t s = 0; s < nsteps; ++s) {
@@ -268,6 +290,7 @@ lbm_status lbm_step(lbm_ctx* c, int32_t nsteps) {
 }
 
 lbm_status lbm_step_save(lbm_ctx* c, float* state_out) {
+    const Range range("lbm_step_save");
     if (!c) return arg_fail(nullptr, "ctx is NULL");
     if (!state_out) return arg_fail(c, "state_out is NULL");
     if (lbm_status s = narrow_check(c); s != LBM_OK) return s;
@@ -289,6 +312,7 @@ lbm_status lbm_macros(lbm_ctx* c, float* rho, float* u, float* chi) {
 }
 
 lbm_status lbm_diag(lbm_ctx* c, lbm_diagnostics* out) {
+    const Range range("lbm_diag");
     if (!c) return arg_fail(nullptr, "ctx is NULL");
     if (!out) return arg_fail(c, "out is NULL");
     cudaError_t e = launch_diag(c->kp, kind(&c->p), c->odd != 0, c->v,
@@ -309,6 +333,7 @@ lbm_status lbm_diag(lbm_ctx* c, lbm_diagnostics* out) {
     out->pad_ = 0;
     if (rec.flags[0]) {
         snprintf(c->err, sizeof c->err, "sticky device flags 0x%x", rec.flags[0]);
+        if (rec.flags[0] & LBM_DEVFLAG_BOUNDS) return LBM_ERR_BOUNDS;
         return (rec.flags[0] & LBM_DEVFLAG_TIMEOUT) ? LBM_ERR_TIMEOUT : LBM_ERR_UNSTABLE;
     }
     return LBM_OK;
@@ -325,6 +350,7 @@ lbm_status lbm_fw_accumulate(lbm_ctx* c, double* acc_dev, double weight) {
 }
 
 lbm_status lbm_get_state(lbm_ctx* c, float* dst) {
+    const Range range("lbm_get_state");
     if (!c) return arg_fail(nullptr, "ctx is NULL");
     if (!dst) return arg_fail(c, "dst is NULL");
     cudaError_t e = launch_get_state(c->kp, kind(&c->p), c->odd != 0, c->v, dst,
@@ -334,6 +360,7 @@ lbm_status lbm_get_state(lbm_ctx* c, float* dst) {
 }
 
 lbm_status lbm_set_state(lbm_ctx* c, const float* src, int64_t step) {
+    const Range range("lbm_set_state");
     if (!c) return arg_fail(nullptr, "ctx is NULL");
     if (!src) return arg_fail(c, "src is NULL");
     if (step < 0) return arg_fail(c, "step must be >= 0");
@@ -385,6 +412,7 @@ lbm_status adjoint_model_check(lbm_ctx* c) {
 
 lbm_status lbm_adjoint_step(lbm_ctx* c, const float* state_n, const float* lam_next, float* lam_n,
                             double* dJdCs_dev, double w_fw) {
+    const Range range("lbm_adjoint_step");
     if (!c) return arg_fail(nullptr, "ctx is NULL");
     if (lbm_status s = adjoint_model_check(c); s != LBM_OK) return s;
     if (!state_n || !lam_n) return arg_fail(c, "state_n and lam_n must not be NULL");
@@ -397,6 +425,7 @@ lbm_status lbm_adjoint_step(lbm_ctx* c, const float* state_n, const float* lam_n
 
 lbm_status lbm_objective_forward(lbm_ctx* c, int32_t nsteps, int32_t K, float* ckpt,
                                  double* J_dev) {
+    const Range range("lbm_objective_forward");
     if (!c) return arg_fail(nullptr, "ctx is NULL");
     if (nsteps < 0 || K < 1) return arg_fail(c, "nsteps must be >= 0 and K >= 1");
     const size_t S = (size_t)(q_of(&c->p) + ns_of(&c->p)) * c->kp.N;
@@ -421,6 +450,7 @@ lbm_status lbm_objective_forward(lbm_ctx* c, int32_t nsteps, int32_t K, float* c
 
 lbm_status lbm_recompute_segment(lbm_ctx* c, const float* ckpt, int32_t k, float* seg,
                                  void* stream) {
+    const Range range("lbm_recompute_segment");
     if (!c) return arg_fail(nullptr, "ctx is NULL");
     if (lbm_status s = sweep_check(c); s != LBM_OK) return s;
     if (k < 1) return arg_fail(c, "k must be >= 1");
@@ -441,6 +471,7 @@ lbm_status lbm_recompute_segment(lbm_ctx* c, const float* ckpt, int32_t k, float
 lbm_status lbm_adjoint_sweep(lbm_ctx* c, const float* ckpt, const float* seg, int64_t n0,
                              int32_t k, float* lam, float* tmp, double* dJdCs_dev, double w_fw,
                              void* stream) {
+    const Range range("lbm_adjoint_sweep");
     if (!c) return arg_fail(nullptr, "ctx is NULL");
     if (lbm_status s = sweep_check(c); s != LBM_OK) return s;
     if (k < 1 || n0 < 0) return arg_fail(c, "k must be >= 1 and n0 >= 0");
@@ -467,6 +498,7 @@ lbm_status lbm_adjoint_sweep(lbm_ctx* c, const float* ckpt, const float* seg, in
 
 lbm_status lbm_adjoint_segment(lbm_ctx* c, const float* ckpt, int64_t n0, int32_t k, float* seg,
                                float* lam, float* tmp, double* dJdCs_dev, double w_fw) {
+    const Range range("lbm_adjoint_segment");
     if (!c) return arg_fail(nullptr, "ctx is NULL");
     if (k < 1 || n0 < 0) return arg_fail(c, "k must be >= 1 and n0 >= 0");
     lbm_status s = lbm_recompute_segment(c, ckpt, k, seg, nullptr);
@@ -500,6 +532,7 @@ size_t lbm_halo_bytes(const lbm_params* p) {
 }
 
 lbm_status lbm_halo_pack(lbm_ctx* c, int32_t face, void* buf) {
+    const Range range("lbm_halo_pack");
     if (!c) return arg_fail(nullptr, "ctx is NULL");
     if (face != 0 && face != 1) return arg_fail(c, "face must be 0 (x = 0) or 1 (x = nx - 1)");
     if (!buf) return arg_fail(c, "buf is NULL");
@@ -509,6 +542,7 @@ lbm_status lbm_halo_pack(lbm_ctx* c, int32_t face, void* buf) {
 }
 
 lbm_status lbm_halo_unpack(lbm_ctx* c, int32_t face, const void* buf) {
+    const Range range("lbm_halo_unpack");
     if (!c) return arg_fail(nullptr, "ctx is NULL");
     if (face != 0 && face != 1) return arg_fail(c, "face must be 0 (x = 0) or 1 (x = nx - 1)");
     if (!buf) return arg_fail(c, "buf is NULL");
@@ -521,6 +555,7 @@ lbm_status lbm_halo_unpack(lbm_ctx* c, int32_t face, const void* buf) {
 int32_t lbm_next_step_odd(const lbm_ctx* c) { return c ? c->odd : -1; }
 
 lbm_status lbm_column_max(lbm_ctx* c, float* m) {
+    const Range range("lbm_column_max");
     if (!c) return arg_fail(nullptr, "ctx is NULL");
     if (!m) return arg_fail(c, "m is NULL");
     cudaError_t e = launch_column_max(c->kp, kind(&c->p), c->odd != 0, c->v, m, c->stream);
@@ -555,5 +590,30 @@ lbm_status lbm_sync(lbm_ctx* c) {
 }
 
 void lbm_destroy(lbm_ctx* c) { free(c); }
+
+int32_t lbm_debug_build(void) {
+#ifdef LBM_DEBUG
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+lbm_status lbm_debug_record(lbm_ctx* c, int64_t out[4]) {
+    if (!c) return arg_fail(nullptr, "ctx is NULL");
+    if (!out) return arg_fail(c, "out is NULL");
+    DbgRecord r;
+    cudaError_t e = cudaMemcpyAsync(&r, dbg_record(c->v.devflags), sizeof r,
+                                    cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "debug record copy");
+    e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "debug record sync");
+    if (r.count == 0) r = DbgRecord{};
+    out[0] = (int64_t)r.count;
+    out[1] = r.site;
+    out[2] = r.off;
+    out[3] = r.extent;
+    return LBM_OK;
+}
 
 }  // extern "C"

@@ -91,13 +91,14 @@ __global__ void init_kernel(KParams kp, S* __restrict__ f, S* __restrict__ phi,
         }
         c = (float)v;
     }
+    constexpr int NS = ScalarLat<SL>::NS;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) Store<S>::st(f + (size_t)i * N + n, 0.0f);
+    for (int i = 0; i < Q; ++i) store_chk(kp, LBM_SITE_STATE, f, (size_t)i * N + n, Q * N, 0.0f);
 #pragma unroll
-    for (int k = 0; k < ScalarLat<SL>::NS; ++k) {
+    for (int k = 0; k < NS; ++k) {
         const float v = kp.sp * (ScalarLat<SL>::w(k) * c);
-        if (rest32<S, SL>() && k == 0) rest_row(phi, ScalarLat<SL>::NS, kp.N)[n] = v;
-        else Store<S>::st(phi + (size_t)k * N + n, v);
+        if (rest32<S, SL>() && k == 0) st_chk(kp, LBM_SITE_STATE, rest_row(phi, NS, kp.N), n, N, v);
+        else store_chk(kp, LBM_SITE_STATE, phi, (size_t)k * N + n, NS * N, v);
     }
 }
 
@@ -105,7 +106,10 @@ __global__ void fill_keys_kernel(unsigned* __restrict__ keys, int n, int* __rest
                                  int reset_flags) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) keys[i] = 0x007fffffu;  // key of -inf
-    if (reset_flags && i == 0) *flags = 0;
+    if (reset_flags && i == 0) {
+        *flags = 0;
+        *dbg_record(flags) = DbgRecord{};
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -139,9 +143,13 @@ __global__ void get_state_kernel(KParams kp, const S* __restrict__ f, const S* _
     gather<NS, ODD, S, ScalarLat<SL>::D0, rest32<S, SL>(), true, size_t>(kp, phi, st, pv);
     const size_t N = kp.N;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) dst[(size_t)i * N + n] = is16<S>() ? fv[i] * kp.isf : fv[i];
+    for (int i = 0; i < Q; ++i)
+        st_chk(kp, LBM_SITE_STATE, dst, (size_t)i * N + n, (Q + NS) * N,
+               is16<S>() ? fv[i] * kp.isf : fv[i]);
 #pragma unroll
-    for (int k = 0; k < NS; ++k) dst[(size_t)(Q + k) * N + n] = is16<S>() ? pv[k] * kp.isp : pv[k];
+    for (int k = 0; k < NS; ++k)
+        st_chk(kp, LBM_SITE_STATE, dst, (size_t)(Q + k) * N + n, (Q + NS) * N,
+               is16<S>() ? pv[k] * kp.isp : pv[k]);
 }
 
 template <int Q, int SL, typename S>
@@ -152,16 +160,18 @@ __global__ void set_state_kernel(KParams kp, S* __restrict__ f, S* __restrict__ 
     const int y = blockIdx.y, z = blockIdx.z;
     const unsigned n = (unsigned)x + (unsigned)kp.nx * ((unsigned)y + (unsigned)kp.ny * (unsigned)z);
     const size_t N = kp.N;
+    constexpr int NS = ScalarLat<SL>::NS;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const float v = src[(size_t)i * N + n];
-        Store<S>::st(f + (size_t)i * N + n, is16<S>() ? v * kp.sf : v);
+        const float v = ld_chk(kp, LBM_SITE_STATE, src, (size_t)i * N + n, (Q + NS) * N);
+        store_chk(kp, LBM_SITE_STATE, f, (size_t)i * N + n, Q * N, is16<S>() ? v * kp.sf : v);
     }
 #pragma unroll
-    for (int k = 0; k < ScalarLat<SL>::NS; ++k) {
-        const float v = src[(size_t)(Q + k) * N + n];
-        if (rest32<S, SL>() && k == 0) rest_row(phi, ScalarLat<SL>::NS, kp.N)[n] = v * kp.sp;
-        else Store<S>::st(phi + (size_t)k * N + n, is16<S>() ? v * kp.sp : v);
+    for (int k = 0; k < NS; ++k) {
+        const float v = ld_chk(kp, LBM_SITE_STATE, src, (size_t)(Q + k) * N + n, (Q + NS) * N);
+        if (rest32<S, SL>() && k == 0)
+            st_chk(kp, LBM_SITE_STATE, rest_row(phi, NS, kp.N), n, N, v * kp.sp);
+        else store_chk(kp, LBM_SITE_STATE, phi, (size_t)k * N + n, NS * N, is16<S>() ? v * kp.sp : v);
     }
 }
 

@@ -43,11 +43,11 @@ __global__ void __launch_bounds__(128, LBM_STEP_MINB) bgk_step_kernel(KParams kp
     gather<NS, ODD, S, D0, R32, true, Off>(kp, phi, st, pv);
     constexpr bool s16 = !std::is_same<S, float>::value;   // populations in storage units
     if (SAVE) {
-        const size_t N = kp.N;
 #pragma unroll
-        for (int i = 0; i < 19; ++i) save[(size_t)i * N + n] = s16 ? fv[i] * kp.isf : fv[i];
+        for (int i = 0; i < 19; ++i) save_pop(kp, save, 19 + NS, i, n, s16 ? fv[i] * kp.isf : fv[i]);
 #pragma unroll
-        for (int k = 0; k < NS; ++k) save[(size_t)(19 + k) * N + n] = s16 ? pv[k] * kp.isp : pv[k];
+        for (int k = 0; k < NS; ++k)
+            save_pop(kp, save, 19 + NS, 19 + k, n, s16 ? pv[k] * kp.isp : pv[k]);
     }
     if (!(kp.flags & LBM_FLAG_NO_COLLIDE)) collide_bgk<s16, SL>(kp, fv, pv);
     if constexpr (R32) feed_rest<S>(pv);
@@ -173,12 +173,23 @@ __global__ void __launch_bounds__(128, LBM_STEP4_MINB) bgk_even4_kernel(KParams 
     float4* __restrict__ rest = reinterpret_cast<float4*>(rest_row(phi, NS, N) + n);
     uint2 wf[19], wp[NS];
     float4 r = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    // the four elements of each word, checked in the debug build
+    auto ok = [&](const S* a, Off o, int rows) {
+        return LBM_IN(kp, LBM_SITE_QUAD, a, a + o, 4, (size_t)rows * N);
+    };
+    const bool rest_ok = !R32 || LBM_IN(kp, LBM_SITE_QUAD, rest_row(phi, NS, N),
+                                        rest_row(phi, NS, N) + n, 4, N);
 #pragma unroll
-    for (int i = 0; i < 19; ++i) wf[i] = ld_pop(fw + (((Off)i * N + n) >> 2));
+    for (int i = 0; i < 19; ++i)
+        wf[i] = ok(f, (Off)i * N + n, 19) ? ld_pop(fw + (((Off)i * N + n) >> 2)) : make_uint2(0, 0);
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
-        if (R32 && k == 0) r = ld_pop(rest);
-        else wp[k] = ld_pop(pw + (((Off)k * N + n) >> 2));
+        if (R32 && k == 0) {
+            if (rest_ok) r = ld_pop(rest);
+        } else {
+            wp[k] = ok(phi, (Off)k * N + n, NS) ? ld_pop(pw + (((Off)k * N + n) >> 2))
+                                                 : make_uint2(0, 0);
+        }
     }
     const bool collide = !(kp.flags & LBM_FLAG_NO_COLLIDE);
 #pragma unroll
@@ -209,11 +220,15 @@ __global__ void __launch_bounds__(128, LBM_STEP4_MINB) bgk_even4_kernel(KParams 
         }
     }
 #pragma unroll
-    for (int i = 0; i < 19; ++i) st_pop(fw + (((Off)opp(i) * N + n) >> 2), wf[i]);
+    for (int i = 0; i < 19; ++i)
+        if (ok(f, (Off)opp(i) * N + n, 19)) st_pop(fw + (((Off)opp(i) * N + n) >> 2), wf[i]);
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
-        if (R32 && k == 0) st_pop(rest, r);
-        else st_pop(pw + (((Off)(opp(k + D0) - D0) * N + n) >> 2), wp[k]);
+        if (R32 && k == 0) {
+            if (rest_ok) st_pop(rest, r);
+        } else if (ok(phi, (Off)(opp(k + D0) - D0) * N + n, NS)) {
+            st_pop(pw + (((Off)(opp(k + D0) - D0) * N + n) >> 2), wp[k]);
+        }
     }
 }
 

@@ -96,6 +96,57 @@ struct KParams {
 };
 
 // ---------------------------------------------------------------------------
+// Index checks of the debug build (compiled with LBM_DEBUG).  Before each
+// population access of the step, halo, adjoint and state-transfer kernels,
+// LBM_IN(kp, site, base, p, n, extent) checks that the n elements at p lie in
+// the array [base, base + extent) (element counts).  A failed check counts
+// itself in the context's DbgRecord (after its two device flag words),
+// records the first failure, sets LBM_DEVFLAG_BOUNDS and yields false: the
+// caller skips the access, and a skipped load gives 0.  With the test hook
+// LBM_FLAG_TEST_BOUNDS every check takes half the true extent, so accesses to
+// the upper half of each array fail the check while no access ever leaves
+// its array.  Without LBM_DEBUG, LBM_IN is the constant true and evaluates
+// nothing.
+struct DbgRecord {
+    unsigned long long count;   // failed checks
+    long long off, extent;      // first failure: element offset and the extent checked
+    int site, pad;              // first failure: LBM_SITE_*
+};
+
+__host__ __device__ inline DbgRecord* dbg_record(int* devflags) {
+    return reinterpret_cast<DbgRecord*>(devflags + 2);
+}
+
+#ifdef LBM_DEBUG
+static __device__ __noinline__ void dbg_fail(int* devflags, int site, long long off,
+                                             long long extent) {
+    if (!devflags) return;
+    DbgRecord* r = dbg_record(devflags);
+    if (atomicAdd(&r->count, 1ull) == 0ull) {
+        r->site = site;
+        r->off = off;
+        r->extent = extent;
+    }
+    atomicOr(devflags, LBM_DEVFLAG_BOUNDS);
+}
+
+template <typename T>
+__device__ __forceinline__ bool dbg_in(int* devflags, int flags, int site, const T* base,
+                                       const T* p, long long n, long long extent) {
+    if (flags & LBM_FLAG_TEST_BOUNDS) extent /= 2;
+    const long long off = (long long)(p - base);
+    if (off >= 0 && off + n <= extent) return true;
+    dbg_fail(devflags, site, off, extent);
+    return false;
+}
+#define LBM_IN(kp, site, base, p, n, extent) \
+    (::lbmgpu::dbg_in((kp).devflags, (kp).flags, (site), (base), (p), (long long)(n), \
+                      (long long)(extent)))
+#else
+#define LBM_IN(kp, site, base, p, n, extent) true
+#endif
+
+// ---------------------------------------------------------------------------
 // Tuning of the step kernels (compile-time): minimum resident blocks per SM
 // requested from the register allocator, and whether population traffic uses
 // the streaming (evict-first) cache policy.  Each population is touched once
@@ -261,14 +312,18 @@ __device__ __forceinline__ float gather_one(const KParams& kp, const S* __restri
                                             const Stencil& st, int k) {
     const unsigned N = kp.N;
     const int d = k + D0;
-    if (R32 && d == 0) return ld_pop(rest_row(a, Q, N) + st.n);
+    if (R32 && d == 0) {
+        const float* r = rest_row(a, Q, N);
+        return LBM_IN(kp, LBM_SITE_GATHER, r, r + st.n, 1, N) ? ld_pop(r + st.n) : 0.0f;
+    }
     Off off = (Off)k * N + st.n;
     if (ODD && d != 0) {
         bool in;
         const unsigned s = nbr(st, -cx27(d), -cy27(d), -cz27(d), in);
         off = (!W || in) ? (Off)(opp(d) - D0) * N + s : off;
     }
-    return Store<S>::ld(a + off);
+    return LBM_IN(kp, LBM_SITE_GATHER, a, a + off, 1, (size_t)Q * N) ? Store<S>::ld(a + off)
+                                                                      : 0.0f;
 }
 
 template <int Q, bool ODD, typename S, int D0 = 0, bool R32 = false, bool W = true,
@@ -278,7 +333,8 @@ __device__ __forceinline__ void scatter_one(const KParams& kp, S* __restrict__ a
     const unsigned N = kp.N;
     const int d = k + D0;
     if (R32 && d == 0) {
-        st_pop(rest_row(a, Q, N) + st.n, v);
+        float* r = rest_row(a, Q, N);
+        if (LBM_IN(kp, LBM_SITE_SCATTER, r, r + st.n, 1, N)) st_pop(r + st.n, v);
         return;
     }
     Off off = (Off)(opp(d) - D0) * N + st.n;
@@ -287,7 +343,7 @@ __device__ __forceinline__ void scatter_one(const KParams& kp, S* __restrict__ a
         const unsigned t = nbr(st, cx27(d), cy27(d), cz27(d), in);
         off = (!W || in) ? (Off)k * N + t : off;
     }
-    Store<S>::st(a + off, v);
+    if (LBM_IN(kp, LBM_SITE_SCATTER, a, a + off, 1, (size_t)Q * N)) Store<S>::st(a + off, v);
 }
 
 template <int Q, bool ODD, typename S, int D0 = 0, bool R32 = false, bool W = true,
@@ -304,6 +360,31 @@ __device__ __forceinline__ void scatter(const KParams& kp, S* __restrict__ a, co
                                         const float (&v)[Q]) {
 #pragma unroll
     for (int k = 0; k < Q; ++k) scatter_one<Q, ODD, S, D0, R32, W, Off>(kp, a, st, k, v[k]);
+}
+
+// Element o of an FP32 buffer of `extent` elements (adjoint fields, saved
+// states), loaded or stored under the debug build's index check.
+__device__ __forceinline__ float ld_chk(const KParams& kp, int site, const float* __restrict__ a,
+                                        size_t o, size_t extent) {
+    return LBM_IN(kp, site, a, a + o, 1, extent) ? a[o] : 0.0f;
+}
+__device__ __forceinline__ void st_chk(const KParams& kp, int site, float* __restrict__ a,
+                                       size_t o, size_t extent, float v) {
+    if (LBM_IN(kp, site, a, a + o, 1, extent)) a[o] = v;
+}
+
+template <typename S>
+__device__ __forceinline__ void store_chk(const KParams& kp, int site, S* __restrict__ a, size_t o,
+                                          size_t extent, float v) {
+    if (LBM_IN(kp, site, a, a + o, 1, extent)) Store<S>::st(a + o, v);
+}
+
+// Saved pre-collision state (lbm_step_save): row r of node n in a buffer of
+// `rows` FP32 rows of N values.
+__device__ __forceinline__ void save_pop(const KParams& kp, float* __restrict__ save, int rows,
+                                         int r, unsigned n, float v) {
+    const size_t o = (size_t)r * kp.N + n;
+    if (LBM_IN(kp, LBM_SITE_STATE, save, save + o, 1, (size_t)rows * kp.N)) save[o] = v;
 }
 
 // Columns searched for the front (Sec. 3.1 with reading R11): all of them

@@ -47,10 +47,9 @@ __device__ __forceinline__ void cumulant_fcm_step_body(const KParams& kp, S* __r
         float pv[27];
         gather<27, ODD, S, 0, R32, W, Off>(kp, phi, st, pv);
         if (SAVE) {
-            const size_t N = kp.N;
 #pragma unroll
             for (int k = 0; k < 27; ++k)
-                save[(size_t)(27 + k) * N + n] = s16 ? pv[k] * kp.isp : pv[k];
+                save_pop(kp, save, 54, 27 + k, n, s16 ? pv[k] * kp.isp : pv[k]);
         }
         if (s16) {
 #pragma unroll
@@ -63,9 +62,8 @@ __device__ __forceinline__ void cumulant_fcm_step_body(const KParams& kp, S* __r
     float fv[27];
     gather<27, ODD, S, 0, false, W, Off>(kp, f, st, fv);
     if (SAVE) {
-        const size_t N = kp.N;
 #pragma unroll
-        for (int i = 0; i < 27; ++i) save[(size_t)i * N + n] = s16 ? fv[i] * kp.isf : fv[i];
+        for (int i = 0; i < 27; ++i) save_pop(kp, save, 54, i, n, s16 ? fv[i] * kp.isf : fv[i]);
     }
     const bool collide = !(kp.flags & LBM_FLAG_NO_COLLIDE);
     float chit = 0.0f, chi = 1.0f, hx = 0.0f, hy = 0.0f, hz = 0.0f;
@@ -113,11 +111,12 @@ __device__ __forceinline__ void cumulant_step_body(const KParams& kp, S* __restr
     constexpr bool s16 = !std::is_same<S, float>::value;   // populations in storage units
     constexpr bool fold = s16 && SL == 7;                  // the collision applies the scales
     if (SAVE) {
-        const size_t N = kp.N;
 #pragma unroll
-        for (int i = 0; i < 27; ++i) save[(size_t)i * N + n] = s16 ? fv[i] * kp.isf : fv[i];
+        for (int i = 0; i < 27; ++i)
+            save_pop(kp, save, 27 + NS, i, n, s16 ? fv[i] * kp.isf : fv[i]);
 #pragma unroll
-        for (int k = 0; k < NS; ++k) save[(size_t)(27 + k) * N + n] = s16 ? pv[k] * kp.isp : pv[k];
+        for (int k = 0; k < NS; ++k)
+            save_pop(kp, save, 27 + NS, 27 + k, n, s16 ? pv[k] * kp.isp : pv[k]);
     }
     if (s16 && !fold) {
 #pragma unroll

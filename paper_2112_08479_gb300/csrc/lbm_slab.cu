@@ -59,13 +59,24 @@ __global__ void halo_pack_kernel(KParams kp, const S* __restrict__ f, const S* _
     const unsigned y = yz % kp.ny, z = yz / kp.ny;
     const unsigned n = z * kp.nxny + y * kp.nx + (FACE == 0 ? 0u : (unsigned)kp.nx - 1u);
     const size_t N = kp.N;
+    // extent of the face buffer, checked in the debug build
+    const size_t nb = (size_t)(NF + face_count(D0, NS, s)) * nyz;
 #pragma unroll
-    for (int d = 0; d < Q; ++d)
-        if (cx27(d) == s) buf[(size_t)face_pos(0, d, s) * nyz + yz] = f[(size_t)d * N + n];
+    for (int d = 0; d < Q; ++d) {
+        if (cx27(d) != s) continue;
+        const size_t o = (size_t)face_pos(0, d, s) * nyz + yz, i = (size_t)d * N + n;
+        if (LBM_IN(kp, LBM_SITE_HALO, buf, buf + o, 1, nb) &&
+            LBM_IN(kp, LBM_SITE_HALO, f, f + i, 1, (size_t)Q * N))
+            buf[o] = f[i];
+    }
 #pragma unroll
-    for (int k = 0; k < NS; ++k)
-        if (cx27(k + D0) == s)
-            buf[(size_t)(NF + face_pos(D0, k + D0, s)) * nyz + yz] = phi[(size_t)k * N + n];
+    for (int k = 0; k < NS; ++k) {
+        if (cx27(k + D0) != s) continue;
+        const size_t o = (size_t)(NF + face_pos(D0, k + D0, s)) * nyz + yz, i = (size_t)k * N + n;
+        if (LBM_IN(kp, LBM_SITE_HALO, buf, buf + o, 1, nb) &&
+            LBM_IN(kp, LBM_SITE_HALO, phi, phi + i, 1, (size_t)NS * N))
+            buf[o] = phi[i];
+    }
 }
 
 // Writes the neighbour's face buffer (its populations with c_x = -s) into
@@ -96,21 +107,29 @@ __global__ void halo_unpack_kernel(KParams kp, S* __restrict__ f, S* __restrict_
         idx = (unsigned)zs * kp.ny + (unsigned)ys;
         return true;
     };
+    // extent of the face buffer, checked in the debug build
+    const size_t nb = (size_t)(NFN + face_count(D0, NS, -s)) * nyz;
 #pragma unroll
     for (int d = 0; d < Q; ++d) {
         if (cx27(d) != s) continue;
         unsigned idx;
-        if (src(cy27(d), cz27(d), idx))
-            f[(size_t)d * N + n] = nbuf[(size_t)face_pos(0, opp(d), -s) * nyz + idx];
+        if (!src(cy27(d), cz27(d), idx)) continue;
+        const size_t o = (size_t)face_pos(0, opp(d), -s) * nyz + idx, i = (size_t)d * N + n;
+        if (LBM_IN(kp, LBM_SITE_HALO, nbuf, nbuf + o, 1, nb) &&
+            LBM_IN(kp, LBM_SITE_HALO, f, f + i, 1, (size_t)Q * N))
+            f[i] = nbuf[o];
     }
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
         const int d = k + D0;
         if (cx27(d) != s) continue;
         unsigned idx;
-        if (src(cy27(d), cz27(d), idx))
-            phi[(size_t)k * N + n] =
-                nbuf[(size_t)(NFN + face_pos(D0, opp(d), -s)) * nyz + idx];
+        if (!src(cy27(d), cz27(d), idx)) continue;
+        const size_t o = (size_t)(NFN + face_pos(D0, opp(d), -s)) * nyz + idx,
+                     i = (size_t)k * N + n;
+        if (LBM_IN(kp, LBM_SITE_HALO, nbuf, nbuf + o, 1, nb) &&
+            LBM_IN(kp, LBM_SITE_HALO, phi, phi + i, 1, (size_t)NS * N))
+            phi[i] = nbuf[o];
     }
 }
 

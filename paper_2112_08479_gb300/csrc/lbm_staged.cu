@@ -223,7 +223,9 @@ __device__ __forceinline__ void stage_gather(const KParams& kp, const Tile& T, i
                 const unsigned g = px ? (unsigned)orow * N + zr[1 - cz] + yr[1 - cy] +
                                             (unsigned)(xs < 0 ? xs + nx : xs - nx)
                                       : (unsigned)row * N + zr[1] + yr[1] + (unsigned)x;
-                v = Store<S>::ld(arr + g);
+                v = LBM_IN(kp, LBM_SITE_STAGED, arr, arr + g, 1, (size_t)(j < Q ? Q : G::NS) * N)
+                        ? Store<S>::ld(arr + g)
+                        : 0.0f;
             } else {
                 v = lds<S>(slot + (HALO - cx + t) * ES);
             }
@@ -274,9 +276,12 @@ __device__ __forceinline__ void stage_scatter(const KParams& kp, const Tile& T, 
                 const unsigned g = px ? (unsigned)row * N + zr[1 + cz] + yr[1 + cy] +
                                             (unsigned)(xt < 0 ? xt + nx : xt - nx)
                                       : (unsigned)orow * N + zr[1] + yr[1] + (unsigned)x;
-                Store<S>::st(arr + g, v);
+                if (LBM_IN(kp, LBM_SITE_STAGED, arr, arr + g, 1, (size_t)(j < Q ? Q : G::NS) * N))
+                    Store<S>::st(arr + g, v);
             } else if (cx > 0 ? rp : rm) {
-                Store<S>::st(arr + ((unsigned)row * N + zr[1 + cz] + yr[1 + cy] + (unsigned)xt), v);
+                const unsigned g = (unsigned)row * N + zr[1 + cz] + yr[1 + cy] + (unsigned)xt;
+                if (LBM_IN(kp, LBM_SITE_STAGED, arr, arr + g, 1, (size_t)(j < Q ? Q : G::NS) * N))
+                    Store<S>::st(arr + g, v);
             } else {
                 sts<S>(slot + (HALO + cx + t) * ES, v);
             }
@@ -377,6 +382,7 @@ __global__ void __launch_bounds__(Geom<Q, SL, S>::TX + 32, LBM_STAGED_BLOCKS)
                     src[h] = rest + T.nb;
                     dst[h] = o;
                     nbytes[h] = TX * 4;
+                    if (!LBM_IN(kp, LBM_SITE_STAGED, rest, rest + T.nb, TX, N)) nbytes[h] = 0;
                 } else {
                     const S* p = base + (size_t)sd.row * N + T.nb;   // own row segment
                     uint32_t bytes = TX * ES;
@@ -401,6 +407,9 @@ __global__ void __launch_bounds__(Geom<Q, SL, S>::TX + 32, LBM_STAGED_BLOCKS)
                     src[h] = p;
                     dst[h] = o;
                     nbytes[h] = bytes;
+                    if (!LBM_IN(kp, LBM_SITE_STAGED, base, p, bytes / ES,
+                                (size_t)(sd.fluid ? Q : NS) * N))
+                        nbytes[h] = 0;
                 }
                 total += nbytes[h];
             }
@@ -424,7 +433,8 @@ __global__ void __launch_bounds__(Geom<Q, SL, S>::TX + 32, LBM_STAGED_BLOCKS)
                 S* base = sd.fluid ? f : phi;
                 const uint32_t o = G::off(j);
                 if (G::R32 && j == Q) {
-                    bulk_store(rest + T.nb, sb + o, TX * 4);
+                    if (LBM_IN(kp, LBM_SITE_STAGED, rest, rest + T.nb, TX, N))
+                        bulk_store(rest + T.nb, sb + o, TX * 4);
                     continue;
                 }
                 void* p = base + (size_t)sd.orow * N + T.nb;     // own slot of the opposite
@@ -446,7 +456,9 @@ __global__ void __launch_bounds__(Geom<Q, SL, S>::TX + 32, LBM_STAGED_BLOCKS)
                         }
                     }
                 }
-                bulk_store(p, sb + so, bytes);
+                if (LBM_IN(kp, LBM_SITE_STAGED, base, (S*)p, bytes / ES,
+                           (size_t)(sd.fluid ? Q : NS) * N))
+                    bulk_store(p, sb + so, bytes);
             }
             bulk_commit();
         };

@@ -12,14 +12,22 @@ import os
 from dataclasses import dataclass, field, fields
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "liblbm.so")
+RELEASE_LIB_PATH = os.path.join(HERE, "liblbm.so")
+DEBUG_LIB_PATH = os.path.join(HERE, "liblbm_debug.so")   # index-checked build (LBM_DEBUG)
+# LBM_LIBRARY selects the library: unset or "release", "debug", or a path
+_choice = os.environ.get("LBM_LIBRARY", "release")
+LIB_PATH = {"release": RELEASE_LIB_PATH, "debug": DEBUG_LIB_PATH}.get(_choice, _choice)
 
-LBM_OK, LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_NOMEM, LBM_ERR_UNSTABLE, LBM_ERR_STATE, LBM_ERR_TIMEOUT = range(7)
+(LBM_OK, LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_NOMEM, LBM_ERR_UNSTABLE, LBM_ERR_STATE, LBM_ERR_TIMEOUT,
+ LBM_ERR_BOUNDS) = range(8)
 LBM_BGK_SMAG_Q19, LBM_CUMULANT_Q27 = 0, 1
 LBM_FP32, LBM_FP16S, LBM_BF16S = 0, 1, 2
 LBM_FLAG_NO_COLLIDE, LBM_FLAG_PERIODIC_X, LBM_FLAG_PERIODIC_Z, LBM_FLAG_ONE_NODE = 1, 2, 4, 8
-LBM_FLAG_TMA_STAGED, LBM_FLAG_TEST_STALL = 16, 32
-LBM_DEVFLAG_NONFINITE, LBM_DEVFLAG_RHO_NONPOS, LBM_DEVFLAG_TIMEOUT = 1, 2, 4
+LBM_FLAG_TMA_STAGED, LBM_FLAG_TEST_STALL, LBM_FLAG_TEST_BOUNDS = 16, 32, 64
+LBM_DEVFLAG_NONFINITE, LBM_DEVFLAG_RHO_NONPOS, LBM_DEVFLAG_TIMEOUT, LBM_DEVFLAG_BOUNDS = 1, 2, 4, 8
+# sites of the debug build's index checks (lbm_debug_record)
+SITES = {1: "gather", 2: "scatter", 3: "pair load", 4: "pair store", 5: "quad", 6: "staged",
+         7: "halo", 8: "adjoint", 9: "state"}
 
 LBM_SCALAR_Q7, LBM_SCALAR_Q6, LBM_SCALAR_Q27 = 0, 1, 2
 
@@ -93,6 +101,8 @@ SIGNATURES = [
     ("lbm_get_step", C.c_int64, [_CTX]),
     ("lbm_sync", C.c_int, [_CTX]),
     ("lbm_destroy", None, [_CTX]),
+    ("lbm_debug_build", C.c_int32, []),
+    ("lbm_debug_record", C.c_int, [_CTX, C.POINTER(C.c_int64)]),
 ]
 
 _lib = None
@@ -257,6 +267,22 @@ def lbm_destroy(ctx):
     load().lbm_destroy(ctx)
 
 
+def lbm_debug_build() -> bool:
+    return bool(load().lbm_debug_build())
+
+
+def lbm_debug_record(ctx) -> list[int]:
+    """[failed checks, site of the first, its element offset, the extent checked]."""
+    out = (C.c_int64 * 4)()
+    _check(load().lbm_debug_record(ctx, out), ctx)
+    return list(out)
+
+
+# Index-check failures of the debug build over every Lattice destroyed so far
+# in this process: [failed checks, first site, its offset, its extent].
+DEBUG_TOTAL = [0, 0, 0, 0]
+
+
 # --- parameters -----------------------------------------------------------------
 
 @dataclass
@@ -361,8 +387,17 @@ class Lattice:
     def __del__(self):
         ctx = getattr(self, "ctx", None)
         if ctx is not None and _lib is not None:
+            if _lib.lbm_debug_build():
+                out = (C.c_int64 * 4)()
+                if _lib.lbm_debug_record(ctx, out) == LBM_OK and out[0]:
+                    if DEBUG_TOTAL[0] == 0:
+                        DEBUG_TOTAL[1:] = list(out)[1:]
+                    DEBUG_TOTAL[0] += out[0]
             _lib.lbm_destroy(ctx)
             self.ctx = None
+
+    def debug_record(self) -> list[int]:
+        return lbm_debug_record(self.ctx)
 
     @property
     def Q(self) -> int:

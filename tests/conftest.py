@@ -11,6 +11,8 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a) and the built library")
     config.addinivalue_line("markers", "slow: long-running CPU test")
+    config.addinivalue_line("markers", "planted_bounds: makes the debug build's index checks "
+                            "fail on purpose (LBM_FLAG_TEST_BOUNDS)")
 
 
 @pytest.fixture(autouse=True, scope="session")
@@ -20,6 +22,24 @@ def _oracle_threads():
     import oracle as O
     O.set_threads(os.cpu_count() or 1)
     yield
+
+
+@pytest.fixture(autouse=True)
+def _index_checks(request):
+    """Under the debug build of the library (LBM_LIBRARY=debug), no index
+    check may fail in a test, except where a test plants the failures."""
+    yield
+    lbm = sys.modules.get("paper_2112_08479_gb300.lbm")
+    if lbm is None or lbm._lib is None or not lbm._lib.lbm_debug_build():
+        return
+    import gc
+    gc.collect()                       # destroy the test's lattices: their records count
+    total = list(lbm.DEBUG_TOTAL)
+    lbm.DEBUG_TOTAL[:] = [0, 0, 0, 0]
+    if "planted_bounds" in request.keywords:
+        return
+    assert total[0] == 0, (f"{total[0]} failed index checks, first at site "
+                           f"{lbm.SITES.get(total[1], total[1])}: offset {total[2]} of {total[3]}")
 
 
 def pytest_collection_modifyitems(config, items):

@@ -35,6 +35,25 @@ def test_header_symbols_exported(lib):
     assert sorted(n for n, _, _ in lbm.SIGNATURES) == names
 
 
+def test_debug_build_exports_the_same_entry_points(lib):
+    """The index-checked debug build (built beside the release library by
+    __graft_entry__.build) exports the same entry points and says so."""
+    if not os.path.exists(_build.DEBUG_LIB) or not _build.up_to_date(_build.DEBUG_LIB):
+        pytest.skip("liblbm_debug.so not built")
+    dbg = C.CDLL(_build.DEBUG_LIB)
+    for n in _declared():
+        assert hasattr(dbg, n), n
+    dbg.lbm_debug_build.restype = C.c_int32
+    assert dbg.lbm_debug_build() == 1
+    assert lbm.lbm_debug_build() is False
+
+
+def test_release_build_rejects_the_index_check_hook(lib):
+    s = lbm.lbm_validate(_good(flags=lbm.LBM_FLAG_TEST_BOUNDS))
+    assert s == lbm.LBM_ERR_ARG
+    assert b"debug build" in lbm.load().lbm_last_error(None)
+
+
 def test_struct_layouts():
     # sizes computed from the C declarations with natural alignment
     assert C.sizeof(lbm.lbm_params) == 6 * 4 + 5 * 8 + 3 * 8 + 8 + 2 * 4 + 8 + 8 + 3 * 8 + 4 * 4
@@ -54,7 +73,7 @@ def test_validate_accepts_defaults(lib):
 
 
 @pytest.mark.parametrize("field,value", [
-    ("nx", 0), ("ny", 70000), ("nz", -1), ("model", 5), ("storage", 9), ("flags", 64),
+    ("nx", 0), ("ny", 70000), ("nz", -1), ("model", 5), ("storage", 9), ("flags", 128),
     ("nu", 0.0), ("nu", float("nan")), ("D", -1.0), ("cs_smag", -0.1), ("sc_t", 0.0),
     ("gprime", float("inf")), ("x0", 17), ("x0", -1), ("H", 0), ("noise_amp", -1.0),
     ("scale_f", 0.0), ("front_threshold", float("nan")), ("nx_global", 8), ("x_offset", -1),

@@ -5,10 +5,11 @@
 #include "lbm_cumulant_collide.cuh"
 #include "lbm_internal.h"
 
-// Minimum resident blocks per SM for the adjoint kernel's register allocation
-// (4: 128 registers).
+// Minimum resident blocks per SM for the adjoint kernel's register allocation:
+// 3 (168 registers) measured a reverse step 4 % shorter than 4 (128
+// registers, 84 bytes of spills) on the 256x32x64 box.
 #ifndef LBM_CUM_ADJ_MINB
-#define LBM_CUM_ADJ_MINB 4
+#define LBM_CUM_ADJ_MINB 3
 #endif
 
 namespace lbmgpu {
@@ -16,18 +17,39 @@ namespace lbmgpu {
 // Out-of-place step on the canonical FP32 layout: the own slots are read as
 // on an even AA step and each post-collision population is pushed to slot i
 // of node x + c_i (own slot opp(i) across a wall) as on an odd AA step.
-__global__ void __launch_bounds__(128) cumulant_push_kernel(KParams kp, const float* __restrict__ src,
+// Element offsets of the saved state and the adjoint field: 32-bit (the
+// adjoint entry points need (Q + NS) N < 2^32); at 168 registers they spill
+// nothing (64-bit: 8 bytes) and the reverse step took 1.2 % less time.
+#ifndef LBM_CUM_ADJ_OFF
+#define LBM_CUM_ADJ_OFF unsigned
+#endif
+// The recompute kernel keeps the compiler's register choice (72, no spills):
+// 5 to 8 resident blocks with 32- or 64-bit offsets measured 2-3 % slower
+// reverse steps.
+#ifndef LBM_CUM_PUSH_MINB
+#define LBM_CUM_PUSH_MINB 0
+#endif
+#if LBM_CUM_PUSH_MINB
+#define LBM_CUM_PUSH_BOUNDS __launch_bounds__(128, LBM_CUM_PUSH_MINB)
+#else
+#define LBM_CUM_PUSH_BOUNDS __launch_bounds__(128)
+#endif
+#ifndef LBM_CUM_PUSH_OFF
+#define LBM_CUM_PUSH_OFF unsigned
+#endif
+__global__ void LBM_CUM_PUSH_BOUNDS cumulant_push_kernel(KParams kp, const float* __restrict__ src,
                                                             float* __restrict__ dst) {
+    using Off = LBM_CUM_PUSH_OFF;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= kp.nx) return;
     const Stencil st = make_stencil(kp, x, blockIdx.y, blockIdx.z);
     const size_t N = kp.N;
     float f[27], p[7];
-    gather<27, false>(kp, src, st, f);
-    gather<7, false>(kp, src + 27 * N, st, p);
+    gather<27, false, float, 0, false, true, Off>(kp, src, st, f);
+    gather<7, false, float, 0, false, true, Off>(kp, src + 27 * N, st, p);
     if (!(kp.flags & LBM_FLAG_NO_COLLIDE)) collide_cumulant<7>(kp, f, p);
-    scatter<27, true>(kp, dst, st, f);
-    scatter<7, true>(kp, dst + 27 * N, st, p);
+    scatter<27, true, float, 0, false, true, Off>(kp, dst, st, f);
+    scatter<7, true, float, 0, false, true, Off>(kp, dst + 27 * N, st, p);
 }
 
 cudaError_t launch_cumulant_push_step(const KParams& kp, const float* src, float* dst,
@@ -95,9 +117,9 @@ __global__ void __launch_bounds__(128, LBM_CUM_ADJ_MINB) cumulant_adjoint_kernel
     }
     float f[27], p[7];
 #pragma unroll
-    for (int i = 0; i < 27; ++i) f[i] = ld_chk(kp, LBM_SITE_ADJOINT, st, (size_t)i * N + n, (size_t)34 * N);
+    for (int i = 0; i < 27; ++i) f[i] = ld_chk(kp, LBM_SITE_ADJOINT, st, (LBM_CUM_ADJ_OFF)i * N + n, (size_t)34 * N);
 #pragma unroll
-    for (int k = 0; k < 7; ++k) p[k] = ld_chk(kp, LBM_SITE_ADJOINT, st, (size_t)(27 + k) * N + n, (size_t)34 * N);
+    for (int k = 0; k < 7; ++k) p[k] = ld_chk(kp, LBM_SITE_ADJOINT, st, (LBM_CUM_ADJ_OFF)(27 + k) * N + n, (size_t)34 * N);
 
     // ---- forward recompute (as collide_cumulant<7>) ----
     float chit = 0.0f;
@@ -276,13 +298,13 @@ __global__ void __launch_bounds__(128, LBM_CUM_ADJ_MINB) cumulant_adjoint_kernel
             const float E = b == 1 ? Ez : (b == 2 ? t + Yz : t - Yz);
             const float X = b == 1 ? Xz : (b == 2 ? Xz + gmxy : Xz - gmxy);
             const float gx = E + gmxx;
-            st_chk(kp, LBM_SITE_ADJOINT, lam, (size_t)dir27(-1, b - 1, c - 1) * N + n, (size_t)34 * N, gx - X);
-            st_chk(kp, LBM_SITE_ADJOINT, lam, (size_t)dir27(0, b - 1, c - 1) * N + n, (size_t)34 * N, E);
-            st_chk(kp, LBM_SITE_ADJOINT, lam, (size_t)dir27(1, b - 1, c - 1) * N + n, (size_t)34 * N, gx + X);
+            st_chk(kp, LBM_SITE_ADJOINT, lam, (LBM_CUM_ADJ_OFF)dir27(-1, b - 1, c - 1) * N + n, (size_t)34 * N, gx - X);
+            st_chk(kp, LBM_SITE_ADJOINT, lam, (LBM_CUM_ADJ_OFF)dir27(0, b - 1, c - 1) * N + n, (size_t)34 * N, E);
+            st_chk(kp, LBM_SITE_ADJOINT, lam, (LBM_CUM_ADJ_OFF)dir27(1, b - 1, c - 1) * N + n, (size_t)34 * N, gx + X);
         }
     }
 #pragma unroll
-    for (int k = 0; k < 7; ++k) st_chk(kp, LBM_SITE_ADJOINT, lam, (size_t)(27 + k) * N + n, (size_t)34 * N, gp[k] + gchit);
+    for (int k = 0; k < 7; ++k) st_chk(kp, LBM_SITE_ADJOINT, lam, (LBM_CUM_ADJ_OFF)(27 + k) * N + n, (size_t)34 * N, gp[k] + gchit);
 }
 
 cudaError_t launch_cumulant_adjoint_step(const KParams& kp, const float* state,

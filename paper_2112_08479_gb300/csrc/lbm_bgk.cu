@@ -24,6 +24,7 @@
 #include "lbm_aa2.cuh"
 #include "lbm_bgk_collide.cuh"
 #include "lbm_internal.h"
+#include "lbm_quad.cuh"
 
 namespace lbmgpu {
 
@@ -126,30 +127,6 @@ __global__ void __launch_bounds__(128, std::is_same<S, float>::value ? LBM_STEP2
 #define LBM_STEP4_MINB 3
 #endif
 
-// Two 16-bit values packed in a 32-bit word: the lower node in the low half
-// (hi = 0), the upper in the high half (hi = 1).
-template <typename S> struct Half16;
-template <> struct Half16<__half> {
-    static __device__ __forceinline__ float get(unsigned w, int hi) {
-        return __half2float(__ushort_as_half((unsigned short)(hi ? w >> 16 : w & 0xffffu)));
-    }
-    static __device__ __forceinline__ unsigned bits(float v) {
-        return __half_as_ushort(__float2half_rn(v));
-    }
-};
-template <> struct Half16<__nv_bfloat16> {
-    static __device__ __forceinline__ float get(unsigned w, int hi) {
-        return __uint_as_float(hi ? w & 0xffff0000u : w << 16);   // exact widening
-    }
-    static __device__ __forceinline__ unsigned bits(float v) {
-        return __bfloat16_as_ushort(__float2bfloat16_rn(v));
-    }
-};
-// w with its low (hi = 0) or high (hi = 1) half replaced by the low half of b.
-__device__ __forceinline__ unsigned put16(unsigned w, unsigned b, int hi) {
-    return __byte_perm(w, b, hi ? 0x5410 : 0x3254);
-}
-
 // Even steps with 16-bit storage and nx a multiple of 4: four x-adjacent
 // nodes per thread, each population row moved as one aligned 8-byte word
 // (a warp reads and writes 256-byte row segments, as the FP32 pair kernel
@@ -159,77 +136,18 @@ __device__ __forceinline__ unsigned put16(unsigned w, unsigned b, int hi) {
 // time.  Same arithmetic per node as bgk_step_kernel.  Odd steps stay with
 // bgk_step2_kernel: there the x-shifted rows of a packed quad need shuffles
 // and byte permutes and measured slower than the paired form.
+struct BgkQuadCollide {
+    template <int SL, typename S>
+    static __device__ __forceinline__ void run(const KParams& kp, float (&f)[19],
+                                               float (&p)[ScalarLat<SL>::NS]) {
+        collide_bgk<true, SL>(kp, f, p);
+    }
+};
+
 template <typename S, int SL, typename Off = unsigned>
 __global__ void __launch_bounds__(128, LBM_STEP4_MINB) bgk_even4_kernel(KParams kp, S* __restrict__ f,
                                                                        S* __restrict__ phi) {
-    const unsigned x = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
-    if (x >= (unsigned)kp.nx) return;
-    constexpr int NS = ScalarLat<SL>::NS, D0 = ScalarLat<SL>::D0;
-    constexpr bool R32 = rest32<S, SL>();
-    const unsigned N = kp.N;
-    const unsigned n = blockIdx.z * kp.nxny + blockIdx.y * kp.nx + x;
-    uint2* __restrict__ fw = reinterpret_cast<uint2*>(f);
-    uint2* __restrict__ pw = reinterpret_cast<uint2*>(phi);
-    float4* __restrict__ rest = reinterpret_cast<float4*>(rest_row(phi, NS, N) + n);
-    uint2 wf[19], wp[NS];
-    float4 r = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    // the four elements of each word, checked in the debug build
-    auto ok = [&](const S* a, Off o, int rows) {
-        return LBM_IN(kp, LBM_SITE_QUAD, a, a + o, 4, (size_t)rows * N);
-    };
-    const bool rest_ok = !R32 || LBM_IN(kp, LBM_SITE_QUAD, rest_row(phi, NS, N),
-                                        rest_row(phi, NS, N) + n, 4, N);
-#pragma unroll
-    for (int i = 0; i < 19; ++i)
-        wf[i] = ok(f, (Off)i * N + n, 19) ? ld_pop(fw + (((Off)i * N + n) >> 2)) : make_uint2(0, 0);
-#pragma unroll
-    for (int k = 0; k < NS; ++k) {
-        if (R32 && k == 0) {
-            if (rest_ok) r = ld_pop(rest);
-        } else {
-            wp[k] = ok(phi, (Off)k * N + n, NS) ? ld_pop(pw + (((Off)k * N + n) >> 2))
-                                                 : make_uint2(0, 0);
-        }
-    }
-    const bool collide = !(kp.flags & LBM_FLAG_NO_COLLIDE);
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {       // node x + j: word half j / 2, 16-bit half j % 2
-        float fv[19], pv[NS];
-#pragma unroll
-        for (int i = 0; i < 19; ++i) fv[i] = Half16<S>::get(j < 2 ? wf[i].x : wf[i].y, j & 1);
-#pragma unroll
-        for (int k = 0; k < NS; ++k) {
-            if (R32 && k == 0) pv[0] = j == 0 ? r.x : j == 1 ? r.y : j == 2 ? r.z : r.w;
-            else pv[k] = Half16<S>::get(j < 2 ? wp[k].x : wp[k].y, j & 1);
-        }
-        if (collide) collide_bgk<true, SL>(kp, fv, pv);
-        if constexpr (R32) feed_rest<S>(pv);
-#pragma unroll
-        for (int i = 0; i < 19; ++i) {
-            unsigned& w = j < 2 ? wf[i].x : wf[i].y;
-            w = put16(w, Half16<S>::bits(fv[i]), j & 1);
-        }
-#pragma unroll
-        for (int k = 0; k < NS; ++k) {
-            if (R32 && k == 0) {
-                (j == 0 ? r.x : j == 1 ? r.y : j == 2 ? r.z : r.w) = pv[0];
-            } else {
-                unsigned& w = j < 2 ? wp[k].x : wp[k].y;
-                w = put16(w, Half16<S>::bits(pv[k]), j & 1);
-            }
-        }
-    }
-#pragma unroll
-    for (int i = 0; i < 19; ++i)
-        if (ok(f, (Off)opp(i) * N + n, 19)) st_pop(fw + (((Off)opp(i) * N + n) >> 2), wf[i]);
-#pragma unroll
-    for (int k = 0; k < NS; ++k) {
-        if (R32 && k == 0) {
-            if (rest_ok) st_pop(rest, r);
-        } else if (ok(phi, (Off)(opp(k + D0) - D0) * N + n, NS)) {
-            st_pop(pw + (((Off)(opp(k + D0) - D0) * N + n) >> 2), wp[k]);
-        }
-    }
+    even4_body<19, SL, S, Off, BgkQuadCollide>(kp, f, phi);
 }
 
 template <typename S, int SL, typename Off>

@@ -9,18 +9,50 @@
 
 #include "lbm_cumulant_collide.cuh"
 #include "lbm_internal.h"
+#include "lbm_quad.cuh"
 
 namespace lbmgpu {
 
 // Minimum resident blocks per SM for the register allocator: the D3Q27 FCM
-// scalar holds more live values, so its instantiation gets its own setting;
-// 3 (168 registers, 36-56 bytes of spills) measured 14.1 G node updates/s
-// against 11.9 for 2 and 11.3 for 4 (128 registers, ~200 bytes of spills).
+// scalar holds more live values, so its instantiation gets its own setting,
+// per parity: odd steps 3 (168 registers, 36 bytes of spills; with 32-bit
+// offsets on both parities 3 measured 14.1 G node updates/s against 11.9
+// for 2 and 11.3 for 4), even steps 4 (below).
 #ifndef LBM_Q27_MINB
 #define LBM_Q27_MINB 3
 #endif
+#ifndef LBM_Q27_MINB_EVEN
+#define LBM_Q27_MINB_EVEN 4
+#endif
+// Even steps of the D3Q27-scalar instantiation take 64-bit element offsets
+// on every box: with 32-bit offsets the compiler keeps the scalar's 27
+// offsets of the first read live across the fluid collision for the second
+// read (216 bytes of spills at 128 registers), with 64-bit ones it recomputes
+// them and fits 128 registers without spills (4 blocks per SM): 4.65 -> 4.33
+// ms per even step at 2048x128x256 (FP32).  Odd steps keep 32-bit offsets at
+// 168 registers (36 bytes of spills): their 64-bit form took 5.35 ms against
+// 4.88, and a spill-free 32-bit form whose second read recomputes its
+// neighbour offsets from an opaque copy of the stencil 5.20.
+#ifndef LBM_Q27_WIDE_EVEN
+#define LBM_Q27_WIDE_EVEN 1
+#endif
 #ifndef LBM_CUM_MINB
 #define LBM_CUM_MINB LBM_STEP_MINB
+#endif
+// Even steps of the D3Q7-scalar instantiation: 64-bit element offsets on
+// every box and 6 resident blocks (80 registers).  With 64-bit offsets the
+// compiler walks each array by a pointer and a row stride instead of keeping
+// 34 row offsets, so the kernel fits 80 registers (FP32 without spills, 16
+// bits with 24 bytes) where the 32-bit form spills 216 bytes; at 2048x128x256
+// the even step took 2.85 -> 2.75 ms (FP32), 2.16 -> 2.12 (FP16), 2.18 ->
+// 2.13 (BF16).  7 and 8 blocks (72, 64 registers) and the 64-bit form at 4
+// blocks measured slower; odd steps, whose neighbour offsets are the live
+// values, keep 32-bit offsets and 4 blocks.
+#ifndef LBM_CUM_MINB_EVEN
+#define LBM_CUM_MINB_EVEN 6
+#endif
+#ifndef LBM_CUM_WIDE_EVEN
+#define LBM_CUM_WIDE_EVEN 1
 #endif
 #ifndef LBM_CUM_WSPLIT
 #define LBM_CUM_WSPLIT 1
@@ -141,7 +173,9 @@ __device__ __forceinline__ void cumulant_step_body(const KParams& kp, S* __restr
 // measured 0.6-0.9 % faster; with the D3Q27 scalar the second body costs
 // registers and was 4 % slower, so that instantiation keeps one body).
 template <bool ODD, bool SAVE, typename S, int SL, typename Off = unsigned>
-__global__ void __launch_bounds__(128, SL == 27 ? LBM_Q27_MINB : LBM_CUM_MINB) cumulant_step_kernel(KParams kp, S* __restrict__ f,
+__global__ void __launch_bounds__(128, SL == 27 ? (ODD || SAVE ? LBM_Q27_MINB : LBM_Q27_MINB_EVEN)
+                                                : (ODD || SAVE ? LBM_CUM_MINB : LBM_CUM_MINB_EVEN))
+    cumulant_step_kernel(KParams kp, S* __restrict__ f,
                                                             S* __restrict__ phi,
                                                             float* __restrict__ save) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -157,10 +191,51 @@ __global__ void __launch_bounds__(128, SL == 27 ? LBM_Q27_MINB : LBM_CUM_MINB) c
     }
 }
 
+// Even steps of 16-bit storage with the D3Q7 scalar and nx a multiple of 4:
+// four nodes per thread on packed 8-byte words (lbm_quad.cuh).
+#ifndef LBM_CUM_QUAD
+#define LBM_CUM_QUAD 1
+#endif
+#ifndef LBM_CUM_QUAD_MINB
+#define LBM_CUM_QUAD_MINB 3
+#endif
+#ifndef LBM_CUM_QUAD_OFF
+#define LBM_CUM_QUAD_OFF size_t
+#endif
+#ifndef LBM_CUM_QUAD_NODES
+#define LBM_CUM_QUAD_NODES 4
+#endif
+struct CumulantQuadCollide {
+    template <int SL, typename S>
+    static __device__ __forceinline__ void run(const KParams& kp, float (&f)[27],
+                                               float (&p)[ScalarLat<SL>::NS]) {
+        collide_cumulant<SL, true>(kp, f, p);   // D3Q7: the collision applies the scales
+    }
+};
+
+template <typename S, typename Off>
+__global__ void __launch_bounds__(128, LBM_CUM_QUAD_MINB)
+    cumulant_even4_kernel(KParams kp, S* __restrict__ f, S* __restrict__ phi) {
+    even4_body<27, 7, S, Off, CumulantQuadCollide, LBM_CUM_QUAD_NODES>(kp, f, phi);
+}
+
 template <typename S, int SL>
 static cudaError_t launch_cumulant_typed(const KParams& kp, bool odd, S* f, S* phi, float* save,
                                         cudaStream_t st) {
+    if constexpr (LBM_CUM_QUAD && SL == 7 && !std::is_same<S, float>::value) {
+        constexpr int QN = LBM_CUM_QUAD_NODES;
+        if (!odd && !save && kp.nx % QN == 0 && !(kp.flags & LBM_FLAG_ONE_NODE)) {
+            dim3 block(128), grid((kp.nx / QN + 127) / 128, kp.ny, kp.nz);
+            if (kp.wide)
+                cumulant_even4_kernel<S, size_t><<<grid, block, 0, st>>>(kp, f, phi);
+            else
+                cumulant_even4_kernel<S, LBM_CUM_QUAD_OFF><<<grid, block, 0, st>>>(kp, f, phi);
+            return cudaGetLastError();
+        }
+    }
     dim3 block(128), grid((kp.nx + 127) / 128, kp.ny, kp.nz);
+    // even steps with 64-bit offsets on every box
+    constexpr bool wide_even = SL == 27 ? LBM_Q27_WIDE_EVEN : LBM_CUM_WIDE_EVEN;
     if (kp.wide) {   // (Q + NS) N >= 2^32: 64-bit element offsets; no saved steps
         if (save) return cudaErrorInvalidValue;
         if (odd) cumulant_step_kernel<true, false, S, SL, size_t><<<grid, block, 0, st>>>(kp, f, phi, nullptr);
@@ -170,9 +245,12 @@ static cudaError_t launch_cumulant_typed(const KParams& kp, bool odd, S* f, S* p
     if (save) {
         if (odd) cumulant_step_kernel<true, true, S, SL><<<grid, block, 0, st>>>(kp, f, phi, save);
         else cumulant_step_kernel<false, true, S, SL><<<grid, block, 0, st>>>(kp, f, phi, save);
+    } else if (odd) {
+        cumulant_step_kernel<true, false, S, SL><<<grid, block, 0, st>>>(kp, f, phi, nullptr);
+    } else if constexpr (wide_even) {
+        cumulant_step_kernel<false, false, S, SL, size_t><<<grid, block, 0, st>>>(kp, f, phi, nullptr);
     } else {
-        if (odd) cumulant_step_kernel<true, false, S, SL><<<grid, block, 0, st>>>(kp, f, phi, nullptr);
-        else cumulant_step_kernel<false, false, S, SL><<<grid, block, 0, st>>>(kp, f, phi, nullptr);
+        cumulant_step_kernel<false, false, S, SL><<<grid, block, 0, st>>>(kp, f, phi, nullptr);
     }
     return cudaGetLastError();
 }

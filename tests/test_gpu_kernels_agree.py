@@ -2,8 +2,9 @@
 
 With nx even the BGK step runs two x-adjacent nodes per thread, with paired
 FP32 accesses and, on odd steps, the block-uniform wall-free and interior
-bodies; with 16-bit storage and nx a multiple of 4 it runs four nodes per
-thread on packed 8-byte words (nx = 34 and 770 take the two-node form).
+bodies; with 16-bit storage and nx a multiple of 4 its even steps run four
+nodes per thread on packed 8-byte words (nx = 34 and 770 take the two-node
+form), and so do the cumulant model's even steps (D3Q7 scalar).
 LBM_FLAG_ONE_NODE selects the one-node kernel.  Cases: x and z walls,
 periodic ends, warp and block edges (nx = 770, 1028: three blocks, the
 middle one wholly interior), both scalar lattices of the BGK fluid.
@@ -60,7 +61,9 @@ def _lat(p, s, step):
 
 
 CASES = [("bgk", "fp32", "q7"), ("bgk", "fp16s", "q7"), ("bgk", "bf16s", "q7"),
-         ("bgk", "fp32", "q6"), ("bgk", "fp16s", "q6")]
+         ("bgk", "fp32", "q6"), ("bgk", "fp16s", "q6"),
+         # the cumulant's four-node even step (16-bit storage, nx a multiple of 4)
+         ("cumulant", "fp16s", "q7"), ("cumulant", "bf16s", "q7")]
 ULP = {"fp16s": 2.0**-10, "bf16s": 2.0**-7}
 
 

@@ -192,7 +192,17 @@ __global__ void __launch_bounds__(128, SL == 27 ? (ODD || SAVE ? LBM_Q27_MINB : 
 }
 
 // Even steps of 16-bit storage with the D3Q7 scalar and nx a multiple of 4:
-// four nodes per thread on packed 8-byte words (lbm_quad.cuh).
+// four nodes per thread on packed 8-byte words (lbm_quad.cuh), 168 registers
+// (72 bytes of spills): 2.14 -> 1.90 ms per even step at 2048x128x256 (FP16),
+// 2.15 -> 1.92 (BF16).  Two nodes per thread on 4-byte words measured 2.12
+// (no spills at 168 registers) and 2.16 (128 registers), four nodes at 255
+// registers 2.20.  Odd steps keep the one-node kernel: a four-node odd form
+// (aligned words of every row, the x-shifted rows assembled by a 32-bit
+// shuffle and a byte permute, the warp-edge elements loaded and stored by
+// the edge lanes; bit-identical streaming) took 3.12 ms against 2.27,
+// issuing 916 instructions per node against 865 (unpacking, repacking and
+// the edge stores cost more than the loads they save) at 50 % issue
+// activity with 12 warps per SM.
 #ifndef LBM_CUM_QUAD
 #define LBM_CUM_QUAD 1
 #endif

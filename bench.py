@@ -324,10 +324,11 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
-def config_dict(ws, model="bgk", storage="fp32", slabs=False):
+def config_dict(ws, model="bgk", storage="fp32", slabs=False, scalar="q7"):
     fluid = "D3Q19 BGK-Smagorinsky" if model == "bgk" else "D3Q27 cumulant"
+    lat = {"q7": "D3Q7", "q6": "D3Q6", "q27": "D3Q27 FCM"}[scalar]
     return {"workload": f"lock-exchange {WORKLOAD['nx']}x{WORKLOAD['ny']}x{WORKLOAD['nz']}, "
-                        f"{fluid} + D3Q7 scalar, {storage.upper()} storage, Re={WORKLOAD['Re']:g}, "
+                        f"{fluid} + {lat} scalar, {storage.upper()} storage, Re={WORKLOAD['Re']:g}, "
                         "100 steps + diagnostics per bench step",
             "nodes": WORKLOAD["nx"] * WORKLOAD["ny"] * WORKLOAD["nz"],
             "steps_per_bench_step": INNER,
@@ -449,11 +450,12 @@ def run_ours(args, ws, rank, local):
         from paper_2112_08479_gb300 import slab
         w = WORKLOAD
         p = lbm.lock_exchange(w["nx"], w["ny"], w["nz"], H=w["H"], x0=w["x0"], u_b=w["u_b"],
-                              Re=w["Re"], model=args.model, storage=args.storage)
+                              Re=w["Re"], model=args.model, storage=args.storage,
+                              scalar=args.scalar)
         lat = slab.SlabLattice(p, rank, ws, device=f"cuda:{local}")
         nodes_total = p.N
     else:
-        lat = make_lattice(args.model, args.storage)
+        lat = make_lattice(args.model, args.storage, args.scalar)
         nodes_total = lat.N * ws
     N = lat.N
     barrier(ws)
@@ -502,12 +504,13 @@ def run_ours(args, ws, rank, local):
     torch.cuda.empty_cache()
 
     peak, peak_kind = measured_peak_hbm()
-    bpn = bytes_per_node(args.model, args.storage)
+    bpn = bytes_per_node(args.model, args.storage, args.scalar)
     achieved = bpn * N / kern / 1e9
-    headline = (args.model, args.storage) == ("bgk", "fp32") and args.workload == "config3"
+    headline = ((args.model, args.storage, args.scalar) == ("bgk", "fp32", "q7")
+                and args.workload == "config3")
     kname = "bgk_step2_kernel" if args.model == "bgk" and WORKLOAD["nx"] % 2 == 0 else f"{args.model}_step_kernel"
-    if args.model == "bgk" and args.storage != "fp32" and WORKLOAD["nx"] % 4 == 0:
-        kname = "bgk_even4_kernel + bgk_step2_kernel"
+    if args.storage != "fp32" and args.scalar == "q7" and WORKLOAD["nx"] % 4 == 0:
+        kname = f"{args.model}_even4_kernel + {kname}"
     traffic, tsrc = profiled_traffic(N) if headline else (None, "not captured for this variant")
     roof = {"bound": "hbm",
             "kernel": f"{kname} (AA even/odd, {args.storage.upper()})",
@@ -553,7 +556,7 @@ def run_ours(args, ws, rank, local):
                 "higher_is_better": True, "scaling": "strong" if slabs else "weak",
                 "vs_baseline": None,
                 "dtype": "f32", "data": "synthetic (lock-exchange initial condition)",
-                "config": config_dict(ws, args.model, args.storage, slabs), "e2e": e2e,
+                "config": config_dict(ws, args.model, args.storage, slabs, args.scalar), "e2e": e2e,
                 "gpu_launches": launches,
                 "roofline": roof, "cpu_baseline": cpu, "cpu_baseline_single_thread": cpu1,
                 "clocks": clocks,
@@ -573,6 +576,8 @@ def main():
     ap.add_argument("--workload", default="config3", choices=sorted(WORKLOADS))
     ap.add_argument("--model", default="bgk", choices=["bgk", "cumulant"])
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16s", "bf16s"])
+    ap.add_argument("--scalar", default="q7", choices=["q7", "q6", "q27"],
+                    help="scalar lattice: D3Q7, D3Q6 (BGK only) or D3Q27 FCM (cumulant only)")
     ap.add_argument("--backend", default=None, choices=["nccl", "gloo"],
                     help="torch.distributed backend for N > 1 (default: nccl with GPUs)")
     ap.add_argument("--decomp", default="slab", choices=["slab", "replicas"],

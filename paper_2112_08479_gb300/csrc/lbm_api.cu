@@ -148,6 +148,8 @@ KParams kparams(const lbm_params* p) {
     k.isf = 1.0f / k.sf;
     k.sp = s16 ? (float)p->scale_phi : 1.0f;
     k.isp = 1.0f / k.sp;
+    // 16-bit storage holds the scalar as scale_phi (Phi - chi_s w)
+    k.chi_s = s16 ? (float)LBM_SCALAR_CHI16 : 1.0f;
     k.nu = (float)p->nu;
     // the correctly rounded FP32 quotient, bit-identical to 1.0f / taup0 on
     // the device, so that a kernel may take either form

@@ -32,10 +32,10 @@ __device__ __forceinline__ void node_macros(const KParams& kp, const S* __restri
     float fv[Q], pv[NS];
     gather<Q, ODD, S, 0, false, true, size_t>(kp, f, st, fv);
     gather<NS, ODD, S, ScalarLat<SL>::D0, rest32<S, SL>(), true, size_t>(kp, phi, st, pv);
-    float c = 0.0f;   // chi - 1 (Phi is held as Phi - w)
+    float c = 0.0f;   // chi - 1 (Phi is held as Phi - w, in 16 bits as Phi - chi_s w)
 #pragma unroll
     for (int k = 0; k < NS; ++k) c += pv[k];
-    if (is16<S>()) c *= kp.isp;
+    if (is16<S>()) c = fmaf(c, kp.isp, kp.chi_s - 1.0f);
     float d = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -74,9 +74,9 @@ __global__ void init_kernel(KParams kp, S* __restrict__ f, S* __restrict__ phi,
     const int y = blockIdx.y, z = blockIdx.z;
     const unsigned n = (unsigned)x + (unsigned)kp.nx * ((unsigned)y + (unsigned)kp.ny * (unsigned)z);
     const size_t N = kp.N;
-    float c;  // chi0 - 1
+    float c;  // chi0 - chi_s: the stored deviation of chi (chi0 - 1 in FP32)
     if (chi0) {
-        c = chi0[n] - 1.0f;
+        c = chi0[n] - (is16<S>() ? kp.chi_s : 1.0f);
     } else {
         // global column and node index (an x-slab keys the noise by the
         // node's index in the whole box)
@@ -89,7 +89,7 @@ __global__ void init_kernel(KParams kp, S* __restrict__ f, S* __restrict__ phi,
             const double r = (double)(splitmix64(seed ^ ng) >> 11) * 0x1.0p-53;
             v += amp * (2.0 * r - 1.0);
         }
-        c = (float)v;
+        c = is16<S>() ? (float)(v + (1.0 - (double)kp.chi_s)) : (float)v;
     }
     constexpr int NS = ScalarLat<SL>::NS;
 #pragma unroll
@@ -149,7 +149,7 @@ __global__ void get_state_kernel(KParams kp, const S* __restrict__ f, const S* _
 #pragma unroll
     for (int k = 0; k < NS; ++k)
         st_chk(kp, LBM_SITE_STATE, dst, (size_t)(Q + k) * N + n, (Q + NS) * N,
-               is16<S>() ? pv[k] * kp.isp : pv[k]);
+               is16<S>() ? phi_canonical(kp, pv[k], ScalarLat<SL>::w(k)) : pv[k]);
 }
 
 template <int Q, int SL, typename S>
@@ -169,9 +169,10 @@ __global__ void set_state_kernel(KParams kp, S* __restrict__ f, S* __restrict__ 
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
         const float v = ld_chk(kp, LBM_SITE_STATE, src, (size_t)(Q + k) * N + n, (Q + NS) * N);
+        const float sv = is16<S>() ? phi_stored(kp, v, ScalarLat<SL>::w(k)) : v;
         if (rest32<S, SL>() && k == 0)
-            st_chk(kp, LBM_SITE_STATE, rest_row(phi, NS, kp.N), n, N, v * kp.sp);
-        else store_chk(kp, LBM_SITE_STATE, phi, (size_t)k * N + n, NS * N, is16<S>() ? v * kp.sp : v);
+            st_chk(kp, LBM_SITE_STATE, rest_row(phi, NS, kp.N), n, N, sv);
+        else store_chk(kp, LBM_SITE_STATE, phi, (size_t)k * N + n, NS * N, sv);
     }
 }
 

@@ -48,7 +48,8 @@ __global__ void __launch_bounds__(128, LBM_STEP_MINB) bgk_step_kernel(KParams kp
         for (int i = 0; i < 19; ++i) save_pop(kp, save, 19 + NS, i, n, s16 ? fv[i] * kp.isf : fv[i]);
 #pragma unroll
         for (int k = 0; k < NS; ++k)
-            save_pop(kp, save, 19 + NS, 19 + k, n, s16 ? pv[k] * kp.isp : pv[k]);
+            save_pop(kp, save, 19 + NS, 19 + k, n,
+                     s16 ? phi_canonical(kp, pv[k], ScalarLat<SL>::w(k)) : pv[k]);
     }
     if (!(kp.flags & LBM_FLAG_NO_COLLIDE)) collide_bgk<s16, SL>(kp, fv, pv);
     if constexpr (R32) feed_rest<S>(pv);
@@ -82,14 +83,17 @@ __device__ __forceinline__ void bgk_step2_body(const KParams& kp, S* __restrict_
     constexpr bool s16 = !std::is_same<S, float>::value;   // populations in storage units
     if (SAVE && st.active) {
         const unsigned N = kp.N;
-        const float a = s16 ? kp.isf : 1.0f, b = s16 ? kp.isp : 1.0f;
+        const float a = s16 ? kp.isf : 1.0f;
 #pragma unroll
         for (int i = 0; i < 19; ++i)
             *reinterpret_cast<float2*>(save + (size_t)i * N + st.n) = make_float2(a * f0[i], a * f1[i]);
 #pragma unroll
-        for (int k = 0; k < NS; ++k)
+        for (int k = 0; k < NS; ++k) {
+            const float w = ScalarLat<SL>::w(k);
             *reinterpret_cast<float2*>(save + (size_t)(19 + k) * N + st.n) =
-                make_float2(b * p0[k], b * p1[k]);
+                s16 ? make_float2(phi_canonical(kp, p0[k], w), phi_canonical(kp, p1[k], w))
+                    : make_float2(p0[k], p1[k]);
+        }
     }
     if (!(kp.flags & LBM_FLAG_NO_COLLIDE)) {
         collide_bgk<s16, SL>(kp, f0, p0);

@@ -44,8 +44,8 @@ __device__ __forceinline__ void collide_bgk(const KParams& kp, float (&f)[19],
     float chs = 0.0f;  // scale_phi (chi - 1)
 #pragma unroll
     for (int k = 0; k < NS; ++k) chs += p[k];
-    const float chit = chs * isp;  // chi - 1
-    const float chi = 1.0f + chit;
+    const float chit = chs * isp;  // chi - chi_s
+    const float chi = kp.chi_s + chit;
     const float Fx = kp.gx * chi, Fy = kp.gy * chi, Fz = kp.gz * chi;
 
     float drho = f[0], jx = 0.0f, jy = 0.0f, jz = 0.0f;

@@ -93,6 +93,7 @@ struct KParams {
     int* devflags;       // sticky device flags (LBM_DEVFLAG_*) of the context
     int x_off, nxg;      // x-slab: global x of local column 0, nx of the whole box
     int wide;            // (Q + NS) N >= 2^32: 64-bit element offsets in the step kernels
+    float chi_s;         // the scalar is stored as sp (Phi - chi_s w): 1 in FP32 storage
 };
 
 // ---------------------------------------------------------------------------
@@ -377,6 +378,19 @@ template <typename S>
 __device__ __forceinline__ void store_chk(const KParams& kp, int site, S* __restrict__ a, size_t o,
                                           size_t extent, float v) {
     if (LBM_IN(kp, site, a, a + o, 1, extent)) Store<S>::st(a + o, v);
+}
+
+// With 16-bit storage the scalar populations are held as scale_phi (Phi_k -
+// chi_s w_k), deviations from the scalar field chi_s (KParams::chi_s); the
+// FP32 form of the state (lbm_get_state, saved steps) is Phi_k - w_k.  The
+// collisions see chi = chi_s + sum_k (stored_k) / scale_phi, and their
+// equilibria keep the same form in the stored units.  These convert one
+// population of weight w.
+__device__ __forceinline__ float phi_canonical(const KParams& kp, float v, float w) {
+    return fmaf(v, kp.isp, w * (kp.chi_s - 1.0f));
+}
+__device__ __forceinline__ float phi_stored(const KParams& kp, float c, float w) {
+    return (c - w * (kp.chi_s - 1.0f)) * kp.sp;
 }
 
 // Saved pre-collision state (lbm_step_save): row r of node n in a buffer of

@@ -81,7 +81,7 @@ __device__ __forceinline__ void cumulant_fcm_step_body(const KParams& kp, S* __r
         if (SAVE) {
 #pragma unroll
             for (int k = 0; k < 27; ++k)
-                save_pop(kp, save, 54, 27 + k, n, s16 ? pv[k] * kp.isp : pv[k]);
+                save_pop(kp, save, 54, 27 + k, n, s16 ? phi_canonical(kp, pv[k], w27(k)) : pv[k]);
         }
         if (s16) {
 #pragma unroll
@@ -148,7 +148,8 @@ __device__ __forceinline__ void cumulant_step_body(const KParams& kp, S* __restr
             save_pop(kp, save, 27 + NS, i, n, s16 ? fv[i] * kp.isf : fv[i]);
 #pragma unroll
         for (int k = 0; k < NS; ++k)
-            save_pop(kp, save, 27 + NS, 27 + k, n, s16 ? pv[k] * kp.isp : pv[k]);
+            save_pop(kp, save, 27 + NS, 27 + k, n,
+                     s16 ? phi_canonical(kp, pv[k], ScalarLat<SL>::w(k)) : pv[k]);
     }
     if (s16 && !fold) {
 #pragma unroll

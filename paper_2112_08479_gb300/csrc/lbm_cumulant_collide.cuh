@@ -102,8 +102,8 @@ template <bool SCALED>
 __device__ __forceinline__ void cumulant_fluid(const KParams& kp, float (&f)[27], float chs,
                                                float& chit_out, float& chi_out, float& hx,
                                                float& hy, float& hz) {
-    const float chit = SCALED ? chs * kp.isp : chs;
-    const float chi = 1.0f + chit;
+    const float chit = SCALED ? chs * kp.isp : chs;   // chi - chi_s
+    const float chi = kp.chi_s + chit;
     const float Fx = kp.gx * chi, Fy = kp.gy * chi, Fz = kp.gz * chi;
 
     // moments of order <= 2, summed by lines

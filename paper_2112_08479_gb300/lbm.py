@@ -30,6 +30,8 @@ SITES = {1: "gather", 2: "scatter", 3: "pair load", 4: "pair store", 5: "quad", 
          7: "halo", 8: "adjoint", 9: "state"}
 
 LBM_SCALAR_Q7, LBM_SCALAR_Q6, LBM_SCALAR_Q27 = 0, 1, 2
+# 16-bit storage holds the scalar as scale_phi (Phi - LBM_SCALAR_CHI16 w)
+LBM_SCALAR_CHI16 = 1.0
 
 MODELS = {"bgk": LBM_BGK_SMAG_Q19, "cumulant": LBM_CUMULANT_Q27}
 SCALARS = {"q7": LBM_SCALAR_Q7, "q6": LBM_SCALAR_Q6, "q27": LBM_SCALAR_Q27}

@@ -36,6 +36,19 @@ def wscalar(p: lbm.Params) -> np.ndarray:
     return O.velocities_scalar(p.scalar)[1]
 
 
+def stored_phi(phi, p: lbm.Params, k0: int = 0) -> np.ndarray:
+    """Magnitude, in canonical units, of what 16-bit storage holds for the
+    canonical scalar rows phi (Phi - w, rows k0, k0 + 1, ... of the scalar
+    lattice): |Phi - LBM_SCALAR_CHI16 w|, the magnitude its rounding scales
+    with.  FP32 storage holds Phi - w itself."""
+    phi = np.asarray(phi, dtype=np.float64)
+    if p.storage == lbm.LBM_FP32:
+        return np.abs(phi)
+    w = wscalar(p)[k0:k0 + phi.shape[0]]
+    w = w.reshape((-1,) + (1,) * (phi.ndim - 1))
+    return np.abs(phi + (1.0 - lbm.LBM_SCALAR_CHI16) * w)
+
+
 def canonical_to_oracle(state: np.ndarray, p: lbm.Params, shifted: bool = True):
     """[Q+7, N] float32 (f - w, Phi - w) -> oracle (f, phi) float64 arrays.
     shifted=False takes the rows as they are (streaming tests, adjoints)."""
@@ -118,5 +131,5 @@ def rest_row_tol(p, pre, rel):
     out = np.zeros(pre.shape[1])
     for m in range(pre.shape[1]):
         _, po = O.collide_node(op, pre[: p.Q, m] + w, pre[p.Q:, m] + ws)
-        out[m] = rel * np.abs(po[1:] - ws[1:]).sum() * 1.01
+        out[m] = rel * stored_phi(po[1:] - ws[1:], p, 1).sum() * 1.01
     return out

@@ -54,6 +54,16 @@ def test_release_build_rejects_the_index_check_hook(lib):
     assert b"debug build" in lbm.load().lbm_last_error(None)
 
 
+def test_storage_constants_match_the_header():
+    src = open(HEADER).read()
+    m = re.search(r"#define LBM_SCALAR_CHI16 ([0-9.]+)", src)
+    assert m and float(m.group(1)) == lbm.LBM_SCALAR_CHI16
+    for name in ("LBM_FLAG_TEST_BOUNDS", "LBM_FLAG_TEST_STALL", "LBM_FLAG_TMA_STAGED",
+                 "LBM_DEVFLAG_BOUNDS", "LBM_DEVFLAG_TIMEOUT"):
+        m = re.search(rf"#define {name} (\d+)", src)
+        assert m and int(m.group(1)) == getattr(lbm, name), name
+
+
 def test_struct_layouts():
     # sizes computed from the C declarations with natural alignment
     assert C.sizeof(lbm.lbm_params) == 6 * 4 + 5 * 8 + 3 * 8 + 8 + 2 * 4 + 8 + 8 + 3 * 8 + 4 * 4

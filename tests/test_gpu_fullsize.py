@@ -9,7 +9,7 @@ import pytest
 import oracle as O
 from paper_2112_08479_gb300 import inputs, lbm
 
-from helpers import rest_row_tol, weights, window_oracle
+from helpers import rest_row_tol, stored_phi, weights, window_oracle
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -61,7 +61,7 @@ def test_full_size_sampled_nodes(model, storage):
             got = s1v[:, z, y, x].cpu().numpy().astype(np.float64)
             # FP32 arithmetic, then round-to-nearest into the storage type
             tol_f = rel * np.abs(f_o) * 1.001 + 1e-5 * scale
-            tol_p = rel * np.abs(phi_o) * 1.001 + 1e-6
+            tol_p = rel * stored_phi(phi_o, p) * 1.001 + 1e-6
             if rel:   # FP32 rest population with rounding feedback
                 col = s0v[:, z, y, x].cpu().numpy().astype(np.float64)[:, None]
                 tol_p[0] = rest_row_tol(p, col, rel)[0] + 1e-6
@@ -114,7 +114,7 @@ def test_wide_box_sampled_nodes(model, storage):
             f_o, phi_o = window_oracle(p, s0v, node, 1)
             got = s1v[:, z, y, x].cpu().numpy().astype(np.float64)
             tol_f = rel * np.abs(f_o) * 1.001 + 1e-5 * scale
-            tol_p = rel * np.abs(phi_o) * 1.001 + 1e-6
+            tol_p = rel * stored_phi(phi_o, p) * 1.001 + 1e-6
             col = s0v[:, z, y, x].cpu().numpy().astype(np.float64)[:, None]
             tol_p[0] = rest_row_tol(p, col, rel)[0] + 1e-6
             assert np.all(np.abs(got[: p.Q] - f_o) <= tol_f), (parity, node)

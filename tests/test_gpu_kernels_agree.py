@@ -31,7 +31,7 @@ import pytest
 
 from paper_2112_08479_gb300 import inputs, lbm
 
-from helpers import weights, wscalar
+from helpers import stored_phi, weights, wscalar
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -109,12 +109,15 @@ def test_collision_steps_match_one_node(model, storage, scalar, geometry, nx):
             assert bad.size == 0, (n, bad[:5].tolist())
         else:
             d = np.abs(x.astype(np.float64) - y)
-            # one ulp of the stored 16-bit value (normal or subnormal range)
-            tol = np.maximum(np.maximum(np.abs(x), np.abs(y)) * scale * ULP[storage], 2.0**-24) / scale
+            # one ulp of the stored 16-bit value (normal or subnormal range);
+            # the scalar is stored as Phi - chi_s w
+            mag = np.maximum(np.abs(x), np.abs(y)).astype(np.float64)
+            mag[Q:] = np.maximum(stored_phi(x[Q:], p2), stored_phi(y[Q:], p2))
+            tol = np.maximum(mag * scale * ULP[storage], 2.0**-24) / scale
             # the FP32 rest population of the scalar takes the roundings of
             # the node's moving scalar populations: one ulp each
             if p2.scalar != lbm.LBM_SCALAR_Q6:
-                tol[Q] = (np.abs(y[Q + 1:]).sum(axis=0) * ULP[storage] + 2.0**-24 * 8
+                tol[Q] = (stored_phi(y[Q + 1:], p2, 1).sum(axis=0) * ULP[storage] + 2.0**-24 * 8
                           + np.abs(y[Q]) * 2.0**-22)
             bad = np.argwhere(d > tol * 1.0001)
             assert bad.size == 0, (n, bad[:5].tolist(), [(float(x[r, c]), float(y[r, c]))

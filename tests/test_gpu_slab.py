@@ -19,6 +19,8 @@ import pytest
 
 from paper_2112_08479_gb300 import lbm
 
+from helpers import stored_phi
+
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
@@ -99,9 +101,10 @@ def test_two_slabs_equal_whole_box(case):
             assert bad.size == 0, (step, bad[:5].tolist())
         else:
             diff = np.abs(got_s.astype(np.float64) - want)
-            tol = np.maximum(np.maximum(np.abs(got_s), np.abs(want)) * scale * ulp,
-                             2.0**-24) / scale
-            tol[p.Q] = np.abs(want[p.Q + 1:]).sum(axis=0) * ulp + 2.0**-20   # FP32 rest row
+            mag = np.maximum(np.abs(got_s), np.abs(want)).astype(np.float64)
+            mag[p.Q:] = np.maximum(stored_phi(got_s[p.Q:], p), stored_phi(want[p.Q:], p))
+            tol = np.maximum(mag * scale * ulp, 2.0**-24) / scale
+            tol[p.Q] = stored_phi(want[p.Q + 1:], p, 1).sum(axis=0) * ulp + 2.0**-20   # FP32 rest
             assert np.all(diff <= tol * 1.0001), step
             assert np.count_nonzero(diff) <= max(16, 1e-3 * diff.size), step
         dw = whole.diag()

@@ -1,5 +1,6 @@
-"""16-bit shifted storage (FP16 / BF16 of scale * (f - w) and scale * Phi,
-round-to-nearest-even, FP32 arithmetic) against the FP64 oracle.
+"""16-bit shifted storage (FP16 / BF16 of scale * (f - w) and
+scale * (Phi - chi_s w), chi_s = LBM_SCALAR_CHI16, round-to-nearest-even, FP32
+arithmetic) against the FP64 oracle.
 
 Bars are derived from the rounding: a stored value is the RN rounding of the
 exact FP32 result, so its error is at most half an ulp of the significand
@@ -11,7 +12,7 @@ import oracle as O
 from paper_2112_08479_gb300 import inputs, lbm
 
 from helpers import (canonical_to_oracle, lock_state_oracle, oracle_params, oracle_to_canonical,
-                     rest_row_tol, weights)
+                     rest_row_tol, stored_phi, weights, wscalar)
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -34,6 +35,18 @@ def _rn(v, storage, scale):
     return t.numpy() / scale
 
 
+def _phi_round_trip(v, p, rows, sixteen=True):
+    """What lbm_set_state followed by lbm_get_state returns for canonical
+    scalar rows v (Phi - w): stored as scale_phi (Phi - chi_s w) in FP32
+    arithmetic (the scale is a power of two), rounded to the storage type
+    (sixteen) or kept in FP32 (the rest population), and converted back."""
+    c = (wscalar(p)[rows] * (lbm.LBM_SCALAR_CHI16 - 1.0)).astype(np.float32)[:, None]
+    t = (v.astype(np.float32) - c).astype(np.float32)
+    if sixteen:
+        t = _rn(t, p.storage, p.scale_phi).astype(np.float32)
+    return (t + c).astype(np.float32)
+
+
 @pytest.mark.parametrize("storage", [lbm.LBM_FP16S, lbm.LBM_BF16S])
 @pytest.mark.parametrize("model", [0, 1])
 def test_set_get_round_trip_is_rn(storage, model):
@@ -43,9 +56,10 @@ def test_set_get_round_trip_is_rn(storage, model):
     lat.set_state(torch.from_numpy(s0).cuda())
     got = lat.get_state().cpu().numpy()
     assert np.array_equal(got[: p.Q], _rn(s0[: p.Q], storage, p.scale_f))
-    # the scalar's rest population is held in FP32 (power-of-two scale: exact)
-    assert np.array_equal(got[p.Q], s0[p.Q])
-    assert np.array_equal(got[p.Q + 1:], _rn(s0[p.Q + 1:], storage, p.scale_phi))
+    # the scalar's rest population is held in FP32 (power-of-two scale; the
+    # shift to chi_s and back rounds in FP32), the others in 16 bits
+    assert np.array_equal(got[p.Q:p.Q + 1], _phi_round_trip(s0[p.Q:p.Q + 1], p, [0], False))
+    assert np.array_equal(got[p.Q + 1:], _phi_round_trip(s0[p.Q + 1:], p, list(range(1, 7))))
 
 
 @pytest.mark.parametrize("storage", [lbm.LBM_FP16S, lbm.LBM_BF16S])
@@ -68,7 +82,8 @@ def test_one_step_within_rounding(storage, model, nx, flags):
         f, phi = O.step(op, f, phi)
         got = lat.get_state().cpu().numpy().astype(np.float64)
         want = oracle_to_canonical(f, phi, p)
-        tol = REL[storage] * np.abs(want) * 1.01 + 1e-5 * np.r_[[scale] * p.Q, [1e-1] * 7][:, None]
+        mag = np.concatenate([np.abs(want[: p.Q]), stored_phi(want[p.Q:], p)])   # what is stored
+        tol = REL[storage] * mag * 1.01 + 1e-5 * np.r_[[scale] * p.Q, [1e-1] * 7][:, None]
         # the FP32 rest population receives the roundings of the populations
         # its node's collision produced
         tol[p.Q] = rest_row_tol(p, pre, REL[storage]) + 1e-6
@@ -127,11 +142,11 @@ def test_fp32_rest_row_is_not_rounded(storage, model, scalar, nx):
     s = (0.1 * inputs.uniform((p.Q + p.NS, p.N), 5, 1.0)).astype(np.float32)
     lat.set_state(torch.from_numpy(s).cuda())
     s0 = lat.get_state().cpu().numpy()
-    assert np.array_equal(s0[p.Q], s[p.Q])
+    assert np.array_equal(s0[p.Q:p.Q + 1], _phi_round_trip(s[p.Q:p.Q + 1], p, [0], False))
     for n in range(1, 3):
         lat.step(1)
         got = lat.get_state().cpu().numpy()
-        assert np.array_equal(got[p.Q], s[p.Q]), n          # the rest never moves
+        assert np.array_equal(got[p.Q], s0[p.Q]), n         # the rest never moves
         assert np.array_equal(np.sort(got[p.Q + 1:], axis=None), np.sort(s0[p.Q + 1:], axis=None))
 
 

@@ -57,6 +57,14 @@ namespace lbmgpu {
 #ifndef LBM_CUM_WSPLIT
 #define LBM_CUM_WSPLIT 1
 #endif
+// Odd steps of blocks with no node at a face of the box read and write at
+// block-uniform offsets from the node (block_no_face below): 2.26 -> 2.20 ms
+// per odd step at 2048x128x256 (FP16), 2.31 -> 2.27 (BF16), 3.04 -> 3.01
+// (FP32).  The same form in the paired BGK kernel's wall-free body measured
+// slower (FP16 odd 1.54 -> 1.59 ms) and was not adopted.
+#ifndef LBM_CUM_NOFACE
+#define LBM_CUM_NOFACE 1
+#endif
 
 // With the D3Q27 scalar the factorized-central-moment collision needs, of
 // the 27 pre-collision scalar populations, only chi, their first moments and
@@ -130,7 +138,58 @@ __device__ __forceinline__ void cumulant_fcm_step_body(const KParams& kp, S* __r
     scatter<27, ODD, S, 0, R32, W, Off>(kp, phi, st, pv);
 }
 
-template <bool ODD, bool SAVE, typename S, int SL, bool W, typename Off>
+// Odd steps of a block none of whose nodes has a neighbour across a face of
+// the box (block_no_face): no wall and no periodic wrap is involved, so the
+// element offset of population k's source (row opp(d), node n - c_d) is n +
+// ((opp(d) - D0) N - c_dx - c_dy nx - c_dz nx ny), and of its target (row k,
+// node n + c_d) n + (k N + c_dx + c_dy nx + c_dz nx ny): the brackets are the
+// same for every thread of the block.  Offsets are formed modulo 2^32 (or
+// 2^64) with Off; the sums land inside the arrays.
+__device__ __forceinline__ bool block_no_face(const KParams& kp) {
+    const int x0 = blockIdx.x * blockDim.x, y = blockIdx.y, z = blockIdx.z;
+    return x0 >= 1 && x0 + (int)blockDim.x <= kp.nx - 1 && y >= 1 && y <= kp.ny - 2 && z >= 1 &&
+           z <= kp.nz - 2;
+}
+template <typename Off>
+__device__ __forceinline__ Off shift_of(const KParams& kp, int d) {
+    return (Off)(long long)(cx27(d) + cy27(d) * kp.nx + cz27(d) * (long long)kp.nxny);
+}
+template <int Q, typename S, int D0 = 0, bool R32 = false, typename Off = unsigned>
+__device__ __forceinline__ void gather_no_face(const KParams& kp, const S* __restrict__ a,
+                                               unsigned n, float (&v)[Q]) {
+    const unsigned N = kp.N;
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+        const int d = k + D0;
+        if (R32 && d == 0) {
+            const float* r = rest_row(a, Q, N);
+            v[k] = LBM_IN(kp, LBM_SITE_GATHER, r, r + n, 1, N) ? ld_pop(r + n) : 0.0f;
+            continue;
+        }
+        const Off o = d == 0 ? (Off)k * N : (Off)(opp(d) - D0) * N - shift_of<Off>(kp, d);
+        const Off e = (Off)n + o;
+        v[k] = LBM_IN(kp, LBM_SITE_GATHER, a, a + e, 1, (size_t)Q * N) ? Store<S>::ld(a + e) : 0.0f;
+    }
+}
+template <int Q, typename S, int D0 = 0, bool R32 = false, typename Off = unsigned>
+__device__ __forceinline__ void scatter_no_face(const KParams& kp, S* __restrict__ a, unsigned n,
+                                                const float (&v)[Q]) {
+    const unsigned N = kp.N;
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+        const int d = k + D0;
+        if (R32 && d == 0) {
+            float* r = rest_row(a, Q, N);
+            if (LBM_IN(kp, LBM_SITE_SCATTER, r, r + n, 1, N)) st_pop(r + n, v[k]);
+            continue;
+        }
+        const Off o = d == 0 ? (Off)k * N : (Off)k * N + shift_of<Off>(kp, d);
+        const Off e = (Off)n + o;
+        if (LBM_IN(kp, LBM_SITE_SCATTER, a, a + e, 1, (size_t)Q * N)) Store<S>::st(a + e, v[k]);
+    }
+}
+
+template <bool ODD, bool SAVE, typename S, int SL, bool W, typename Off, bool NOFACE = false>
 __device__ __forceinline__ void cumulant_step_body(const KParams& kp, S* __restrict__ f,
                                                    S* __restrict__ phi, float* __restrict__ save,
                                                    const Stencil& st) {
@@ -138,8 +197,13 @@ __device__ __forceinline__ void cumulant_step_body(const KParams& kp, S* __restr
     constexpr int NS = ScalarLat<SL>::NS;
     constexpr bool R32 = rest32<S, SL>();
     float fv[27], pv[NS];
-    gather<27, ODD, S, 0, false, W, Off>(kp, f, st, fv);
-    gather<NS, ODD, S, 0, R32, W, Off>(kp, phi, st, pv);
+    if constexpr (NOFACE) {
+        gather_no_face<27, S, 0, false, Off>(kp, f, n, fv);
+        gather_no_face<NS, S, 0, R32, Off>(kp, phi, n, pv);
+    } else {
+        gather<27, ODD, S, 0, false, W, Off>(kp, f, st, fv);
+        gather<NS, ODD, S, 0, R32, W, Off>(kp, phi, st, pv);
+    }
     constexpr bool s16 = !std::is_same<S, float>::value;   // populations in storage units
     constexpr bool fold = s16 && SL == 7;                  // the collision applies the scales
     if (SAVE) {
@@ -165,8 +229,13 @@ __device__ __forceinline__ void cumulant_step_body(const KParams& kp, S* __restr
         for (int k = 0; k < NS; ++k) pv[k] *= kp.sp;
     }
     if constexpr (R32) feed_rest<S>(pv);
-    scatter<27, ODD, S, 0, false, W, Off>(kp, f, st, fv);
-    scatter<NS, ODD, S, 0, R32, W, Off>(kp, phi, st, pv);
+    if constexpr (NOFACE) {
+        scatter_no_face<27, S, 0, false, Off>(kp, f, n, fv);
+        scatter_no_face<NS, S, 0, R32, Off>(kp, phi, n, pv);
+    } else {
+        scatter<27, ODD, S, 0, false, W, Off>(kp, f, st, fv);
+        scatter<NS, ODD, S, 0, R32, W, Off>(kp, phi, st, pv);
+    }
 }
 
 // One node per thread.  On odd steps the blocks with no wall neighbour
@@ -185,7 +254,11 @@ __global__ void __launch_bounds__(128, SL == 27 ? (ODD || SAVE ? LBM_Q27_MINB : 
     if constexpr (SL == 27) {
         cumulant_fcm_step_body<ODD, SAVE, S, true, Off>(kp, f, phi, save, st);
     } else {
-        if (!ODD || (LBM_CUM_WSPLIT && block_interior(kp)))
+        if (!ODD)
+            cumulant_step_body<ODD, SAVE, S, SL, false, Off>(kp, f, phi, save, st);
+        else if (LBM_CUM_NOFACE && block_no_face(kp))
+            cumulant_step_body<ODD, SAVE, S, SL, false, Off, true>(kp, f, phi, save, st);
+        else if (!LBM_CUM_NOFACE && LBM_CUM_WSPLIT && block_interior(kp))
             cumulant_step_body<ODD, SAVE, S, SL, false, Off>(kp, f, phi, save, st);
         else
             cumulant_step_body<ODD, SAVE, S, SL, true, Off>(kp, f, phi, save, st);

@@ -42,7 +42,7 @@ def _to_dev(a):
 @pytest.mark.parametrize("model", [0, 1])
 @pytest.mark.parametrize("shape", [(5, 3, 4), (7, 4, 6), (130, 2, 3), (2, 3, 4), (64, 2, 3),
                                    (66, 3, 2), (258, 2, 2), (1030, 2, 4), (512, 3, 2),
-                                   (1536, 2, 2)])
+                                   (1536, 2, 2), (512, 4, 5)])
 @pytest.mark.parametrize("flags", [0, lbm.LBM_FLAG_PERIODIC_X, lbm.LBM_FLAG_PERIODIC_Z])
 def test_streaming_permutation_bit_exact(model, shape, flags):
     """Collision off: after n steps (even and odd AA parities) the GPU state is
@@ -51,7 +51,8 @@ def test_streaming_permutation_bit_exact(model, shape, flags):
     (one active lane, one full warp, a warp plus one lane, a block edge;
     1030 x 2 x 4 has blocks away from every wall, which take the
     single-element shifted accesses on odd steps; nx = 512 and 1536 give
-    several 128-node blocks per row)."""
+    several 128-node blocks per row; 512 x 4 x 5 has cumulant blocks with no
+    node at a face of the box, whose odd steps use block-uniform offsets)."""
     nx, ny, nz = shape
     p = lbm.Params(nx, ny, nz, model=model, flags=lbm.LBM_FLAG_NO_COLLIDE | flags, x0=1, H=nz)
     lat = _lat(p)

@@ -61,7 +61,9 @@ namespace lbmgpu {
 // block-uniform offsets from the node (block_no_face below): 2.26 -> 2.20 ms
 // per odd step at 2048x128x256 (FP16), 2.31 -> 2.27 (BF16), 3.04 -> 3.01
 // (FP32).  The same form in the paired BGK kernel's wall-free body measured
-// slower (FP16 odd 1.54 -> 1.59 ms) and was not adopted.
+// slower (FP16 odd 1.54 -> 1.59 ms), and as a second odd body of the D3Q27
+// FCM instantiation no faster (FP32 4.90 -> 4.89 ms, FP16 4.04 -> 4.11, 36 ->
+// 92 bytes of spills in FP32); neither was adopted.
 #ifndef LBM_CUM_NOFACE
 #define LBM_CUM_NOFACE 1
 #endif

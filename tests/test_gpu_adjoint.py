@@ -277,10 +277,13 @@ def test_front_gradient_vs_fp64_reference_sub_case():
 
 @pytest.mark.parametrize("flags", [0, lbm.LBM_FLAG_PERIODIC_X | lbm.LBM_FLAG_PERIODIC_Z])
 @pytest.mark.parametrize("w_fw", [0.0, 1.0])
-def test_cumulant_adjoint_step_matches_autograd_vjp(flags, w_fw):
+@pytest.mark.parametrize("nx", [20, 260])
+def test_cumulant_adjoint_step_matches_autograd_vjp(flags, w_fw, nx):
     """One reverse step of the cumulant model against torch.autograd on the
-    FP64 restatement (truncated ln / exp of the moment generating function)."""
-    p = _sub_case(nx=20, ny=5, nz=6, model=lbm.LBM_CUMULANT_Q27, flags=flags, gprime=3e-3,
+    FP64 restatement (truncated ln / exp of the moment generating function).
+    nx = 260 spans three blocks per row (the middle ones away from every
+    wall)."""
+    p = _sub_case(nx=nx, ny=5, nz=6, model=lbm.LBM_CUMULANT_Q27, flags=flags, gprime=3e-3,
                   eg=(0.3, -0.4, -0.866), nu=0.01, D=0.02, omega_bulk=0.8)
     lat = lbm.Lattice(p, device="cuda")
     s0 = _random_state(p, 3)

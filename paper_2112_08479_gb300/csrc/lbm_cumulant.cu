@@ -47,7 +47,8 @@ namespace lbmgpu {
 // the even step took 2.85 -> 2.75 ms (FP32), 2.16 -> 2.12 (FP16), 2.18 ->
 // 2.13 (BF16).  7 and 8 blocks (72, 64 registers) and the 64-bit form at 4
 // blocks measured slower; odd steps, whose neighbour offsets are the live
-// values, keep 32-bit offsets and 4 blocks.
+// values, keep 32-bit offsets and 4 blocks (5 blocks: 208 bytes of spills,
+// 2.22 -> 2.69 ms per FP16 odd step).
 #ifndef LBM_CUM_MINB_EVEN
 #define LBM_CUM_MINB_EVEN 6
 #endif

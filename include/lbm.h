@@ -107,9 +107,9 @@ typedef enum lbm_storage {
                                   than the default kernel on GB300; ignored elsewhere */
 #define LBM_FLAG_TEST_STALL 32 /* test hook of the failure path of LBM_FLAG_TMA_STAGED: each
                                   block's first tile is announced on its barrier but never
-                                  copied, so its wait cannot end; every wait gives up after 0.1 s, the kernel
-                                  sets LBM_DEVFLAG_TIMEOUT and returns (lbm_diag then
-                                  reports LBM_ERR_TIMEOUT); no fault, no hang */
+                                  copied, so its wait cannot end; every wait gives up after
+                                  0.1 s, the kernel sets LBM_DEVFLAG_TIMEOUT and returns
+                                  (lbm_diag then reports LBM_ERR_TIMEOUT); no fault, no hang */
 #define LBM_FLAG_TEST_BOUNDS 64 /* test hook of the index checks of the debug build (rejected
                                    with LBM_ERR_ARG by the release build): every check uses
                                    half of its array's true extent, so the in-bounds accesses

@@ -64,7 +64,12 @@ namespace lbmgpu {
 // (FP32).  The same form in the paired BGK kernel's wall-free body measured
 // slower (FP16 odd 1.54 -> 1.59 ms), and as a second odd body of the D3Q27
 // FCM instantiation no faster (FP32 4.90 -> 4.89 ms, FP16 4.04 -> 4.11, 36 ->
-// 92 bytes of spills in FP32); neither was adopted.
+// 92 bytes of spills in FP32); neither was adopted.  Running the blocks
+// away from every face as a kernel of their own (a compact grid, the
+// block-uniform body alone, 64-bit offsets: 80 registers without spills, 6
+// blocks per SM) and the face blocks as a second launch (enumerated on a 1-D
+// grid) measured FP32 odd steps 3.01 -> 2.97 ms but FP16 2.20 -> 2.43 and
+// BF16 2.27 -> 2.43, and was not adopted either.
 #ifndef LBM_CUM_NOFACE
 #define LBM_CUM_NOFACE 1
 #endif
